@@ -1,0 +1,232 @@
+"""Oracle for the regularized dipole sum: a plain double-precision CPU statement.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package; the library's product
+path never does.  It shares no code with the CUDA library; both sides only take
+their inputs from the seeded generators in ``paper_2405_16788_gb300.synthetic``.
+
+Every function cites the part of the paper (arXiv 2405.16788) that it states:
+see ``dipole_oracle.c`` for the list of readings taken where the paper is
+silent.  Parity is pinned by ``tests/test_oracle_pins.py`` (closed forms, the
+Gauss lemma, Prop. 1 and Prop. 2, brute-force limits of Barnes-Hut, the
+adjoint identity and tree invariants on exhaustive small cases).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dipole_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: the Morton quantisation, the far test and the node radius
+# are specified operation by operation (no fused multiply-add contraction).
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+          "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile dipole_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_F = ctypes.c_float
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.orc_num_threads.restype = _I
+        lib.orc_rho.restype = ctypes.c_double
+        lib.orc_rho.argtypes = [ctypes.c_double]
+        lib.orc_interleave.restype = ctypes.c_uint32
+        lib.orc_interleave.argtypes = [ctypes.c_uint32] * 3
+        lib.orc_morton.argtypes = [_I64, _P, _P, _P]
+        lib.orc_brute_forward.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P]
+        lib.orc_brute_adjoint.argtypes = [_I64, _P, _P, _P, _P, _I, _I64, _P, _P, _P]
+        lib.orc_tree_build.restype = _P
+        lib.orc_tree_build.argtypes = [_I64, _P, _P, _P, _P, _I, _I]
+        lib.orc_tree_free.argtypes = [_P]
+        lib.orc_tree_num_nodes.restype = _I64
+        lib.orc_tree_num_nodes.argtypes = [_P]
+        lib.orc_tree_export.argtypes = [_P] * 15
+        lib.orc_tree_update.argtypes = [_P, _P, _I]
+        lib.orc_bh_forward.argtypes = [_P, _I64, _P, _F, _P, _P]
+        lib.orc_bh_adjoint.argtypes = [_P, _I64, _P, _F, _P, _P]
+        lib.orc_far_test.restype = _I
+        lib.orc_far_test.argtypes = [_P, _P, _F, _F]
+        _lib = lib
+        return lib
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(_load().orc_num_threads())
+
+
+def rho(t: float) -> float:
+    """rho(t) = erf(t) - 2t/sqrt(pi) exp(-t^2); Sec. 3.1, eq. (regularized_poisson)."""
+    return float(_load().orc_rho(float(t)))
+
+
+def interleave(qx: int, qy: int, qz: int) -> int:
+    """30-bit Morton interleave: x bit k -> 3k+2, y -> 3k+1, z -> 3k."""
+    return int(_load().orc_interleave(qx, qy, qz))
+
+
+def morton(points):
+    """Bounding cube and codes in input order: returns (lo[3], ext, codes[n])."""
+    p = _f32(points)
+    n = p.shape[0]
+    lo_ext = np.zeros(4, np.float32)
+    codes = np.zeros(n, np.uint32)
+    _load().orc_morton(n, _ptr(p), _ptr(lo_ext), _ptr(codes))
+    return lo_ext[:3].copy(), float(lo_ext[3]), codes
+
+
+def brute_forward(points, normals, areas, eps, mu, queries):
+    """Plain O(NQ) sum, eq. (dipole_sum)/(appearance_features): out [Q, C] float64."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    mu = _f32(mu)
+    if mu.ndim == 1:
+        mu = mu[:, None]
+    q = _f32(queries)
+    n, C, nq = p.shape[0], mu.shape[1], q.shape[0]
+    out = np.zeros((nq, C), np.float64)
+    _load().orc_brute_forward(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, _ptr(mu), nq, _ptr(q),
+                              _ptr(out))
+    return out
+
+
+def brute_adjoint(points, normals, areas, eps, queries, g):
+    """dL/dmu [N, C] float64 for dL/dD = g [Q, C]: the transpose of brute_forward."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    q = _f32(queries)
+    g = _f64(g)
+    if g.ndim == 1:
+        g = g[:, None]
+    n, nq, C = p.shape[0], q.shape[0], g.shape[1]
+    out = np.zeros((n, C), np.float64)
+    _load().orc_brute_adjoint(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, nq, _ptr(q), _ptr(g),
+                              _ptr(out))
+    return out
+
+
+def far_test(x, c, r, beta) -> bool:
+    """The far test of Alg. 1 in the float operation order the oracle uses."""
+    xx, cc = _f32(x), _f32(c)
+    return bool(_load().orc_far_test(_ptr(xx), _ptr(cc), float(r), float(beta)))
+
+
+class Tree:
+    """CPU octree, node aggregates and Barnes-Hut queries (Sec. 5, Alg. 1)."""
+
+    def __init__(self, points, normals, areas, eps=None, leaf_size=8, max_depth=10):
+        lib = _load()
+        self._p, self._n, self._a = _f32(points), _f32(normals), _f32(areas)
+        self._e = None if eps is None else _f32(eps)
+        self.n = self._p.shape[0]
+        h = lib.orc_tree_build(self.n, _ptr(self._p), _ptr(self._n), _ptr(self._a),
+                               _ptr(self._e), int(leaf_size), int(max_depth))
+        if not h:
+            raise ValueError("oracle tree build rejected its arguments")
+        self._h = ctypes.c_void_p(h)
+        self.nn = int(lib.orc_tree_num_nodes(self._h))
+        self.C = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().orc_tree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self) -> dict:
+        """All integer arrays and node geometry as numpy arrays."""
+        n, nn = self.n, self.nn
+        o = dict(lo_ext=np.zeros(4, np.float32), code=np.zeros(n, np.uint32),
+                 perm=np.zeros(n, np.uint32), first=np.zeros(nn, np.int32),
+                 count=np.zeros(nn, np.int32), level=np.zeros(nn, np.int32),
+                 parent=np.zeros(nn, np.int32), skip=np.zeros(nn, np.int32),
+                 is_leaf=np.zeros(nn, np.int32), area=np.zeros(nn, np.float64),
+                 cen=np.zeros((nn, 3), np.float64), eps=np.zeros(nn, np.float64),
+                 cen32=np.zeros((nn, 3), np.float32), r32=np.zeros(nn, np.float32))
+        keys = ["lo_ext", "code", "perm", "first", "count", "level", "parent", "skip",
+                "is_leaf", "area", "cen", "eps", "cen32", "r32"]
+        _load().orc_tree_export(self._h, *[_ptr(o[k]) for k in keys])
+        return o
+
+    def update(self, mu):
+        """Tree update of the node moments, eq. (farfield_dipole_features)."""
+        mu = _f32(mu)
+        if mu.ndim == 1:
+            mu = mu[:, None]
+        if mu.shape[0] != self.n:
+            raise ValueError("mu must have one row per point")
+        self.C = mu.shape[1]
+        _load().orc_tree_update(self._h, _ptr(mu), self.C)
+
+    def forward(self, queries, beta, counters=False):
+        """PrimalQuery for every query (Alg. 1): [Q, C] float64 (and [Q,3] counters)."""
+        if self.C is None:
+            raise RuntimeError("call update() first")
+        q = _f32(queries)
+        nq = q.shape[0]
+        out = np.zeros((nq, self.C), np.float64)
+        cnt = np.zeros((nq, 3), np.int64) if counters else None
+        _load().orc_bh_forward(self._h, nq, _ptr(q), float(beta), _ptr(out), _ptr(cnt))
+        return (out, cnt) if counters else out
+
+    def adjoint(self, queries, beta, g):
+        """Two-stage adjoint (Sec. 5.2, App. C): dL/dmu [N, C] float64, input order."""
+        if self.C is None:
+            raise RuntimeError("call update() first")
+        q = _f32(queries)
+        g = _f64(g)
+        if g.ndim == 1:
+            g = g[:, None]
+        if g.shape != (q.shape[0], self.C):
+            raise ValueError("g must be [Q, C]")
+        out = np.zeros((self.n, self.C), np.float64)
+        _load().orc_bh_adjoint(self._h, q.shape[0], _ptr(q), float(beta), _ptr(g), _ptr(out))
+        return out

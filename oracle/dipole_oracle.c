@@ -1,0 +1,568 @@
+/*
+ * Oracle for the regularized dipole sum and its Barnes-Hut evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, double-precision CPU
+ * statement of what the GPU library computes.  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it; the product path never
+ * does.  It shares no code, header or constant table with the CUDA library.
+ *
+ * Paper: Chen, Miller, Gkioulekas, "3D Reconstruction with Fast Dipole Sums"
+ * (arXiv 2405.16788).  Citations name the paper's sections and equations.
+ *
+ *   rho, P_eps          Sec. 3.1, eq. (regularized_poisson) and eq. (pcwn)
+ *   dipole sum          Sec. 3.2, eq. (dipole_sum); multi-channel: eq. (appearance_features)
+ *   node aggregates     Sec. 5.1, eqs. (farfield_dipole), (farfield_dipole_features)
+ *   far field           Sec. 5.1, eq. (farfield)
+ *   primal query        Alg. 1, PrimalQuery
+ *   adjoint, stage 1    Alg. 1, AdjointQuery; App. C, eq. (farfield_gradient)
+ *   adjoint, stage 2    Sec. 5.2 (two-stage scheme); App. C, eq. (farfield_features_gradient)
+ *
+ * Readings of the paper that this file takes where the paper is silent or
+ * ambiguous (each one is also listed in the design notes):
+ *   R1  The 1/(4 pi) of eq. (pcwn) is kept in the far field, in GetContribution
+ *       and in IncrementGradient (the printed forms drop it).
+ *   R2  rho(t) = erf(t) - 2t/sqrt(pi) exp(-t^2) with t = r/eps, as printed.
+ *       eps = 0 means rho = 1 (the singular kernel).  A term with r = 0 is 0.
+ *   R3  Leaves hold up to leaf_size points (single points in the paper); an
+ *       opened leaf sums its points exactly.  The far test comes first, then
+ *       the leaf test, as in Alg. 1.
+ *   R4  The octree is the compressed 30-bit Morton octree specified below.
+ *   R5  Per-point eps_m: a node uses the area-weighted mean eps of its points.
+ *   R6  The far test is evaluated in single precision on single-precision node
+ *       geometry with the fixed operation order below, so that a CPU and a GPU
+ *       implementation take identical decisions.  All values are double.
+ *   R7  Node sums (area, area-weighted position, area-weighted eps) are formed
+ *       in double, point by point inside a leaf and child by child inside an
+ *       internal node, both in Morton order.  The node centroid is that ratio
+ *       rounded to float; the node radius is the largest float distance from
+ *       that float centroid to a point of the node.
+ *   R8  AS(m) in eq. (farfield_features_gradient) includes the leaf holding m.
+ *
+ * Compile with -ffp-contract=off: the Morton quantisation, the far test and
+ * the radius are specified operation by operation.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MAX_LEVEL 10 /* 30-bit codes: 10 octal digits */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel (Sec. 3.1)                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* rho(t) = erf(t) - (2 t / sqrt(pi)) exp(-t^2): the regularizing factor of
+ * eq. (regularized_poisson).  t = +inf gives 1. */
+double orc_rho(double t) {
+    if (isinf(t)) return 1.0;
+    return erf(t) - 2.0 * t / sqrt(ORC_PI) * exp(-t * t);
+}
+
+/* rho(r / eps), with eps = 0 meaning the singular kernel (R2). */
+static double rho_r(double r, double eps) {
+    if (eps == 0.0) return 1.0;
+    return orc_rho(r / eps);
+}
+
+/* A * P_eps(x, p) : area times the regularized Poisson kernel, eq. (pcwn) with
+ * the factor of eq. (regularized_poisson).  Returns 0 when x == p (R2). */
+static double point_weight(const double x[3], double px, double py, double pz,
+                           double nx, double ny, double nz, double A, double eps) {
+    double dx = px - x[0], dy = py - x[1], dz = pz - x[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return 0.0;
+    double r = sqrt(r2);
+    return A * rho_r(r, eps) * (nx * dx + ny * dy + nz * dz) / (4.0 * ORC_PI * r2 * r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute force: the plain definition, eq. (dipole_sum) / (appearance_features) */
+/* ------------------------------------------------------------------------ */
+
+/* out[j*C + c] = sum_m A_m P_eps_m(x_j, p_m) mu[m*C + c].
+ * pts, nrm: [n,3]; area, eps: [n] (eps may be NULL: all zero); mu: [n,C]. */
+void orc_brute_forward(int64_t n, const float* pts, const float* nrm, const float* area,
+                       const float* eps, int C, const float* mu, int64_t q,
+                       const float* qry, double* out) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < q; ++j) {
+        double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double* o = out + j * C;
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        for (int64_t m = 0; m < n; ++m) {
+            double w = point_weight(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], nrm[3 * m],
+                                    nrm[3 * m + 1], nrm[3 * m + 2], area[m],
+                                    eps ? (double)eps[m] : 0.0);
+            for (int c = 0; c < C; ++c) o[c] += w * (double)mu[m * C + c];
+        }
+    }
+}
+
+/* Gradient of L with respect to mu when dL/dD(x_j) = g[j*C + c]:
+ * grad[m*C + c] = sum_j g[j*C + c] A_m P_eps_m(x_j, p_m).  D is linear in mu. */
+void orc_brute_adjoint(int64_t n, const float* pts, const float* nrm, const float* area,
+                       const float* eps, int C, int64_t q, const float* qry, const double* g,
+                       double* grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < n; ++m) {
+        double* gm = grad + m * C;
+        for (int c = 0; c < C; ++c) gm[c] = 0.0;
+        for (int64_t j = 0; j < q; ++j) {
+            double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+            double w = point_weight(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], nrm[3 * m],
+                                    nrm[3 * m + 1], nrm[3 * m + 2], area[m],
+                                    eps ? (double)eps[m] : 0.0);
+            for (int c = 0; c < C; ++c) gm[c] += w * g[j * C + c];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Octree (R4), Sec. 5.1 and Sec. 5.3 "tree construction"                     */
+/* ------------------------------------------------------------------------ */
+/*
+ * Bounding cube: lo = per-axis float minimum; ext = largest per-axis
+ * (max - min), computed in float; ext = 1 when it is 0.
+ * Quantisation: s = 1024 / ext (float division); per axis
+ *   q = min(1023, floor((p - lo) * s)) with the subtraction and the product
+ *   rounded to float one at a time.
+ * Code: bit k of qx goes to bit 3k+2, of qy to 3k+1, of qz to 3k.
+ * Order: by (code, original index).
+ * A node at level l is a maximal run of sorted codes sharing their top 3l
+ * bits.  A run with at most leaf_size points, or at level max_depth, is a
+ * leaf.  Otherwise its children are the runs at level l+1 inside it, in code
+ * order; when there is only one, the node is that child (chains collapse).
+ * Nodes are stored in depth-first preorder; skip[t] is the index just past
+ * t's subtree.
+ */
+
+static uint32_t spread10(uint32_t v) {
+    uint32_t r = 0;
+    for (int k = 0; k < 10; ++k) r |= ((v >> k) & 1u) << (3 * k);
+    return r;
+}
+
+uint32_t orc_interleave(uint32_t qx, uint32_t qy, uint32_t qz) {
+    return (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+}
+
+/* Bounding cube and 30-bit codes in input order. lo_ext: out[4] = lo.xyz, ext. */
+void orc_morton(int64_t n, const float* pts, float* lo_ext, uint32_t* codes) {
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = pts[a]; hi[a] = pts[a]; }
+    for (int64_t m = 1; m < n; ++m)
+        for (int a = 0; a < 3; ++a) {
+            float v = pts[3 * m + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float e = hi[a] - lo[a];
+        if (e > ext) ext = e;
+    }
+    if (!(ext > 0.0f)) ext = 1.0f;
+    float s = 1024.0f / ext;
+    for (int64_t m = 0; m < n; ++m) {
+        uint32_t qv[3];
+        for (int a = 0; a < 3; ++a) {
+            float d = pts[3 * m + a] - lo[a];
+            float t = d * s;
+            float f = floorf(t);
+            uint32_t qa = (uint32_t)f;
+            qv[a] = qa > 1023u ? 1023u : qa;
+        }
+        codes[m] = orc_interleave(qv[0], qv[1], qv[2]);
+    }
+    lo_ext[0] = lo[0]; lo_ext[1] = lo[1]; lo_ext[2] = lo[2]; lo_ext[3] = ext;
+}
+
+static int cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+typedef struct orc_tree {
+    int64_t n, nn, cap;
+    int leaf_size, max_depth;
+    float lo_ext[4];
+    uint32_t* code;  /* [n] sorted */
+    uint32_t* perm;  /* [n] sorted position -> input index */
+    float* p;        /* [n,3] sorted positions */
+    float* nrm;      /* [n,3] sorted normals */
+    float* A;        /* [n] sorted areas */
+    float* eps;      /* [n] sorted regularization radii */
+    int32_t *first, *count, *level, *parent, *skip, *is_leaf; /* [nn] */
+    int32_t* leaf_of; /* [n] sorted position -> leaf node */
+    double* area;     /* [nn]  A~_t */
+    double* cen;      /* [nn,3] p~_t (double) */
+    double* epsn;     /* [nn]  eps~_t */
+    float* cen32;     /* [nn,3] p~_t rounded to float (far test, R6/R7) */
+    float* r32;       /* [nn]  r~_t (R7) */
+    int C;
+    double* mu;       /* [n,C] sorted attributes */
+    double* nt;       /* [nn,3C] n~_t^c, eq. (farfield_dipole_features) */
+    double *s_area, *s_ap, *s_ae; /* [nn], [nn,3], [nn] double node sums (R7) */
+} orc_tree;
+
+static int32_t emit(orc_tree* T, int64_t a, int64_t cnt, int level, int32_t parent, int leaf) {
+    int64_t i = T->nn++;
+    T->first[i] = (int32_t)a;
+    T->count[i] = (int32_t)cnt;
+    T->level[i] = level;
+    T->parent[i] = parent;
+    T->is_leaf[i] = leaf;
+    T->skip[i] = (int32_t)(i + 1);
+    return (int32_t)i;
+}
+
+static void build_node(orc_tree* T, int64_t a, int64_t b, int level, int32_t parent) {
+    int64_t cnt = b - a;
+    if (cnt <= T->leaf_size || level >= T->max_depth) {
+        int32_t t = emit(T, a, cnt, level, parent, 1);
+        for (int64_t m = a; m < b; ++m) T->leaf_of[m] = t;
+        return;
+    }
+    int shift = 3 * (ORC_MAX_LEVEL - 1 - level);
+    uint32_t d0 = (T->code[a] >> shift) & 7u, d1 = (T->code[b - 1] >> shift) & 7u;
+    if (d0 == d1) { /* one child: the node is that child */
+        build_node(T, a, b, level + 1, parent);
+        return;
+    }
+    int32_t t = emit(T, a, cnt, level, parent, 0);
+    int64_t s = a;
+    while (s < b) {
+        uint32_t d = (T->code[s] >> shift) & 7u;
+        int64_t e = s + 1;
+        while (e < b && ((T->code[e] >> shift) & 7u) == d) ++e;
+        build_node(T, s, e, level + 1, t);
+        s = e;
+    }
+    T->skip[t] = (int32_t)T->nn;
+}
+
+/* Children of internal node t in order: t+1, skip[t+1], ... while < skip[t]. */
+
+/* Node sums in the order of R7, then centroid, mean eps, float centroid. */
+static void node_sums(orc_tree* T, int32_t t) {
+    double sa = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0;
+    if (T->is_leaf[t]) {
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double A = T->A[m];
+            sa += A;
+            sx += A * (double)T->p[3 * m];
+            sy += A * (double)T->p[3 * m + 1];
+            sz += A * (double)T->p[3 * m + 2];
+            se += A * (double)T->eps[m];
+        }
+    } else {
+        for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c]) {
+            node_sums(T, c);
+            sa += T->s_area[c];
+            sx += T->s_ap[3 * c];
+            sy += T->s_ap[3 * c + 1];
+            sz += T->s_ap[3 * c + 2];
+            se += T->s_ae[c];
+        }
+    }
+    T->s_area[t] = sa;
+    T->s_ap[3 * t] = sx; T->s_ap[3 * t + 1] = sy; T->s_ap[3 * t + 2] = sz;
+    T->s_ae[t] = se;
+    /* eq. (farfield_dipole): A~ = sum A; p~ = sum A p / A~ */
+    T->area[t] = sa;
+    T->cen[3 * t] = sx / sa; T->cen[3 * t + 1] = sy / sa; T->cen[3 * t + 2] = sz / sa;
+    T->epsn[t] = se / sa; /* R5 */
+    for (int a = 0; a < 3; ++a) T->cen32[3 * t + a] = (float)T->cen[3 * t + a];
+    /* r~ = max_m |p_m - p~| over the node's points, in float (R7) */
+    float r = 0.0f;
+    for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+        float ex = T->p[3 * m] - T->cen32[3 * t];
+        float ey = T->p[3 * m + 1] - T->cen32[3 * t + 1];
+        float ez = T->p[3 * m + 2] - T->cen32[3 * t + 2];
+        float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        float d = sqrtf(d2);
+        if (d > r) r = d;
+    }
+    T->r32[t] = r;
+}
+
+void orc_tree_free(orc_tree* T) {
+    if (!T) return;
+    free(T->code); free(T->perm); free(T->p); free(T->nrm); free(T->A); free(T->eps);
+    free(T->first); free(T->count); free(T->level); free(T->parent); free(T->skip);
+    free(T->is_leaf); free(T->leaf_of); free(T->area); free(T->cen); free(T->epsn);
+    free(T->cen32); free(T->r32); free(T->mu); free(T->nt);
+    free(T->s_area); free(T->s_ap); free(T->s_ae);
+    free(T);
+}
+
+/* Build the octree over n points (input order).  eps may be NULL (all zero).
+ * Returns NULL on bad arguments: n < 1, leaf_size < 1, max_depth outside
+ * [0, 10], or a non-positive area (R: areas must be > 0 for p~ to exist). */
+orc_tree* orc_tree_build(int64_t n, const float* pts, const float* nrm, const float* area,
+                         const float* eps, int leaf_size, int max_depth) {
+    if (n < 1 || leaf_size < 1 || max_depth < 0 || max_depth > ORC_MAX_LEVEL) return NULL;
+    for (int64_t m = 0; m < n; ++m)
+        if (!(area[m] > 0.0f)) return NULL;
+    orc_tree* T = (orc_tree*)calloc(1, sizeof(orc_tree));
+    T->n = n;
+    T->cap = 2 * n + 1;
+    T->leaf_size = leaf_size;
+    T->max_depth = max_depth;
+    uint32_t* codes_in = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    orc_morton(n, pts, T->lo_ext, codes_in);
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * n);
+    for (int64_t m = 0; m < n; ++m) key[m] = ((uint64_t)codes_in[m] << 32) | (uint64_t)m;
+    qsort(key, (size_t)n, sizeof(uint64_t), cmp_u64);
+    T->code = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    T->perm = (uint32_t*)malloc(sizeof(uint32_t) * n);
+    T->p = (float*)malloc(sizeof(float) * 3 * n);
+    T->nrm = (float*)malloc(sizeof(float) * 3 * n);
+    T->A = (float*)malloc(sizeof(float) * n);
+    T->eps = (float*)malloc(sizeof(float) * n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t m = (uint32_t)(key[i] & 0xffffffffu);
+        T->code[i] = (uint32_t)(key[i] >> 32);
+        T->perm[i] = m;
+        for (int a = 0; a < 3; ++a) {
+            T->p[3 * i + a] = pts[3 * (int64_t)m + a];
+            T->nrm[3 * i + a] = nrm[3 * (int64_t)m + a];
+        }
+        T->A[i] = area[m];
+        T->eps[i] = eps ? eps[m] : 0.0f;
+    }
+    free(key);
+    free(codes_in);
+    int64_t cap = T->cap;
+    T->first = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->count = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->level = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->parent = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->skip = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->is_leaf = (int32_t*)malloc(sizeof(int32_t) * cap);
+    T->leaf_of = (int32_t*)malloc(sizeof(int32_t) * n);
+    T->nn = 0;
+    build_node(T, 0, n, 0, -1);
+    int64_t nn = T->nn;
+    T->area = (double*)malloc(sizeof(double) * nn);
+    T->cen = (double*)malloc(sizeof(double) * 3 * nn);
+    T->epsn = (double*)malloc(sizeof(double) * nn);
+    T->cen32 = (float*)malloc(sizeof(float) * 3 * nn);
+    T->r32 = (float*)malloc(sizeof(float) * nn);
+    T->s_area = (double*)malloc(sizeof(double) * nn);
+    T->s_ap = (double*)malloc(sizeof(double) * 3 * nn);
+    T->s_ae = (double*)malloc(sizeof(double) * nn);
+    node_sums(T, 0);
+    return T;
+}
+
+int64_t orc_tree_num_nodes(const orc_tree* T) { return T->nn; }
+
+/* Copy out the tree.  Any pointer may be NULL. */
+void orc_tree_export(const orc_tree* T, float* lo_ext, uint32_t* code, uint32_t* perm,
+                     int32_t* first, int32_t* count, int32_t* level, int32_t* parent,
+                     int32_t* skip, int32_t* is_leaf, double* area, double* cen, double* epsn,
+                     float* cen32, float* r32) {
+    int64_t n = T->n, nn = T->nn;
+    if (lo_ext) memcpy(lo_ext, T->lo_ext, sizeof(float) * 4);
+    if (code) memcpy(code, T->code, sizeof(uint32_t) * n);
+    if (perm) memcpy(perm, T->perm, sizeof(uint32_t) * n);
+    if (first) memcpy(first, T->first, sizeof(int32_t) * nn);
+    if (count) memcpy(count, T->count, sizeof(int32_t) * nn);
+    if (level) memcpy(level, T->level, sizeof(int32_t) * nn);
+    if (parent) memcpy(parent, T->parent, sizeof(int32_t) * nn);
+    if (skip) memcpy(skip, T->skip, sizeof(int32_t) * nn);
+    if (is_leaf) memcpy(is_leaf, T->is_leaf, sizeof(int32_t) * nn);
+    if (area) memcpy(area, T->area, sizeof(double) * nn);
+    if (cen) memcpy(cen, T->cen, sizeof(double) * 3 * nn);
+    if (epsn) memcpy(epsn, T->epsn, sizeof(double) * nn);
+    if (cen32) memcpy(cen32, T->cen32, sizeof(float) * 3 * nn);
+    if (r32) memcpy(r32, T->r32, sizeof(float) * nn);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree update: eq. (farfield_dipole_features)                                */
+/* ------------------------------------------------------------------------ */
+
+/* n~_t^c = (1/A~_t) sum_{m in t} A_m n_m mu_m^c for every node; mu: [n,C] in
+ * input order. */
+void orc_tree_update(orc_tree* T, const float* mu, int C) {
+    int64_t n = T->n, nn = T->nn;
+    free(T->mu);
+    free(T->nt);
+    T->C = C;
+    T->mu = (double*)malloc(sizeof(double) * n * C);
+    T->nt = (double*)calloc((size_t)(nn * 3 * C), sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < C; ++c) T->mu[i * C + c] = mu[(int64_t)T->perm[i] * C + c];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < nn; ++t) {
+        double* o = T->nt + t * 3 * C;
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double A = T->A[m];
+            for (int c = 0; c < C; ++c) {
+                double v = A * T->mu[m * C + c];
+                o[3 * c] += v * T->nrm[3 * m];
+                o[3 * c + 1] += v * T->nrm[3 * m + 1];
+                o[3 * c + 2] += v * T->nrm[3 * m + 2];
+            }
+        }
+        for (int k = 0; k < 3 * C; ++k) o[k] /= T->area[t];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Barnes-Hut queries: Alg. 1                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Far test of Alg. 1, |x - p~_t| > beta r~_t, in float with a fixed order (R6). */
+static int far_test(const float x[3], const float* c, float r, float beta) {
+    float dx = x[0] - c[0];
+    float dy = x[1] - c[1];
+    float dz = x[2] - c[2];
+    float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float R = beta * r;
+    return d2 > R * R;
+}
+
+int orc_far_test(const float* x, const float* c, float r, float beta) {
+    return far_test(x, c, r, beta);
+}
+
+/* rho(|p~ - x| / eps~) (p~ - x) / (4 pi |p~ - x|^3): the common factor of
+ * GetContribution (eq. farfield) and IncrementGradient (eq. farfield_gradient),
+ * without A~ and n~ (R1). */
+static void far_vector(const orc_tree* T, int32_t t, const double x[3], double v[3]) {
+    double dx = T->cen[3 * t] - x[0], dy = T->cen[3 * t + 1] - x[1], dz = T->cen[3 * t + 2] - x[2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    double d = sqrt(d2);
+    double k = rho_r(d, T->epsn[t]) / (4.0 * ORC_PI * d2 * d);
+    v[0] = k * dx; v[1] = k * dy; v[2] = k * dz;
+}
+
+typedef struct { int64_t tested, accepted, leafpts; } counters;
+
+/* PrimalQuery(x, node): returns all C channels at once (Sec. 5.3). */
+static void primal_query(const orc_tree* T, const float xf[3], const double x[3], int32_t t,
+                         float beta, double* out, counters* k) {
+    int C = T->C;
+    k->tested++;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
+        /* GetContribution: A~ rho (p~ - x)/|p~ - x|^3 . n~ / (4 pi) */
+        double v[3];
+        far_vector(T, t, x, v);
+        const double* nt = T->nt + (int64_t)t * 3 * C;
+        for (int c = 0; c < C; ++c)
+            out[c] += T->area[t] * (v[0] * nt[3 * c] + v[1] * nt[3 * c + 1] + v[2] * nt[3 * c + 2]);
+        k->accepted++;
+        return;
+    }
+    if (T->is_leaf[t]) { /* exact sum over the leaf's points (R3) */
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double w = point_weight(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2],
+                                    T->nrm[3 * m], T->nrm[3 * m + 1], T->nrm[3 * m + 2],
+                                    T->A[m], T->eps[m]);
+            for (int c = 0; c < C; ++c) out[c] += w * T->mu[m * C + c];
+        }
+        k->leafpts += T->count[t];
+        return;
+    }
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c])
+        primal_query(T, xf, x, c, beta, out, k);
+}
+
+/* out[j*C + c] = Barnes-Hut dipole sum at qry[j]; cnt (may be NULL) receives
+ * per query {nodes tested, nodes accepted, leaf points summed}. */
+void orc_bh_forward(const orc_tree* T, int64_t q, const float* qry, float beta, double* out,
+                    int64_t* cnt) {
+    int C = T->C;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        double* o = out + j * C;
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        counters k = {0, 0, 0};
+        primal_query(T, xf, x, 0, beta, o, &k);
+        if (cnt) { cnt[3 * j] = k.tested; cnt[3 * j + 1] = k.accepted; cnt[3 * j + 2] = k.leafpts; }
+    }
+}
+
+/* AdjointQuery(dD, x, node): stage 1 of the two-stage scheme (Sec. 5.2).
+ * dnt: [nn,3C] node gradients d n~_t; dmu: [n,C] sorted, for opened leaves. */
+static void adjoint_query(const orc_tree* T, const float xf[3], const double x[3],
+                          const double* g, int32_t t, float beta, double* dnt, double* dmu) {
+    int C = T->C;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
+        /* IncrementGradient, eq. (farfield_gradient) */
+        double v[3];
+        far_vector(T, t, x, v);
+        double* o = dnt + (int64_t)t * 3 * C;
+        for (int c = 0; c < C; ++c)
+            for (int a = 0; a < 3; ++a) {
+                double inc = T->area[t] * v[a] * g[c];
+#pragma omp atomic
+                o[3 * c + a] += inc;
+            }
+        return;
+    }
+    if (T->is_leaf[t]) { /* opened leaf: exact per-point derivative (R3) */
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double w = point_weight(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2],
+                                    T->nrm[3 * m], T->nrm[3 * m + 1], T->nrm[3 * m + 2],
+                                    T->A[m], T->eps[m]);
+            for (int c = 0; c < C; ++c) {
+                double inc = w * g[c];
+#pragma omp atomic
+                dmu[m * C + c] += inc;
+            }
+        }
+        return;
+    }
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c])
+        adjoint_query(T, xf, x, g, c, beta, dnt, dmu);
+}
+
+/* grad[m*C + c] (input order) = d L / d mu_m^c, given g[j*C + c] = dL/dD^c(x_j):
+ * stage 1 over all queries, then stage 2, eq. (farfield_features_gradient):
+ *   d mu_m = sum_{t in AS(m)} (A_m / A~_t) n_m . d n~_t   (R8). */
+void orc_bh_adjoint(const orc_tree* T, int64_t q, const float* qry, float beta, const double* g,
+                    double* grad) {
+    int C = T->C;
+    int64_t n = T->n, nn = T->nn;
+    double* dnt = (double*)calloc((size_t)(nn * 3 * C), sizeof(double));
+    double* dmu = (double*)calloc((size_t)(n * C), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        adjoint_query(T, xf, x, g + j * C, 0, beta, dnt, dmu);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < n; ++m) {
+        double* gm = grad + (int64_t)T->perm[m] * C;
+        for (int c = 0; c < C; ++c) gm[c] = dmu[m * C + c];
+        for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
+            double f = (double)T->A[m] / T->area[t];
+            const double* d = dnt + (int64_t)t * 3 * C;
+            for (int c = 0; c < C; ++c)
+                gm[c] += f * (T->nrm[3 * m] * d[3 * c] + T->nrm[3 * m + 1] * d[3 * c + 1] +
+                              T->nrm[3 * m + 2] * d[3 * c + 2]);
+        }
+    }
+    free(dnt);
+    free(dmu);
+}
