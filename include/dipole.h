@@ -1,0 +1,208 @@
+/*
+ * dipole.h -- C ABI of the GB300 (sm_103a) library for Barnes-Hut fast
+ * summation of regularized dipole sums, forward and adjoint.
+ *
+ * Method: Chen, Miller, Gkioulekas, "3D Reconstruction with Fast Dipole Sums"
+ * (arXiv 2405.16788).  For points p_m with outward unit normals n_m, area
+ * weights A_m > 0, regularization radii eps_m >= 0 and C attribute channels
+ * mu_m^c, the library evaluates at query points x
+ *
+ *   D^c(x) = sum_m A_m rho(|p_m - x| / eps_m) n_m.(p_m - x) / (4 pi |p_m - x|^3) mu_m^c,
+ *   rho(t) = erf(t) - (2t/sqrt(pi)) exp(-t^2)
+ *
+ * (Sec. 3.2, eq. dipole_sum; Sec. 3.1, eq. regularized_poisson; Sec. 4.1,
+ * eq. appearance_features for several channels), approximated by Barnes-Hut
+ * (Sec. 5.1, eq. farfield; Alg. 1, PrimalQuery), and its adjoint with respect
+ * to mu by the two-stage scheme of Sec. 5.2 (Alg. 1, AdjointQuery; App. C,
+ * eqs. farfield_gradient and farfield_features_gradient).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments are DEVICE pointers on the current CUDA device, owned by
+ *    the caller, unless a comment says "host".  Float arrays are row-major
+ *    and contiguous.  Points, attributes and gradients are in the caller's
+ *    order; the library keeps its own Morton-ordered copies.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous on it unless a comment says otherwise.
+ *  - Every call returns a dipole_status; nothing crosses the ABI as a C++
+ *    exception.  On failure dipole_last_error() gives a message for the
+ *    calling thread.  Errors found by kernels (a traversal that exceeded its
+ *    step bound, a non-finite query) set a device status word that
+ *    dipole_sync_status() returns and clears.
+ *  - The tree owns its device memory; dipole_tree_destroy releases it.
+ */
+#ifndef DIPOLE_H
+#define DIPOLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dipole_tree dipole_tree;
+
+typedef enum {
+    DIPOLE_OK = 0,
+    DIPOLE_EINVAL = -1,      /* bad argument (null pointer, size, non-positive area, ...) */
+    DIPOLE_ENOMEM = -2,      /* device allocation failed */
+    DIPOLE_ECUDA = -3,       /* a CUDA call failed; see dipole_last_error() */
+    DIPOLE_ENONFINITE = -4,  /* a non-finite input was found */
+    DIPOLE_ETRAVERSAL = -5,  /* a traversal exceeded its step bound (corrupt tree) */
+    DIPOLE_ESTATE = -6       /* call out of order (e.g. forward before any refit) */
+} dipole_status;
+
+typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
+
+/* Octree parameters.  leaf_size in [1, 64] (the paper's leaves are single
+ * points, Sec. 5.1; 8 is the default here); max_depth in [0, 10] octal digits
+ * of the 30-bit Morton code. */
+typedef struct {
+    int32_t leaf_size;
+    int32_t max_depth;
+} dipole_build_params;
+
+typedef struct {
+    int64_t n_points;
+    int64_t n_nodes;
+    int32_t channels;    /* C of the last refit, 0 before the first */
+    int32_t dtype;       /* dipole_dtype of the last refit */
+    int32_t leaf_size;
+    int32_t max_depth;
+    float bbox_lo[3];    /* bounding cube of the Morton quantisation */
+    float bbox_ext;
+} dipole_tree_info;
+
+/*
+ * Build the octree over n points (Sec. 5.3, "tree construction and update":
+ * built once, positions are not optimized) and the node geometry of
+ * Sec. 5.1, eq. farfield_dipole: area A~_t = sum A_m, centroid
+ * p~_t = sum A_m p_m / A~_t, radius r~_t = max |p_m - p~_t|, and the node
+ * regularization radius eps~_t = sum A_m eps_m / A~_t.
+ *
+ *   points  [n,3] float   positions p_m
+ *   normals [n,3] float   outward unit normals n_m
+ *   areas   [n]   float   area weights A_m, each > 0
+ *   radii   [n]   float   regularization radii eps_m >= 0, or NULL for all 0
+ *                         (eps = 0 is the singular kernel of eq. pcwn)
+ *   n       >= 1
+ *   params  NULL for {leaf_size 8, max_depth 10}
+ *   out     receives the new tree (host pointer to a host pointer)
+ *
+ * The tree is the compressed 30-bit Morton octree: bounding cube, per-axis
+ * quantisation to 1024 cells, codes sorted stably, nodes = maximal runs of
+ * equal code prefixes that branch, leaves = runs of at most leaf_size points
+ * (or at max_depth), in depth-first preorder.  Its integer arrays are
+ * bit-identical to the CPU oracle's.
+ *
+ * Synchronizes `stream` once (the node count sizes the node arrays).
+ * Errors: DIPOLE_EINVAL for a null pointer, n < 1, bad params, an area <= 0
+ * or a negative radius; DIPOLE_ENONFINITE for a non-finite input.
+ */
+int dipole_build_tree(const float* points, const float* normals, const float* areas,
+                      const float* radii, int64_t n, const dipole_build_params* params,
+                      void* stream, dipole_tree** out);
+
+/*
+ * Tree update of the node moments (Sec. 5.3: done at the start of every
+ * iteration; Sec. 5.1, eq. farfield_dipole_features):
+ *   S_t^c = A~_t n~_t^c = sum_{m in t} A_m n_m mu_m^c   (3 values per channel)
+ *
+ *   attrs     [n, channels] float (dtype DIPOLE_F32) or bfloat16 (DIPOLE_BF16)
+ *   channels  in [1, 64]
+ *
+ * The attributes are copied into Morton order in the given dtype (bf16
+ * storage halves their bytes; arithmetic is float).  Node sums are float for
+ * small nodes and double for nodes of 2^15 or more points.
+ * Errors: DIPOLE_EINVAL for a null pointer or a bad channel count/dtype.
+ */
+int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,
+                 void* stream);
+
+/*
+ * Primal queries (Alg. 1, PrimalQuery; all channels in one traversal, Sec.
+ * 5.3): out[j, c] = Barnes-Hut estimate of D^c(queries[j]).  A node t is far
+ * when |x - p~_t| > beta r~_t (strict), evaluated in float as
+ *   dx = x - p~ (per axis), d2 = fma(dz,dz, fma(dy,dy, dx*dx)), R = beta*r~,
+ *   far = d2 > R*R;
+ * a far node contributes rho(d/eps~_t) S_t.(p~_t - x) / (4 pi d^3) (eq.
+ * farfield with the 1/(4 pi) of eq. pcwn); an opened leaf adds its points
+ * exactly.  Sums are float with Kahan compensation.
+ *
+ *   queries [q,3] float; q >= 0 (q = 0 is a no-op)
+ *   beta    > 0 (larger is more accurate; the paper gives no value)
+ *   out     [q, channels] float (channels of the last refit)
+ *
+ * Queries are sorted by Morton code internally.  Reentrant: concurrent
+ * forward calls on one tree are allowed.  Errors: DIPOLE_ESTATE before the
+ * first refit; DIPOLE_EINVAL for null pointers or beta <= 0.
+ */
+int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                   float* out, void* stream);
+
+/*
+ * Adjoint queries, two-stage (Sec. 5.2, App. C).  Given grad_out[j, c] =
+ * dL/dD^c(queries[j]):
+ *   stage 1 (Alg. 1, AdjointQuery; eq. farfield_gradient): the same traversal
+ *     as dipole_forward adds rho(d/eps~) (p~ - x)/(4 pi d^3) g^c into dS_t^c at
+ *     every far node and the exact per-point term into the points of opened
+ *     leaves;
+ *   stage 2 (eq. farfield_features_gradient): dL/dmu_m^c = A_m n_m . sum over
+ *     the nodes holding m of dS_t^c, plus the opened-leaf terms.
+ *
+ *   grad_out   [q, channels] float
+ *   grad_attrs [n, channels] float, caller's point order
+ *   accumulate 0: overwrite grad_attrs; 1: add to it
+ *
+ * The result does not depend on the attributes (D is linear in mu), only on
+ * the geometry and channels of the last refit.  Uses scratch owned by the
+ * tree: adjoint calls on one tree must not overlap.
+ */
+int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                   const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream);
+
+/*
+ * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,
+ * leaf points summed} (int32 [q,3], device).  Same traversal and decisions as
+ * dipole_forward; used for the roofline's algorithmic bytes and to check the
+ * traversal decisions against the oracle.
+ */
+int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        int32_t* counts, void* stream);
+
+/* Synchronize `stream`, then return and clear the device status word:
+ * DIPOLE_OK, DIPOLE_ETRAVERSAL or DIPOLE_ENONFINITE. */
+int dipole_sync_status(dipole_tree* tree, void* stream);
+
+/* Sizes and parameters of the tree (host struct; no device work). */
+int dipole_tree_info_get(const dipole_tree* tree, dipole_tree_info* info);
+
+/*
+ * Copy the tree to HOST arrays (synchronizes `stream`).  Any pointer may be
+ * NULL.  Node arrays have n_nodes entries in preorder; point arrays n_points
+ * entries in Morton order.
+ *   codes, perm              uint32 [n]   sorted codes; perm[i] = caller index of point i
+ *   first, count, level,     int32 [nn]   point range, octree level, parent (-1 at root),
+ *   parent, skip, is_leaf                 index past the subtree, leaf flag
+ *   centroid [nn,3] float, radius [nn] float, area [nn] double, eps [nn] float
+ *   moments  [nn, 3*channels] float  S_t^c as (c, axis), or NULL; needs a refit
+ */
+int dipole_tree_export(const dipole_tree* tree, uint32_t* codes, uint32_t* perm, int32_t* first,
+                       int32_t* count, int32_t* level, int32_t* parent, int32_t* skip,
+                       int32_t* is_leaf, float* centroid, float* radius, double* area,
+                       float* eps, float* moments, void* stream);
+
+/* Release the tree and its device memory (synchronizes the device).  NULL is a no-op. */
+void dipole_tree_destroy(dipole_tree* tree);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* dipole_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all trees).  Host counter, no device work; for accounting. */
+uint64_t dipole_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIPOLE_H */

@@ -1,0 +1,258 @@
+// C ABI entry points (include/dipole.h): argument checks, error reporting and
+// the tree object's lifetime.  All compute runs in the kernels of
+// tree_build.cu, refit.cu, traverse.cu and sort.cu.
+#include <atomic>
+#include <cstdio>
+#include <string>
+
+#include "../../include/dipole.h"
+#include "kernels.cuh"
+#include "tree.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Stream-ordered allocations return to the pool on free; keep the pool's
+// memory instead of releasing it at every synchronization.
+void configure_pool_once() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = true;
+}
+
+void free_tree_memory(dipole_tree* t) {
+    void* bufs[] = {t->pts,    t->code,    t->perm,   t->leaf_of, t->nodes,  t->first,
+                    t->count,  t->level,   t->parent, t->skip,    t->is_leaf, t->nchild,
+                    t->big_idx, t->agg64,  t->eps_node, t->bbox,  t->status, t->mu,
+                    t->S,      t->S64,     t->dS,     t->dmu,     t->arrive};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+int status_to_code(int st) {
+    if (st & dip::kStatusTraversal) return DIPOLE_ETRAVERSAL;
+    if (st & dip::kStatusNonFinite) return DIPOLE_ENONFINITE;
+    return DIPOLE_OK;
+}
+}  // namespace
+
+void dip::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int dip_fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int dip_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
+             cudaGetErrorString(e), what, file, line);
+    g_last_error = buf;
+    return e == cudaErrorMemoryAllocation ? DIPOLE_ENOMEM : DIPOLE_ECUDA;
+}
+
+extern "C" {
+
+const char* dipole_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t dipole_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int dipole_build_tree(const float* points, const float* normals, const float* areas,
+                      const float* radii, int64_t n, const dipole_build_params* params,
+                      void* stream, dipole_tree** out) {
+    if (!out) return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: out is NULL");
+    *out = nullptr;
+    if (!points || !normals || !areas)
+        return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: points, normals and areas are required");
+    if (n < 1) return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: n must be >= 1");
+    if (n > (int64_t)INT32_MAX / 2)
+        return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: n must be < 2^30");
+    int leaf_size = 8, max_depth = 10;
+    if (params) {
+        leaf_size = params->leaf_size;
+        max_depth = params->max_depth;
+    }
+    if (leaf_size < 1 || leaf_size > 64)
+        return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: leaf_size must be in [1, 64]");
+    if (max_depth < 0 || max_depth > 10)
+        return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: max_depth must be in [0, 10]");
+    configure_pool_once();
+    dipole_tree* t = new (std::nothrow) dipole_tree();
+    if (!t) return dip_fail(DIPOLE_ENOMEM, "dipole_build_tree: out of host memory");
+    cudaGetDevice(&t->device);
+    t->n = n;
+    t->leaf_size = leaf_size;
+    t->max_depth = max_depth;
+    int rc = dip::build_tree(t, points, normals, areas, radii, as_stream(stream));
+    if (rc != 0) {
+        cudaStreamSynchronize(as_stream(stream));
+        free_tree_memory(t);
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return DIPOLE_OK;
+}
+
+int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,
+                 void* stream) {
+    if (!tree || !attrs) return dip_fail(DIPOLE_EINVAL, "dipole_refit: tree and attrs are required");
+    if (channels < 1 || channels > dip::kMaxChannels)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit: channels must be in [1, 64]");
+    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit: dtype must be DIPOLE_F32 or DIPOLE_BF16");
+    return dip::refit(tree, attrs, channels, dtype, as_stream(stream));
+}
+
+int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                   float* out, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward: call dipole_refit first");
+    if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_forward: q must be >= 0");
+    if (q > 0 && (!queries || !out))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward: queries and out are required");
+    if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_forward: q must be < 2^31");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr,
+                      as_stream(stream));
+}
+
+int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                   const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint: call dipole_refit first");
+    if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: q must be >= 0");
+    if (!grad_attrs) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: grad_attrs is required");
+    if (q > 0 && (!queries || !grad_out))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: queries and grad_out are required");
+    if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: q must be < 2^31");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: accumulate must be 0 or 1");
+    return dip::query(tree, 1, queries, q, beta, nullptr, grad_out, grad_attrs, accumulate,
+                      nullptr, as_stream(stream));
+}
+
+int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        int32_t* counts, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: tree is NULL");
+    if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: q must be >= 0");
+    if (q > 0 && (!queries || !counts))
+        return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: queries and counts are required");
+    if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: q must be < 2^31");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    return dip::query(tree, 2, queries, q, beta, nullptr, nullptr, nullptr, 0, counts,
+                      as_stream(stream));
+}
+
+int dipole_sync_status(dipole_tree* tree, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_sync_status: tree is NULL");
+    int st = 0;
+    DIP_CUDA_TRY(cudaMemcpyAsync(&st, tree->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 as_stream(stream)));
+    DIP_CUDA_TRY(cudaMemsetAsync(tree->status, 0, sizeof(int), as_stream(stream)));
+    DIP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    DIP_CUDA_TRY(cudaGetLastError());
+    int code = status_to_code(st);
+    if (code == DIPOLE_ETRAVERSAL)
+        return dip_fail(code, "a traversal exceeded its step bound (corrupt tree)");
+    if (code == DIPOLE_ENONFINITE) return dip_fail(code, "a non-finite query point was seen");
+    return DIPOLE_OK;
+}
+
+int dipole_tree_info_get(const dipole_tree* tree, dipole_tree_info* info) {
+    if (!tree || !info) return dip_fail(DIPOLE_EINVAL, "dipole_tree_info_get: NULL argument");
+    info->n_points = tree->n;
+    info->n_nodes = tree->nn;
+    info->channels = tree->C;
+    info->dtype = tree->dtype;
+    info->leaf_size = tree->leaf_size;
+    info->max_depth = tree->max_depth;
+    for (int a = 0; a < 3; ++a) info->bbox_lo[a] = tree->bbox_host[a];
+    info->bbox_ext = tree->bbox_host[3];
+    return DIPOLE_OK;
+}
+
+int dipole_tree_export(const dipole_tree* tree, uint32_t* codes, uint32_t* perm, int32_t* first,
+                       int32_t* count, int32_t* level, int32_t* parent, int32_t* skip,
+                       int32_t* is_leaf, float* centroid, float* radius, double* area,
+                       float* eps, float* moments, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_tree_export: tree is NULL");
+    if (moments && tree->C == 0)
+        return dip_fail(DIPOLE_ESTATE, "dipole_tree_export: moments need a refit first");
+    cudaStream_t s = as_stream(stream);
+    const size_t n = (size_t)tree->n, nn = (size_t)tree->nn;
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    };
+    DIP_CUDA_TRY(cp(codes, tree->code, n * 4));
+    DIP_CUDA_TRY(cp(perm, tree->perm, n * 4));
+    DIP_CUDA_TRY(cp(first, tree->first, nn * 4));
+    DIP_CUDA_TRY(cp(count, tree->count, nn * 4));
+    DIP_CUDA_TRY(cp(level, tree->level, nn * 4));
+    DIP_CUDA_TRY(cp(parent, tree->parent, nn * 4));
+    DIP_CUDA_TRY(cp(skip, tree->skip, nn * 4));
+    DIP_CUDA_TRY(cp(is_leaf, tree->is_leaf, nn * 4));
+    DIP_CUDA_TRY(cp(eps, tree->eps_node, nn * 4));
+    if (centroid || radius || area) {
+        dip::NodeRec* hn = new dip::NodeRec[nn];
+        double* agg = new double[nn * 5];
+        cudaError_t e1 = cudaMemcpyAsync(hn, tree->nodes, nn * sizeof(dip::NodeRec),
+                                         cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaMemcpyAsync(agg, tree->agg64, nn * 5 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s);
+        cudaError_t e3 = cudaStreamSynchronize(s);
+        if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) {
+            for (size_t t = 0; t < nn; ++t) {
+                if (centroid) {
+                    centroid[3 * t] = hn[t].geo.x;
+                    centroid[3 * t + 1] = hn[t].geo.y;
+                    centroid[3 * t + 2] = hn[t].geo.z;
+                }
+                if (radius) radius[t] = hn[t].geo.w;
+                if (area) area[t] = agg[5 * t];
+            }
+        }
+        delete[] hn;
+        delete[] agg;
+        DIP_CUDA_TRY(e1);
+        DIP_CUDA_TRY(e2);
+        DIP_CUDA_TRY(e3);
+    }
+    if (moments) {
+        const int C = tree->C, SR = dip::srow(tree->Cp);
+        float* hs = new float[nn * SR];
+        cudaError_t e1 = cudaMemcpyAsync(hs, tree->S, nn * SR * sizeof(float),
+                                         cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e1 == cudaSuccess && e2 == cudaSuccess)
+            for (size_t t = 0; t < nn; ++t)
+                for (int j = 0; j < 3 * C; ++j) moments[t * 3 * C + j] = hs[t * SR + j];
+        delete[] hs;
+        DIP_CUDA_TRY(e1);
+        DIP_CUDA_TRY(e2);
+    }
+    DIP_CUDA_TRY(cudaStreamSynchronize(s));
+    return DIPOLE_OK;
+}
+
+void dipole_tree_destroy(dipole_tree* tree) {
+    if (!tree) return;
+    cudaDeviceSynchronize();
+    free_tree_memory(tree);
+    delete tree;
+}
+
+}  // extern "C"

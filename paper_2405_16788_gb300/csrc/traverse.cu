@@ -1,0 +1,331 @@
+// Barnes-Hut primal and adjoint queries (Alg. 1; Sec. 5.1, eq. farfield;
+// Sec. 5.2 and App. C, eq. farfield_gradient).
+//
+// Persistent, warp-cooperative, stackless traversal.  Queries are sorted by
+// Morton code, so the 32 queries of a warp are neighbours.  The tree is in
+// depth-first preorder with skip indices: a query at node t moves to skip[t]
+// when t is far or a leaf, else to t+1 (its first child).  Every lane keeps
+// its own next node; the warp visits the smallest of them, so all lanes that
+// need a node read it in the same instruction (one 32-byte broadcast from L2
+// instead of up to 32 scattered reads), and lanes whose next node lies
+// further on wait.  Each lane therefore takes exactly the decisions of its
+// own depth-first traversal (Alg. 1), in the same order.
+//
+// The adjoint (stage 1) recomputes the traversal rather than storing
+// interaction lists.  The lanes taking a far node are all at that node in the
+// same step, so their contributions to dS_t are summed inside the warp before
+// one set of atomics; the same holds for the points of an opened leaf.
+#include "kernels.cuh"
+#include "tree.cuh"
+
+namespace dip {
+namespace {
+
+constexpr int kQThreads = 256;
+enum { kForward = 0, kAdjoint = 1, kCount = 2 };
+
+struct QueryArgs {
+    const NodeRec* nodes;
+    const PointRec* pts;
+    unsigned nn;
+    int* status;
+    const float* q;
+    int64_t nq;
+    const uint32_t* qperm;
+    float beta;
+    int C;
+    const void* mu;
+    const float* S;
+    float* out;
+    const float* g;
+    float* dS;
+    float* dmu;
+    int32_t* counts;
+    unsigned long long* work;
+};
+
+template <typename AT>
+__device__ __forceinline__ void load_row(const AT* p, float* v, int n);
+
+template <>
+__device__ __forceinline__ void load_row<float>(const float* p, float* v, int n) {
+    if (n == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if (n == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_row<__nv_bfloat16>(const __nv_bfloat16* p, float* v, int n) {
+    if (n == 4) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+        v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
+        v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
+    } else if (n == 2) {
+        const unsigned a = __ldg(reinterpret_cast<const unsigned*>(p));
+        v[0] = __uint_as_float(a << 16); v[1] = __uint_as_float(a & 0xffff0000u);
+    } else {
+        v[0] = __bfloat162float(p[0]);
+    }
+}
+
+template <int CP, typename AT, int MODE>
+__global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
+    constexpr int SR = srow(CP);
+    constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const NodeRec* __restrict__ nodes = a.nodes;
+    const PointRec* __restrict__ pts = a.pts;
+    const unsigned nn = a.nn;
+
+    for (;;) {
+        unsigned long long pk = 0;
+        if (lane == 0) pk = atomicAdd(a.work, 1ull);
+        pk = __shfl_sync(FULL, pk, 0);
+        const int64_t base = (int64_t)pk * 32;
+        if (base >= a.nq) break;
+        const int64_t qi = base + lane;
+        const bool valid = qi < a.nq;
+        const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
+
+        float acc[MODE == kForward ? CP : 1], cmp[MODE == kForward ? CP : 1];
+        float g[MODE == kAdjoint ? CP : 1];
+        if (MODE == kForward) {
+#pragma unroll
+            for (int c = 0; c < CP; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
+        }
+        if (MODE == kAdjoint) {
+#pragma unroll
+            for (int c = 0; c < CP; ++c) g[c] = (valid && c < a.C) ? a.g[qo * a.C + c] * kInv4Pi : 0.f;
+        }
+        int n_tested = 0, n_far = 0, n_pts = 0;
+
+        unsigned next = valid ? 0u : nn;
+        unsigned steps = 0;
+        for (;;) {
+            const unsigned n = __reduce_min_sync(FULL, next);
+            if (n >= nn) break;
+            if (++steps > nn) {  // a well-formed tree needs at most nn steps
+                if (lane == 0) atomicOr(a.status, kStatusTraversal);
+                break;
+            }
+            const float4 geo = __ldg(&nodes[n].geo);
+            const int4 meta = __ldg(&nodes[n].meta);
+            const bool act = next == n;
+            // far test of Alg. 1 in a fixed float operation order
+            const float dx = __fsub_rn(x0, geo.x);
+            const float dy = __fsub_rn(x1, geo.y);
+            const float dz = __fsub_rn(x2, geo.z);
+            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            const float R = __fmul_rn(a.beta, geo.w);
+            const bool far = act && (d2 > __fmul_rn(R, R));
+            const bool leaf = meta.z > 0;
+            const bool open_leaf = act && !far && leaf;
+            if (act) next = (far || leaf) ? (unsigned)meta.x : n + 1u;
+
+            if (MODE == kCount) {
+                if (act) {
+                    ++n_tested;
+                    if (far) ++n_far;
+                    else if (leaf) n_pts += meta.z;
+                }
+                continue;
+            }
+
+            if (__any_sync(FULL, far)) {
+                // far field, eq. farfield: rho(d/eps~) S.(p~ - x) / d^3 (1/4pi applied at the end)
+                float k = 0.f;
+                if (far) k = rho_over_d3(d2, __int_as_float(meta.w));
+                const float vx = -k * dx, vy = -k * dy, vz = -k * dz;
+                if (MODE == kForward) {
+                    const float* Sr = a.S + (size_t)n * SR;
+#pragma unroll
+                    for (int c0 = 0; c0 < CP; c0 += CH) {
+                        float s[3 * CH + 3];
+#pragma unroll
+                        for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
+                            const float4 q4 = __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
+                            s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
+                        }
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
+                            if (far) kahan_add(acc[c0 + c], cmp[c0 + c], term);
+                        }
+                    }
+                } else if (MODE == kAdjoint) {
+                    // eq. farfield_gradient: dS_t^c += rho (p~ - x)/d^3 g^c
+                    float* dst = a.dS + (size_t)n * SR;
+#pragma unroll
+                    for (int c0 = 0; c0 < CP; c0 += CH) {
+                        float v[3 * CH];
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            v[3 * c] = vx * g[c0 + c];
+                            v[3 * c + 1] = vy * g[c0 + c];
+                            v[3 * c + 2] = vz * g[c0 + c];
+                        }
+                        warp_reduce_add<3 * CH>(v, dst + 3 * c0, lane);
+                    }
+                }
+            }
+
+            if (__any_sync(FULL, open_leaf)) {
+                // opened leaf: exact sum over its points (eq. dipole_sum)
+                const int f = meta.y, cnt = meta.z;
+                for (int j = 0; j < cnt; ++j) {
+                    const PointRec pr = pts[f + j];
+                    float k = 0.f;
+                    if (open_leaf) {
+                        const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
+                        const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        if (r2 > 0.f)
+                            k = rho_over_d3(r2, pr.geo.w) *
+                                fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
+                    }
+                    if (MODE == kForward) {
+                        const AT* mrow = reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * CP;
+#pragma unroll
+                        for (int c0 = 0; c0 < CP; c0 += CH) {
+                            float m[CH];
+                            load_row<AT>(mrow + c0, m, CH);
+#pragma unroll
+                            for (int c = 0; c < CH; ++c)
+                                if (open_leaf) kahan_add(acc[c0 + c], cmp[c0 + c], k * m[c]);
+                        }
+                    } else if (MODE == kAdjoint) {
+                        float* dst = a.dmu + (size_t)(f + j) * CP;
+#pragma unroll
+                        for (int c0 = 0; c0 < CP; c0 += CH) {
+                            float v[CH];
+#pragma unroll
+                            for (int c = 0; c < CH; ++c) v[c] = k * g[c0 + c];
+                            warp_reduce_add<CH>(v, dst + c0, lane);
+                        }
+                    }
+                }
+            }
+        }
+
+        if (valid) {
+            if (MODE == kForward) {
+#pragma unroll
+                for (int c = 0; c < CP; ++c)
+                    if (c < a.C) a.out[qo * a.C + c] = __fsub_rn(acc[c], cmp[c]) * kInv4Pi;
+            } else if (MODE == kCount) {
+                a.counts[3 * qo] = n_tested;
+                a.counts[3 * qo + 1] = n_far;
+                a.counts[3 * qo + 2] = n_pts;
+            }
+        }
+    }
+}
+
+template <int CP, typename AT, int MODE>
+void launch_query(const QueryArgs& a, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<CP, AT, MODE>, kQThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t need = (a.nq + 31) / 32;                       // warp packets
+    int64_t blocks = (need + (kQThreads / 32) - 1) / (kQThreads / 32);
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    note_launch(); k_query<CP, AT, MODE><<<(unsigned)(blocks < cap ? blocks : cap), kQThreads, 0, s>>>(a);
+}
+
+template <int MODE>
+int dispatch(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
+    if constexpr (MODE == kCount) {
+        launch_query<1, float, kCount>(a, s);
+        return 0;
+    } else {
+#define DIP_Q_CASE(K)                                                                    \
+    case K:                                                                              \
+        if constexpr (MODE == kAdjoint) launch_query<K, float, MODE>(a, s);              \
+        else if (t->dtype == 0) launch_query<K, float, MODE>(a, s);                      \
+        else launch_query<K, __nv_bfloat16, MODE>(a, s);                                 \
+        break;
+    switch (t->Cp) {
+        DIP_Q_CASE(1)
+        DIP_Q_CASE(2)
+        DIP_Q_CASE(4)
+        DIP_Q_CASE(8)
+        DIP_Q_CASE(16)
+        DIP_Q_CASE(32)
+        DIP_Q_CASE(64)
+        default:
+            return dip_fail(-1, "unsupported channel count");
+    }
+#undef DIP_Q_CASE
+    return 0;
+    }
+}
+
+}  // namespace
+
+int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta, float* out,
+          const float* g, float* grad, int accumulate, int32_t* counts, cudaStream_t s) {
+    const int SR = srow(t->Cp > 0 ? t->Cp : 1);
+    // Morton order of the queries: codes in the tree's cube, sorted with their indices.
+    uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
+    unsigned long long* work = nullptr;
+    DIP_CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(unsigned long long), s));
+    if (q > 0) {
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&codes, sizeof(uint32_t) * q, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ktmp, sizeof(uint32_t) * q, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
+        query_codes(queries, q, t->bbox, codes, idx, t->status, s);
+        radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, 30, s);
+    }
+    DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    if (mode == kAdjoint) {
+        DIP_CUDA_TRY(cudaMemsetAsync(t->dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(t->dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
+    }
+    int rc = 0;
+    if (q > 0) {
+        QueryArgs a;
+        a.nodes = t->nodes;
+        a.pts = t->pts;
+        a.nn = (unsigned)t->nn;
+        a.status = t->status;
+        a.q = queries;
+        a.nq = q;
+        a.qperm = idx;
+        a.beta = beta;
+        a.C = t->C;
+        a.mu = t->mu;
+        a.S = t->S;
+        a.out = out;
+        a.g = g;
+        a.dS = t->dS;
+        a.dmu = t->dmu;
+        a.counts = counts;
+        a.work = work;
+        if (mode == kForward) rc = dispatch<kForward>(t, a, s);
+        else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
+        else rc = dispatch<kCount>(t, a, s);
+    }
+    if (rc == 0 && mode == kAdjoint) rc = stage2(t, grad, accumulate, s);
+    cudaFreeAsync(work, s);
+    if (codes) {
+        cudaFreeAsync(codes, s); cudaFreeAsync(idx, s); cudaFreeAsync(ktmp, s);
+        cudaFreeAsync(vtmp, s); cudaFreeAsync(hist, s);
+    }
+    if (rc) return rc;
+    DIP_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace dip

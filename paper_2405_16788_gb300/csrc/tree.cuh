@@ -1,0 +1,84 @@
+// The tree object behind the opaque dipole_tree handle, and the host launchers
+// of the build, refit and query kernels.
+#pragma once
+
+#include "common.cuh"
+
+struct dipole_tree {
+    int device = 0;
+    int64_t n = 0;
+    int64_t nn = 0;
+    int leaf_size = 8;
+    int max_depth = 10;
+
+    // points, Morton order
+    dip::PointRec* pts = nullptr;
+    uint32_t* code = nullptr;
+    uint32_t* perm = nullptr;
+    int32_t* leaf_of = nullptr;  // [n] leaf node holding each point
+
+    // nodes, depth-first preorder
+    dip::NodeRec* nodes = nullptr;
+    int32_t* first = nullptr;
+    int32_t* count = nullptr;
+    int32_t* level = nullptr;
+    int32_t* parent = nullptr;
+    int32_t* skip = nullptr;
+    int32_t* is_leaf = nullptr;
+    int32_t* nchild = nullptr;
+    int32_t* big_idx = nullptr;  // index into S64 for nodes with >= kBigNode points, else -1
+    int64_t nbig = 0;
+    double* agg64 = nullptr;     // [nn, 5] sum A, sum A p (3), sum A eps
+    float* eps_node = nullptr;   // [nn]
+    float* bbox = nullptr;       // device: lo.xyz, ext, 1024/ext
+    float bbox_host[5] = {0, 0, 0, 1, 1024};
+    int* status = nullptr;       // device status word
+
+    // attributes (set by refit)
+    int C = 0;
+    int Cp = 0;
+    int dtype = 0;
+    void* mu = nullptr;          // [n, Cp] float or bf16, Morton order
+    float* S = nullptr;          // [nn, 3 Cp]
+    double* S64 = nullptr;       // [nbig, 3 Cp]
+    float* dS = nullptr;         // [nn, 3 Cp] adjoint node accumulators
+    float* dmu = nullptr;        // [n, Cp] adjoint opened-leaf accumulators
+    uint32_t* arrive = nullptr;  // [nn] bottom-up arrival counters
+    int attr_Cp_alloc = 0;
+    int attr_dtype_alloc = -1;
+
+    dip::TreeView view() const {
+        dip::TreeView v;
+        v.n = n;
+        v.nn = nn;
+        v.nodes = nodes;
+        v.pts = pts;
+        v.perm = perm;
+        v.parent = parent;
+        v.first = first;
+        v.count = count;
+        v.is_leaf = is_leaf;
+        v.bbox = bbox;
+        v.status = status;
+        return v;
+    }
+};
+
+namespace dip {
+
+// Build everything but the attribute state.  Returns a dipole_status.
+int build_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
+               const float* radii, cudaStream_t s);
+
+// Tree update of node moments (eq. farfield_dipole_features).
+int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
+
+// Queries.  mode: 0 forward (out), 1 adjoint (g -> grad), 2 counts.
+int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta,
+          float* out, const float* g, float* grad, int accumulate, int32_t* counts,
+          cudaStream_t s);
+
+// Stage 2 of the adjoint (eq. farfield_features_gradient) into grad [n, C].
+int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s);
+
+}  // namespace dip

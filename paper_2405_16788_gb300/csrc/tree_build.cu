@@ -1,0 +1,470 @@
+// Octree construction and node geometry (Sec. 5.1, eq. farfield_dipole;
+// Sec. 5.3: the tree is built once because positions are not optimized).
+//
+// Tree definition (the paper says only "octree"): 30-bit Morton codes over
+// the bounding cube, points sorted stably by code; a node at level l is a
+// maximal run of sorted codes sharing their top 3l bits; a run of at most
+// leaf_size points, or at level max_depth, is a leaf; a run whose points all
+// share the next digit is the same node as its only child.  Nodes are stored
+// in depth-first preorder with skip[t] = the index just past t's subtree.
+//
+// GPU construction: preorder is the order of (first point, level), so every
+// sorted point i enumerates the runs that start at i level by level (their
+// ends found by galloping search over the sorted codes), keeps the ones the
+// definition keeps, and an exclusive scan of the per-point node counts gives
+// every node its preorder index.  No recursion, no per-level launches.
+#include "tree.cuh"
+
+#include <float.h>
+
+namespace dip {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Input validation and per-block bounding boxes.
+__global__ void __launch_bounds__(kThreads) k_bbox_partial(const float* __restrict__ p,
+                                                           const float* __restrict__ nrm,
+                                                           const float* __restrict__ A,
+                                                           const float* __restrict__ eps,
+                                                           int64_t n, float* partial, int* status) {
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float x = p[3 * i], y = p[3 * i + 1], z = p[3 * i + 2];
+        float a = A[i];
+        float e = eps ? eps[i] : 0.0f;
+        bool fin = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(nrm[3 * i]) &&
+                   isfinite(nrm[3 * i + 1]) && isfinite(nrm[3 * i + 2]) && isfinite(a) &&
+                   isfinite(e);
+        if (!fin) bad |= kStatusNonFinite;
+        if (!(a > 0.0f)) bad |= kStatusBadArea;
+        if (e < 0.0f) bad |= kStatusBadRadius;
+        lo[0] = fminf(lo[0], x); hi[0] = fmaxf(hi[0], x);
+        lo[1] = fminf(lo[1], y); hi[1] = fmaxf(hi[1], y);
+        lo[2] = fminf(lo[2], z); hi[2] = fmaxf(hi[2], z);
+    }
+    if (bad) atomicOr(status, bad);
+    __shared__ float sh[6][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float l = warp_min(lo[a]), h = warp_max(hi[a]);
+        if (lane == 0) { sh[a][warp] = l; sh[3 + a][warp] = h; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float v = sh[threadIdx.x][0];
+        for (int w = 1; w < kThreads / 32; ++w)
+            v = threadIdx.x < 3 ? fminf(v, sh[threadIdx.x][w]) : fmaxf(v, sh[threadIdx.x][w]);
+        partial[blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+// Bounding cube: lo = per-axis minimum; ext = largest per-axis extent (float
+// subtraction), 1 if 0; scale = 1024 / ext (correctly rounded division).
+__global__ void k_bbox_final(const float* partial, int nb, float* bbox) {
+    if (threadIdx.x != 0) return;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = partial[a]; hi[a] = partial[3 + a]; }
+    for (int b = 1; b < nb; ++b)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], partial[b * 6 + a]);
+            hi[a] = fmaxf(hi[a], partial[b * 6 + 3 + a]);
+        }
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float e = __fsub_rn(hi[a], lo[a]);
+        if (e > ext) ext = e;
+    }
+    if (!(ext > 0.0f)) ext = 1.0f;
+    bbox[0] = lo[0]; bbox[1] = lo[1]; bbox[2] = lo[2];
+    bbox[3] = ext;
+    bbox[4] = __fdiv_rn(1024.0f, ext);
+}
+
+__global__ void k_pack(const uint32_t* __restrict__ perm, const float* __restrict__ p,
+                       const float* __restrict__ nrm, const float* __restrict__ A,
+                       const float* __restrict__ eps, int64_t n, PointRec* __restrict__ pts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = perm[i];
+        float a = A[m];
+        float e = eps ? eps[m] : 0.0f;
+        PointRec r;
+        r.geo = make_float4(p[3 * m], p[3 * m + 1], p[3 * m + 2], __frcp_rn(e));
+        r.w = make_float4(__fmul_rn(a, nrm[3 * m]), __fmul_rn(a, nrm[3 * m + 1]),
+                          __fmul_rn(a, nrm[3 * m + 2]), a);
+        pts[i] = r;
+    }
+}
+
+// ------------------------------------------------------------- topology
+__device__ __forceinline__ int lcp_digits(uint32_t a, uint32_t b) {
+    uint32_t x = a ^ b;
+    return x ? (__clz(x) - 2) / 3 : kMaxLevel;
+}
+
+__device__ __forceinline__ bool same_run(uint32_t a, uint32_t b, int l) {
+    return l == 0 || ((a ^ b) >> (30 - 3 * l)) == 0u;
+}
+
+// First index >= lb whose code leaves the level-l run of code ci (every index
+// in (i, lb) is known to be inside it).  Galloping, then bisection.
+__device__ int64_t run_end(const uint32_t* __restrict__ c, int64_t n, uint32_t ci, int l,
+                           int64_t lb) {
+    if (lb >= n || !same_run(ci, c[lb], l)) return lb;
+    int64_t lo = lb, hi, step = 1;
+    for (;;) {
+        hi = lo + step;
+        if (hi >= n) { hi = n; break; }
+        if (!same_run(ci, c[hi], l)) break;
+        lo = hi;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        if (same_run(ci, c[mid], l)) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+// Runs starting at sorted point i that are nodes.  Bit l of the returned mask:
+// the level-l run starting at i is a node; bit l of *imask: it is internal.
+// e[l] receives the end of the level-l run holding i, for the levels visited.
+__device__ uint32_t analyze_point(const uint32_t* __restrict__ c, int64_t n, int64_t i,
+                                  int leaf_size, int max_depth, int64_t* e, uint32_t* imask) {
+    const uint32_t ci = c[i];
+    const int s = (i == 0) ? 0 : lcp_digits(c[i - 1], ci) + 1;
+    *imask = 0;
+    if (s > max_depth) return 0;
+    const int lmin = s > 0 ? s - 1 : 0;
+    int64_t lb = i + 1;
+    for (int l = max_depth; l >= lmin; --l) {
+        lb = run_end(c, n, ci, l, lb);
+        e[l] = lb;
+    }
+    uint32_t mask = 0;
+    for (int l = s; l <= max_depth; ++l) {
+        const int64_t cnt = e[l] - i;
+        if (l < max_depth && cnt > leaf_size && e[l + 1] < e[l]) {  // branches at digit l
+            mask |= 1u << l;
+            *imask |= 1u << l;
+            continue;
+        }
+        if (!(cnt <= leaf_size || l == max_depth)) continue;  // single child: collapsed
+        bool parent_open = true;                               // root
+        if (l > 0) {
+            // the level-(l-1) run holding i has more than leaf_size points?
+            const int64_t pe = e[l - 1];
+            if (pe - i <= leaf_size) {
+                const int64_t k = pe - leaf_size - 1;
+                parent_open = (k >= 0) && same_run(c[k], ci, l - 1);
+            }
+        }
+        if (parent_open) mask |= 1u << l;
+    }
+    return mask;
+}
+
+__global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf_size,
+                             int max_depth, uint32_t* __restrict__ cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e[kMaxLevel + 2];
+        uint32_t im;
+        cnt[i] = __popc(analyze_point(c, n, i, leaf_size, max_depth, e, &im));
+    }
+}
+
+__global__ void k_topo_emit(const uint32_t* __restrict__ c, int64_t n, int leaf_size,
+                            int max_depth, const uint32_t* __restrict__ off,
+                            int32_t* __restrict__ first, int32_t* __restrict__ count,
+                            int32_t* __restrict__ level, int32_t* __restrict__ skip,
+                            int32_t* __restrict__ is_leaf, int32_t* __restrict__ leaf_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e[kMaxLevel + 2];
+        uint32_t im;
+        uint32_t mask = analyze_point(c, n, i, leaf_size, max_depth, e, &im);
+        uint32_t t = off[i];
+        for (int l = 0; l <= max_depth; ++l) {
+            if (!(mask & (1u << l))) continue;
+            first[t] = (int32_t)i;
+            count[t] = (int32_t)(e[l] - i);
+            level[t] = l;
+            skip[t] = (int32_t)off[e[l]];
+            const bool leaf = !(im & (1u << l));
+            is_leaf[t] = leaf ? 1 : 0;
+            if (leaf)
+                for (int64_t m = i; m < e[l]; ++m) leaf_of[m] = (int32_t)t;
+            ++t;
+        }
+    }
+}
+
+// Children of internal node t: t+1, skip[t+1], ... below skip[t].
+__global__ void k_children(int64_t nn, const int32_t* __restrict__ skip,
+                           const int32_t* __restrict__ is_leaf, int32_t* __restrict__ parent,
+                           int32_t* __restrict__ nchild, int* status) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (is_leaf[t]) { nchild[t] = 0; continue; }
+        int k = 0;
+        int32_t end = skip[t];
+        for (int32_t ch = (int32_t)t + 1; ch < end;) {
+            parent[ch] = (int32_t)t;
+            ++k;
+            int32_t nx = skip[ch];
+            if (nx <= ch || k > 8) { atomicOr(status, kStatusTraversal); break; }
+            ch = nx;
+        }
+        nchild[t] = k;
+    }
+}
+
+// Node sums in double: point by point inside a leaf, child by child inside an
+// internal node, both in Morton order, so that the float centroid is the
+// same on any machine.  Each leaf thread climbs while it is the last child to
+// finish (arrival counters).
+__device__ __forceinline__ void finalize_geom(int64_t t, const double* s, float4* cen4,
+                                              float* eps_node) {
+    double sa = s[0];
+    double cx = __ddiv_rn(s[1], sa), cy = __ddiv_rn(s[2], sa), cz = __ddiv_rn(s[3], sa);
+    cen4[t] = make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz),
+                          0.0f);
+    eps_node[t] = __double2float_rn(__ddiv_rn(s[4], sa));
+}
+
+__global__ void k_geom(int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
+                       const float* __restrict__ radii, const int32_t* __restrict__ first,
+                       const int32_t* __restrict__ count, const int32_t* __restrict__ is_leaf,
+                       const int32_t* __restrict__ parent, const int32_t* __restrict__ nchild,
+                       const int32_t* __restrict__ skip, unsigned int* arrive, double* agg,
+                       float4* cen4, float* eps_node) {
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < nn;
+         t0 += (int64_t)gridDim.x * blockDim.x) {
+        if (!is_leaf[t0]) continue;
+        double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        const int64_t f = first[t0], k = count[t0];
+        for (int64_t m = f; m < f + k; ++m) {
+            const float4 g = pts[m].geo;
+            const double a = (double)pts[m].w.w;
+            const double e = radii ? (double)radii[perm[m]] : 0.0;
+            s[0] = __dadd_rn(s[0], a);
+            s[1] = __dadd_rn(s[1], __dmul_rn(a, (double)g.x));  // products are exact
+            s[2] = __dadd_rn(s[2], __dmul_rn(a, (double)g.y));
+            s[3] = __dadd_rn(s[3], __dmul_rn(a, (double)g.z));
+            s[4] = __dadd_rn(s[4], __dmul_rn(a, e));
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) agg[t0 * 5 + j] = s[j];
+        finalize_geom(t0, s, cen4, eps_node);
+        __threadfence();
+        int64_t t = t0;
+        for (;;) {
+            const int32_t p = parent[t];
+            if (p < 0) break;
+            if (atomicAdd(&arrive[p], 1u) != (unsigned)(nchild[p] - 1)) break;
+            __threadfence();
+            double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int32_t ch = p + 1; ch < skip[p]; ch = skip[ch]) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], __ldcg(&agg[(int64_t)ch * 5 + j]));
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
+            finalize_geom(p, q, cen4, eps_node);
+            __threadfence();
+            t = p;
+        }
+    }
+}
+
+// r~_t = max over the node's points of the float distance to the float
+// centroid (fixed operation order).  One thread per point walks its ancestors;
+// lanes at the same node combine with a warp max before one atomicMax.
+__global__ void k_radius(int64_t n, const PointRec* __restrict__ pts,
+                         const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ parent,
+                         const float4* __restrict__ cen4, unsigned int* __restrict__ rbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        int32_t t = valid ? leaf_of[i] : -1;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (valid) { const float4 g = pts[i].geo; px = g.x; py = g.y; pz = g.z; }
+        while (__any_sync(0xffffffffu, t >= 0)) {
+            unsigned int bits = 0u;
+            if (t >= 0) {
+                const float4 c = cen4[t];
+                const float ex = __fsub_rn(px, c.x), ey = __fsub_rn(py, c.y), ez = __fsub_rn(pz, c.z);
+                const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+                bits = __float_as_uint(__fsqrt_rn(d2));
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)t);
+            const unsigned int m = __reduce_max_sync(peers, bits);
+            if (t >= 0 && lane == __ffs(peers) - 1) atomicMax(&rbits[t], m);
+            if (t >= 0) t = parent[t];
+        }
+    }
+}
+
+__global__ void k_finalize_nodes(int64_t nn, const float4* __restrict__ cen4,
+                                 const unsigned int* __restrict__ rbits,
+                                 const int32_t* __restrict__ skip, const int32_t* __restrict__ first,
+                                 const int32_t* __restrict__ count,
+                                 const int32_t* __restrict__ is_leaf,
+                                 const float* __restrict__ eps_node, NodeRec* __restrict__ nodes,
+                                 int32_t* __restrict__ big_idx, unsigned int* nbig) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float4 c = cen4[t];
+        NodeRec r;
+        r.geo = make_float4(c.x, c.y, c.z, __uint_as_float(rbits[t]));
+        r.meta = make_int4(skip[t], first[t], is_leaf[t] ? count[t] : 0,
+                           __float_as_int(__frcp_rn(eps_node[t])));
+        nodes[t] = r;
+        big_idx[t] = (count[t] >= kBigNode) ? (int32_t)atomicAdd(nbig, 1u) : -1;
+    }
+}
+
+unsigned grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms() * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
+    size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    return cudaMallocAsync((void**)p, bytes, s);
+}
+
+}  // namespace
+
+int build_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
+               const float* radii, cudaStream_t s) {
+    const int64_t n = t->n;
+    // persistent point arrays
+    DIP_CUDA_TRY(dalloc(&t->pts, n, s));
+    DIP_CUDA_TRY(dalloc(&t->code, n, s));
+    DIP_CUDA_TRY(dalloc(&t->perm, n, s));
+    DIP_CUDA_TRY(dalloc(&t->leaf_of, n, s));
+    DIP_CUDA_TRY(dalloc(&t->bbox, 8, s));
+    DIP_CUDA_TRY(dalloc(&t->status, 1, s));
+    DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
+
+    // temporaries
+    uint32_t *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr, *off = nullptr, *scan_tmp = nullptr;
+    float* partial = nullptr;
+    const unsigned nbb = grid_for(n, kThreads);
+    DIP_CUDA_TRY(dalloc(&ktmp, n, s));
+    DIP_CUDA_TRY(dalloc(&vtmp, n, s));
+    DIP_CUDA_TRY(dalloc(&hist, radix_hist_entries(n), s));
+    DIP_CUDA_TRY(dalloc(&off, n + 1, s));
+    DIP_CUDA_TRY(dalloc(&scan_tmp, scan_tmp_entries(n + 1), s));
+    DIP_CUDA_TRY(dalloc(&partial, (int64_t)nbb * 6, s));
+
+    note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
+    note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
+    query_codes(points, n, t->bbox, t->code, t->perm, t->status, s);
+    radix_sort_pairs(t->code, t->perm, ktmp, vtmp, hist, n, 30, s);
+    note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
+                                                      t->pts);
+    note_launch(); k_topo_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size,
+                                                            t->max_depth, off);
+    DIP_CUDA_TRY(cudaMemsetAsync(off + n, 0, sizeof(uint32_t), s));
+    exclusive_scan_u32(off, n + 1, scan_tmp, s);
+    uint32_t nn_host = 0;
+    int status_host = 0;
+    DIP_CUDA_TRY(cudaMemcpyAsync(&nn_host, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(&status_host, t->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->bbox_host, t->bbox, 5 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    DIP_CUDA_TRY(cudaStreamSynchronize(s));
+    DIP_CUDA_TRY(cudaGetLastError());
+
+    auto free_tmp = [&]() {
+        cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s); cudaFreeAsync(hist, s);
+        cudaFreeAsync(off, s); cudaFreeAsync(scan_tmp, s); cudaFreeAsync(partial, s);
+    };
+    if (status_host & kStatusNonFinite) {
+        free_tmp();
+        return dip_fail(-4, "dipole_build_tree: non-finite point, normal, area or radius");
+    }
+    if (status_host & kStatusBadArea) {
+        free_tmp();
+        return dip_fail(-1, "dipole_build_tree: every area weight must be > 0");
+    }
+    if (status_host & kStatusBadRadius) {
+        free_tmp();
+        return dip_fail(-1, "dipole_build_tree: radii must be >= 0");
+    }
+    const int64_t nn = nn_host;
+    t->nn = nn;
+
+    DIP_CUDA_TRY(dalloc(&t->nodes, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->first, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->count, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->level, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->parent, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->skip, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->is_leaf, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->nchild, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->big_idx, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
+    DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
+    float4* cen4 = nullptr;
+    unsigned int *rbits = nullptr, *arrive = nullptr, *nbig = nullptr;
+    DIP_CUDA_TRY(dalloc(&cen4, nn, s));
+    DIP_CUDA_TRY(dalloc(&rbits, nn, s));
+    DIP_CUDA_TRY(dalloc(&arrive, nn, s));
+    DIP_CUDA_TRY(dalloc(&nbig, 1, s));
+
+    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size, t->max_depth,
+                                                           off, t->first, t->count, t->level,
+                                                           t->skip, t->is_leaf, t->leaf_of);
+    DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
+    note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
+                                                           t->nchild, t->status);
+    DIP_CUDA_TRY(cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * nn, s));
+    note_launch(); k_geom<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->pts, t->perm, radii, t->first,
+                                                       t->count, t->is_leaf, t->parent, t->nchild,
+                                                       t->skip, arrive, t->agg64, cen4,
+                                                       t->eps_node);
+    DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
+    note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
+                                                        rbits);
+    DIP_CUDA_TRY(cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s));
+    note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
+                                                                 t->first, t->count, t->is_leaf,
+                                                                 t->eps_node, t->nodes,
+                                                                 t->big_idx, nbig);
+    free_tmp();
+    cudaFreeAsync(cen4, s);
+    cudaFreeAsync(rbits, s);
+    cudaFreeAsync(arrive, s);
+    cudaFreeAsync(nbig, s);
+    DIP_CUDA_TRY(cudaGetLastError());
+    // Nodes of one level are disjoint, so each level has at most n / kBigNode
+    // big nodes: an upper bound that needs no second synchronization.
+    t->nbig = (int64_t)(t->max_depth + 1) * (n / kBigNode + 1);
+    return 0;
+}
+
+}  // namespace dip

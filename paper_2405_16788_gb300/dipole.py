@@ -1,0 +1,323 @@
+"""Python binding of libdipole (include/dipole.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module checks
+tensor devices, dtypes and shapes, passes raw device pointers and the current
+CUDA stream, and turns status codes into exceptions.  There is no CPU path:
+if libdipole.so is missing or cannot be loaded, importing the functions raises.
+
+Method: Barnes-Hut fast summation of regularized dipole sums, forward and
+adjoint (Chen, Miller, Gkioulekas, arXiv 2405.16788, Sec. 5 and Alg. 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdipole.so")
+
+DIPOLE_OK = 0
+DIPOLE_EINVAL = -1
+DIPOLE_ENOMEM = -2
+DIPOLE_ECUDA = -3
+DIPOLE_ENONFINITE = -4
+DIPOLE_ETRAVERSAL = -5
+DIPOLE_ESTATE = -6
+DIPOLE_F32 = 0
+DIPOLE_BF16 = 1
+
+EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
+            "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
+            "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
+            "dipole_kernel_launches"]
+
+
+class DipoleError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _BuildParams(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32)]
+
+
+class _TreeInfo(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("channels", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("bbox_lo", ctypes.c_float * 3), ("bbox_ext", ctypes.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libdipole.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libdipole.so not found at {path}: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        P, I32, I64, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        sig = {
+            "dipole_build_tree": [P, P, P, P, I64, P, P, P],
+            "dipole_refit": [P, P, I32, I32, P],
+            "dipole_forward": [P, P, I64, F, P, P],
+            "dipole_adjoint": [P, P, I64, F, P, P, I32, P],
+            "dipole_query_counts": [P, P, I64, F, P, P],
+            "dipole_sync_status": [P, P],
+            "dipole_tree_info_get": [P, P],
+            "dipole_tree_export": [P] * 15,
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.dipole_tree_destroy.argtypes = [P]
+        lib.dipole_tree_destroy.restype = None
+        lib.dipole_last_error.argtypes = []
+        lib.dipole_last_error.restype = ctypes.c_char_p
+        lib.dipole_kernel_launches.argtypes = []
+        lib.dipole_kernel_launches.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def dipole_last_error() -> str:
+    return load_library().dipole_last_error().decode()
+
+
+def dipole_kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().dipole_kernel_launches())
+
+
+def _check(rc: int):
+    if rc != DIPOLE_OK:
+        raise DipoleError(rc, dipole_last_error())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype=torch.float32, shape=None) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names
+
+def dipole_build_tree(points, normals, areas, radii=None, leaf_size=8, max_depth=10,
+                      stream=None) -> int:
+    """Build the octree and node geometry; returns the opaque tree handle."""
+    lib = load_library()
+    n = int(points.shape[0])
+    pp = _dev(points, "points", shape=(n, 3))
+    pn = _dev(normals, "normals", shape=(n, 3))
+    pa = _dev(areas, "areas", shape=(n,))
+    pr = None if radii is None else _dev(radii, "radii", shape=(n,))
+    params = _BuildParams(int(leaf_size), int(max_depth))
+    h = ctypes.c_void_p()
+    _check(lib.dipole_build_tree(pp, pn, pa, pr, n, ctypes.byref(params), _stream(stream),
+                                 ctypes.byref(h)))
+    return h.value
+
+
+def dipole_refit(tree: int, attrs: torch.Tensor, stream=None):
+    if attrs.dim() == 1:
+        attrs = attrs[:, None]
+    dt = {torch.float32: DIPOLE_F32, torch.bfloat16: DIPOLE_BF16}.get(attrs.dtype)
+    if dt is None:
+        raise TypeError("attrs must be float32 or bfloat16")
+    p = _dev(attrs, "attrs", dtype=None)
+    _check(load_library().dipole_refit(ctypes.c_void_p(tree), p, int(attrs.shape[1]), dt,
+                                       _stream(stream)))
+
+
+def dipole_forward(tree: int, queries: torch.Tensor, beta: float, out: torch.Tensor,
+                   stream=None):
+    q = int(queries.shape[0])
+    _check(load_library().dipole_forward(ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)),
+                                         q, float(beta), _dev(out, "out"), _stream(stream)))
+
+
+def dipole_adjoint(tree: int, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                   grad_attrs: torch.Tensor, accumulate: bool = False, stream=None):
+    q = int(queries.shape[0])
+    _check(load_library().dipole_adjoint(ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)),
+                                         q, float(beta), _dev(grad_out, "grad_out"),
+                                         _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)),
+                                         _stream(stream)))
+
+
+def dipole_query_counts(tree: int, queries: torch.Tensor, beta: float, counts: torch.Tensor,
+                        stream=None):
+    q = int(queries.shape[0])
+    _check(load_library().dipole_query_counts(ctypes.c_void_p(tree),
+                                              _dev(queries, "queries", shape=(q, 3)), q,
+                                              float(beta),
+                                              _dev(counts, "counts", dtype=torch.int32,
+                                                   shape=(q, 3)),
+                                              _stream(stream)))
+
+
+def dipole_sync_status(tree: int, stream=None):
+    _check(load_library().dipole_sync_status(ctypes.c_void_p(tree), _stream(stream)))
+
+
+def dipole_tree_info_get(tree: int) -> dict:
+    info = _TreeInfo()
+    _check(load_library().dipole_tree_info_get(ctypes.c_void_p(tree), ctypes.byref(info)))
+    return dict(n_points=info.n_points, n_nodes=info.n_nodes, channels=info.channels,
+                dtype=info.dtype, leaf_size=info.leaf_size, max_depth=info.max_depth,
+                bbox_lo=list(info.bbox_lo), bbox_ext=info.bbox_ext)
+
+
+def dipole_tree_export(tree: int, moments: bool = False, stream=None) -> dict:
+    info = dipole_tree_info_get(tree)
+    n, nn, C = info["n_points"], info["n_nodes"], info["channels"]
+    o = dict(code=np.zeros(n, np.uint32), perm=np.zeros(n, np.uint32),
+             first=np.zeros(nn, np.int32), count=np.zeros(nn, np.int32),
+             level=np.zeros(nn, np.int32), parent=np.zeros(nn, np.int32),
+             skip=np.zeros(nn, np.int32), is_leaf=np.zeros(nn, np.int32),
+             cen32=np.zeros((nn, 3), np.float32), r32=np.zeros(nn, np.float32),
+             area=np.zeros(nn, np.float64), eps=np.zeros(nn, np.float32))
+    if moments:
+        o["moments"] = np.zeros((nn, 3 * C), np.float32)
+    keys = ["code", "perm", "first", "count", "level", "parent", "skip", "is_leaf", "cen32",
+            "r32", "area", "eps", "moments"]
+    ptrs = [o[k].ctypes.data_as(ctypes.c_void_p) if k in o else None for k in keys]
+    _check(load_library().dipole_tree_export(ctypes.c_void_p(tree), *ptrs, _stream(stream)))
+    return o
+
+
+def dipole_tree_destroy(tree: int):
+    if tree:
+        load_library().dipole_tree_destroy(ctypes.c_void_p(tree))
+
+
+# ---------------------------------------------------------------- objects
+
+class DipoleTree:
+    """Owns a dipole_tree handle.  Inputs are float32 CUDA tensors in the
+    caller's point order; outputs come back in that order."""
+
+    def __init__(self, points, normals, areas, radii=None, leaf_size=8, max_depth=10,
+                 stream=None):
+        self.n = int(points.shape[0])
+        # kernels still read the inputs after the build call returns (stream order)
+        self._inputs = (points, normals, areas, radii)
+        self.handle = dipole_build_tree(points, normals, areas, radii, leaf_size, max_depth,
+                                        stream)
+        self.C = 0
+        self.device = points.device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dipole_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return dipole_tree_info_get(self.handle)
+
+    def refit(self, attrs: torch.Tensor, stream=None):
+        if attrs.dim() == 1:
+            attrs = attrs[:, None]
+        if attrs.shape[0] != self.n:
+            raise ValueError("attrs must have one row per point")
+        attrs = attrs.contiguous()
+        dipole_refit(self.handle, attrs, stream)
+        self.C = int(attrs.shape[1])
+        self._attrs = attrs
+
+    def forward(self, queries: torch.Tensor, beta: float, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        if out is None:
+            out = torch.empty((queries.shape[0], self.C), device=queries.device,
+                              dtype=torch.float32)
+        dipole_forward(self.handle, queries, beta, out, stream)
+        return out
+
+    def adjoint(self, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                grad_attrs: torch.Tensor | None = None, accumulate: bool = False,
+                stream=None) -> torch.Tensor:
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        if grad_attrs is None:
+            grad_attrs = torch.empty((self.n, self.C), device=queries.device, dtype=torch.float32)
+            accumulate = False
+        dipole_adjoint(self.handle, queries, beta, grad_out.contiguous(), grad_attrs, accumulate,
+                       stream)
+        return grad_attrs
+
+    def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
+        counts = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.int32)
+        dipole_query_counts(self.handle, queries, beta, counts, stream)
+        return counts
+
+    def sync_status(self, stream=None):
+        dipole_sync_status(self.handle, stream)
+
+    def export(self, moments: bool = False) -> dict:
+        return dipole_tree_export(self.handle, moments)
+
+
+class DipoleSum(torch.autograd.Function):
+    """D = dipole sum of `attrs` at `queries` (Barnes-Hut, Alg. 1).  Forward runs
+    the tree update then the primal queries; backward runs the two-stage adjoint
+    (Sec. 5.2), recomputing the traversal instead of storing interaction lists."""
+
+    @staticmethod
+    def forward(ctx, attrs, tree: DipoleTree, queries, beta: float):
+        tree.refit(attrs)
+        out = tree.forward(queries, beta)
+        ctx.tree = tree
+        ctx.beta = float(beta)
+        ctx.C = tree.C
+        ctx.attr_dtype = attrs.dtype
+        ctx.attr_shape = attrs.shape
+        ctx.save_for_backward(queries)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (queries,) = ctx.saved_tensors
+        tree = ctx.tree
+        if tree.C != ctx.C:
+            raise DipoleError(DIPOLE_ESTATE, "the tree was refit with another channel count "
+                                             "between forward and backward")
+        g = tree.adjoint(queries, ctx.beta, grad_out.to(torch.float32).contiguous())
+        return g.to(ctx.attr_dtype).reshape(ctx.attr_shape), None, None, None
+
+
+def dipole_sum(attrs: torch.Tensor, tree: DipoleTree, queries: torch.Tensor, beta: float = 2.0):
+    return DipoleSum.apply(attrs, tree, queries, beta)

@@ -25,3 +25,14 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionstart(session):
+    """Build the CUDA library and the oracle once, before any test imports them."""
+    try:
+        from paper_2405_16788_gb300 import _build
+        _build.build()
+    except Exception as e:  # the ABI tests report the failure themselves
+        print(f"libdipole build failed: {e}")
+    import oracle
+    oracle.build()

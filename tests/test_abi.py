@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/dipole.h declares (no GPU needed: no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dipole.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dipole_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2405_16788_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
+                 "dipole_tree_destroy", "dipole_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (dipole_[a-z0-9_]+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_through_binding(lib_path):
+    from paper_2405_16788_gb300 import dipole
+    lib = dipole.load_library()
+    for n in _declared():
+        assert hasattr(lib, n)
+    assert set(dipole.EXPORTED) <= set(_declared())
+    assert isinstance(dipole.dipole_last_error(), str)
+
+
+def test_argument_errors_without_gpu(lib_path):
+    """Host-side validation rejects bad arguments before touching the device."""
+    from paper_2405_16788_gb300 import dipole
+    lib = dipole.load_library()
+    out = ctypes.c_void_p()
+    assert lib.dipole_build_tree(None, None, None, None, 10, None, None, ctypes.byref(out)) == -1
+    assert "required" in dipole.dipole_last_error()
+    assert lib.dipole_forward(None, None, 0, 2.0, None, None) == -1
+    assert lib.dipole_refit(None, None, 4, 0, None) == -1
+    assert lib.dipole_adjoint(None, None, 0, 2.0, None, None, 0, None) == -1
+    lib.dipole_tree_destroy(None)  # a no-op
+
+
+def test_oracle_and_library_share_nothing():
+    """The oracle neither includes the library's headers nor imports its package."""
+    osrc = open(os.path.join(ROOT, "oracle", "dipole_oracle.c")).read()
+    opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert "#include \"" not in osrc
+    assert "paper_2405_16788_gb300" not in re.sub(r'""".*?"""', "", opy, flags=re.S)
+    for f in os.listdir(os.path.join(ROOT, "paper_2405_16788_gb300", "csrc")):
+        assert "oracle" not in open(os.path.join(ROOT, "paper_2405_16788_gb300", "csrc", f)).read()
+    for f in ["dipole.py", "_build.py", "__init__.py"]:
+        txt = open(os.path.join(ROOT, "paper_2405_16788_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt

@@ -1,0 +1,180 @@
+"""GPU primal queries vs the oracle's double-precision Barnes-Hut on the same
+tree: norm-wise error <= 1e-4 per channel, traversal decisions (per-query
+counts of tested nodes, far nodes and leaf points) bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_16788_gb300 import synthetic as syn
+from _helpers import bf16_round, gpu_tree, normwise, oracle_tree, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def _run(cloud, mu, queries, beta=2.0, leaf_size=8, max_depth=10, counts=True):
+    import torch
+    gt = gpu_tree(cloud, leaf_size, max_depth)
+    gt.refit(to_dev(mu))
+    q = to_dev(queries)
+    y = gt.forward(q, beta).cpu().numpy()
+    c = gt.query_counts(q, beta).cpu().numpy() if counts else None
+    gt.sync_status()
+    ot = oracle_tree(cloud, leaf_size, max_depth)
+    ot.update(mu)
+    ref, rc = ot.forward(queries, beta, counters=True)
+    return y, ref, c, rc
+
+
+def test_sphere_2k():
+    w = syn.workload("sphere-2k")
+    y, ref, c, rc = _run(w.cloud, w.mu, w.queries)
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)
+
+
+@pytest.mark.parametrize("beta", [0.5, 1.0, 2.0, 4.0])
+def test_scene_betas(beta):
+    w = syn.workload("scene-200k", scale=0.1)
+    y, ref, c, rc = _run(w.cloud, w.mu, w.queries[:30011], beta)
+    assert np.all(normwise(y, ref) <= TOL), normwise(y, ref)
+    assert np.array_equal(c.astype(np.int64), rc)
+
+
+@pytest.mark.parametrize("C", [1, 2, 3, 5, 8, 16, 33])
+def test_channel_counts(C):
+    w = syn.workload("scene-200k", scale=0.05)
+    mu = syn.attributes(w.cloud.n, C, seed=C)
+    y, ref, _, _ = _run(w.cloud, mu, w.queries[:5000], counts=False)
+    assert y.shape == (5000, C)
+    assert np.all(normwise(y, ref) <= TOL)
+
+
+@pytest.mark.parametrize("leaf_size", [1, 4, 16])
+def test_leaf_sizes(leaf_size):
+    w = syn.workload("scene-200k", scale=0.05)
+    y, ref, c, rc = _run(w.cloud, w.mu, w.queries[:7000], leaf_size=leaf_size)
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)
+
+
+def test_no_far_node_is_brute_force():
+    """beta -> infinity opens every node: the GPU sum is exact, compared with the
+    oracle's brute force (the plain definition, eq. dipole_sum)."""
+    w = syn.workload("sphere-2k")
+    c = w.cloud
+    y, _, _, _ = _run(c, w.mu, w.queries, beta=1e30, counts=False)
+    bf = oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
+    assert np.all(normwise(y, bf) <= TOL)
+
+
+def test_singular_kernel_eps_zero_and_queries_on_points():
+    """eps = 0 (eq. pcwn) and queries exactly at points (a zero-distance term is 0)."""
+    cl = syn.sphere_cloud(3000, seed=4, eps=None)
+    mu = syn.attributes(cl.n, 2, seed=5, kind="unit01")
+    q = np.concatenate([cl.points[:64], syn.uniform_box_queries(1000, seed=6)])
+    y, ref, c, rc = _run(cl, mu, q)
+    assert np.all(np.isfinite(y))
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)
+
+
+def test_small_and_ragged_sizes():
+    rng = np.random.default_rng(11)
+    for n in [1, 2, 9, 70]:
+        p = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+        cl = syn.Cloud(p, syn._unit(rng.normal(size=(n, 3))).astype(np.float32),
+                       rng.uniform(0.01, 0.1, n).astype(np.float32),
+                       rng.uniform(0.0, 0.2, n).astype(np.float32))
+        mu = rng.normal(size=(n, 3)).astype(np.float32)
+        for nq in [1, 31, 33, 65]:
+            q = rng.uniform(-2, 2, (nq, 3)).astype(np.float32)
+            y, ref, c, rc = _run(cl, mu, q)
+            assert np.all(normwise(y, ref) <= TOL), (n, nq)
+            assert np.array_equal(c.astype(np.int64), rc)
+
+
+def test_duplicate_points_deep_leaf():
+    """Many coincident points: a depth-10 leaf with more than leaf_size points."""
+    rng = np.random.default_rng(12)
+    p = np.concatenate([np.zeros((50, 3)), rng.uniform(-1, 1, (500, 3))]).astype(np.float32)
+    n = len(p)
+    cl = syn.Cloud(p, syn._unit(rng.normal(size=(n, 3))).astype(np.float32),
+                   np.full(n, 0.01, np.float32), np.full(n, 0.03, np.float32))
+    mu = rng.uniform(0, 1, (n, 1)).astype(np.float32)
+    q = np.concatenate([rng.normal(scale=0.05, size=(300, 3)),
+                        rng.uniform(-1, 1, (300, 3))]).astype(np.float32)
+    y, ref, c, rc = _run(cl, mu, q)
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)
+
+
+def test_zero_queries_and_state_errors():
+    import torch
+    from paper_2405_16788_gb300 import dipole
+    w = syn.workload("sphere-2k")
+    gt = gpu_tree(w.cloud)
+    with pytest.raises(dipole.DipoleError) as e:
+        gt.forward(to_dev(w.queries[:10]), 2.0)
+    assert e.value.code == dipole.DIPOLE_ESTATE
+    gt.refit(to_dev(w.mu))
+    out = gt.forward(torch.zeros((0, 3), device="cuda"), 2.0)
+    assert out.shape == (0, 1)
+    with pytest.raises(dipole.DipoleError):
+        gt.forward(to_dev(w.queries[:10]), 0.0)
+    gt.sync_status()
+
+
+def test_nonfinite_query_is_reported_not_hung():
+    from paper_2405_16788_gb300 import dipole
+    w = syn.workload("sphere-2k")
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    q = w.queries[:100].copy()
+    q[7, 0] = np.nan
+    y = gt.forward(to_dev(q), 2.0).cpu().numpy()
+    with pytest.raises(dipole.DipoleError) as e:
+        gt.sync_status()
+    assert e.value.code == dipole.DIPOLE_ENONFINITE
+    ref = oracle_tree(w.cloud)
+    ref.update(w.mu)
+    r = ref.forward(np.delete(q, 7, axis=0), 2.0)
+    assert np.all(normwise(np.delete(y, 7, axis=0), r) <= TOL)
+    gt.sync_status()  # cleared
+
+
+def test_bf16_attributes():
+    """Attributes stored as bfloat16: kernel error vs the oracle on the rounded
+    attributes <= 1e-4; total error vs the float32 attributes <= 3e-3."""
+    import torch
+    w = syn.workload("scene-200k", scale=0.1)
+    mu = syn.attributes(w.cloud.n, 16, seed=21)
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(mu).to(torch.bfloat16))
+    q = w.queries[:20000]
+    y = gt.forward(to_dev(q), 2.0).cpu().numpy()
+    ot = oracle_tree(w.cloud)
+    ot.update(bf16_round(mu))
+    assert np.all(normwise(y, ot.forward(q, 2.0)) <= TOL)
+    ot.update(mu)
+    assert np.all(normwise(y, ot.forward(q, 2.0)) <= 3e-3)
+
+
+@pytest.mark.slow
+def test_full_size_scene_1m_sampled():
+    """The benchmark's workload and launch configuration (1M points, 524,288
+    ray-sample queries, C = 4): all queries on the GPU, 4096 sampled ones
+    checked against the oracle, decisions bit-exact."""
+    w = syn.workload("scene-1m")
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    q = to_dev(w.queries)
+    y = gt.forward(q, 2.0).cpu().numpy()
+    cnt = gt.query_counts(q, 2.0).cpu().numpy()
+    gt.sync_status()
+    idx = np.random.default_rng(0).choice(len(w.queries), 4096, replace=False)
+    ot = oracle_tree(w.cloud)
+    ot.update(w.mu)
+    ref, rc = ot.forward(w.queries[idx], 2.0, counters=True)
+    assert np.all(normwise(y[idx], ref) <= TOL), normwise(y[idx], ref)
+    assert np.array_equal(cnt[idx].astype(np.int64), rc)
