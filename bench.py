@@ -41,8 +41,8 @@ LEAF = 8
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="scene-1m")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -224,21 +224,20 @@ def measured_traffic(kernel: str):
 
 
 def l2_probe(torch, dev):
-    """Best-of-10 copy bandwidth over a 48 MB working set (inside L2)."""
-    a = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device=dev).uniform_()
-    b = torch.empty_like(a)
+    """Best-of-10 read bandwidth of one reduction kernel that reads a 32 MB
+    buffer 32 times (a stride-0 view), so the data comes from L2."""
+    a = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device=dev).uniform_()
+    v = a.expand(32, a.numel())
     for _ in range(3):
-        b.copy_(a)
+        v.sum()
     best = 0.0
     for _ in range(10):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(20):
-            b.copy_(a)
+        v.sum()
         e1.record()
         e1.synchronize()
-        gbs = 20 * 2 * a.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-        best = max(best, gbs)
+        best = max(best, v.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
     return best
 
 
