@@ -10,10 +10,10 @@
  *   D^c(x) = sum_m A_m rho(|p_m - x| / eps_m) n_m.(p_m - x) / (4 pi |p_m - x|^3) mu_m^c,
  *   rho(t) = erf(t) - (2t/sqrt(pi)) exp(-t^2)
  *
- * (Sec. 3.2, eq. dipole_sum; Sec. 3.1, eq. regularized_poisson; Sec. 4.1,
+ * (Sec. 4.2, eq. dipole_sum; Sec. 4.1, eq. regularized_poisson; Sec. 5.1,
  * eq. appearance_features for several channels), approximated by Barnes-Hut
- * (Sec. 5.1, eq. farfield; Alg. 1, PrimalQuery), and its adjoint with respect
- * to mu by the two-stage scheme of Sec. 5.2 (Alg. 1, AdjointQuery; App. C,
+ * (Sec. 6.1, eq. farfield; Alg. 1, PrimalQuery), and its adjoint with respect
+ * to mu by the two-stage scheme of Sec. 6.2 (Alg. 1, AdjointQuery; App. C,
  * eqs. farfield_gradient and farfield_features_gradient).
  *
  * Conventions shared by every entry point:
@@ -54,7 +54,7 @@ typedef enum {
 typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
 
 /* Octree parameters.  leaf_size in [1, 64] (the paper's leaves are single
- * points, Sec. 5.1; 8 is the default here); max_depth in [0, 10] octal digits
+ * points, Sec. 6.1; 8 is the default here); max_depth in [0, 10] octal digits
  * of the 30-bit Morton code. */
 typedef struct {
     int32_t leaf_size;
@@ -73,9 +73,9 @@ typedef struct {
 } dipole_tree_info;
 
 /*
- * Build the octree over n points (Sec. 5.3, "tree construction and update":
+ * Build the octree over n points (Sec. 6.3, "tree construction and update":
  * built once, positions are not optimized) and the node geometry of
- * Sec. 5.1, eq. farfield_dipole: area A~_t = sum A_m, centroid
+ * Sec. 6.1, eq. farfield_dipole: area A~_t = sum A_m, centroid
  * p~_t = sum A_m p_m / A~_t, radius r~_t = max |p_m - p~_t|, and the node
  * regularization radius eps~_t = sum A_m eps_m / A~_t.
  *
@@ -103,8 +103,8 @@ int dipole_build_tree(const float* points, const float* normals, const float* ar
                       void* stream, dipole_tree** out);
 
 /*
- * Tree update of the node moments (Sec. 5.3: done at the start of every
- * iteration; Sec. 5.1, eq. farfield_dipole_features):
+ * Tree update of the node moments (Sec. 6.3: done at the start of every
+ * iteration; Sec. 6.1, eq. farfield_dipole_features):
  *   S_t^c = A~_t n~_t^c = sum_{m in t} A_m n_m mu_m^c   (3 values per channel)
  *
  *   attrs     [n, channels] float (dtype DIPOLE_F32) or bfloat16 (DIPOLE_BF16)
@@ -140,7 +140,7 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
                    float* out, void* stream);
 
 /*
- * Adjoint queries, two-stage (Sec. 5.2, App. C).  Given grad_out[j, c] =
+ * Adjoint queries, two-stage (Sec. 6.2, App. C).  Given grad_out[j, c] =
  * dL/dD^c(queries[j]):
  *   stage 1 (Alg. 1, AdjointQuery; eq. farfield_gradient): the same traversal
  *     as dipole_forward adds rho(d/eps~) (p~ - x)/(4 pi d^3) g^c into dS_t^c at

@@ -99,7 +99,7 @@ def num_threads() -> int:
 
 
 def rho(t: float) -> float:
-    """rho(t) = erf(t) - 2t/sqrt(pi) exp(-t^2); Sec. 3.1, eq. (regularized_poisson)."""
+    """rho(t) = erf(t) - 2t/sqrt(pi) exp(-t^2); Sec. 4.1, eq. (regularized_poisson)."""
     return float(_load().orc_rho(float(t)))
 
 
@@ -155,7 +155,7 @@ def far_test(x, c, r, beta) -> bool:
 
 
 class Tree:
-    """CPU octree, node aggregates and Barnes-Hut queries (Sec. 5, Alg. 1)."""
+    """CPU octree, node aggregates and Barnes-Hut queries (Sec. 6, Alg. 1)."""
 
     def __init__(self, points, normals, areas, eps=None, leaf_size=8, max_depth=10):
         lib = _load()
@@ -218,7 +218,7 @@ class Tree:
         return (out, cnt) if counters else out
 
     def adjoint(self, queries, beta, g):
-        """Two-stage adjoint (Sec. 5.2, App. C): dL/dmu [N, C] float64, input order."""
+        """Two-stage adjoint (Sec. 6.2, App. C): dL/dmu [N, C] float64, input order."""
         if self.C is None:
             raise RuntimeError("call update() first")
         q = _f32(queries)

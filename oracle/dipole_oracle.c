@@ -9,13 +9,13 @@
  * Paper: Chen, Miller, Gkioulekas, "3D Reconstruction with Fast Dipole Sums"
  * (arXiv 2405.16788).  Citations name the paper's sections and equations.
  *
- *   rho, P_eps          Sec. 3.1, eq. (regularized_poisson) and eq. (pcwn)
- *   dipole sum          Sec. 3.2, eq. (dipole_sum); multi-channel: eq. (appearance_features)
- *   node aggregates     Sec. 5.1, eqs. (farfield_dipole), (farfield_dipole_features)
- *   far field           Sec. 5.1, eq. (farfield)
+ *   rho, P_eps          Sec. 4.1, eq. (regularized_poisson) and eq. (pcwn)
+ *   dipole sum          Sec. 4.2, eq. (dipole_sum); multi-channel: eq. (appearance_features)
+ *   node aggregates     Sec. 6.1, eqs. (farfield_dipole), (farfield_dipole_features)
+ *   far field           Sec. 6.1, eq. (farfield)
  *   primal query        Alg. 1, PrimalQuery
  *   adjoint, stage 1    Alg. 1, AdjointQuery; App. C, eq. (farfield_gradient)
- *   adjoint, stage 2    Sec. 5.2 (two-stage scheme); App. C, eq. (farfield_features_gradient)
+ *   adjoint, stage 2    Sec. 6.2 (two-stage scheme); App. C, eq. (farfield_features_gradient)
  *
  * Readings of the paper that this file takes where the paper is silent or
  * ambiguous (each one is also listed in the design notes):
@@ -61,7 +61,7 @@ int orc_num_threads(void) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Kernel (Sec. 3.1)                                                          */
+/* Kernel (Sec. 4.1)                                                          */
 /* ------------------------------------------------------------------------ */
 
 /* rho(t) = erf(t) - (2 t / sqrt(pi)) exp(-t^2): the regularizing factor of
@@ -131,7 +131,7 @@ void orc_brute_adjoint(int64_t n, const float* pts, const float* nrm, const floa
 }
 
 /* ------------------------------------------------------------------------ */
-/* Octree (R4), Sec. 5.1 and Sec. 5.3 "tree construction"                     */
+/* Octree (R4), Sec. 6.1 and Sec. 6.3 "tree construction"                     */
 /* ------------------------------------------------------------------------ */
 /*
  * Bounding cube: lo = per-axis float minimum; ext = largest per-axis
@@ -455,7 +455,7 @@ static void far_vector(const orc_tree* T, int32_t t, const double x[3], double v
 
 typedef struct { int64_t tested, accepted, leafpts; } counters;
 
-/* PrimalQuery(x, node): returns all C channels at once (Sec. 5.3). */
+/* PrimalQuery(x, node): returns all C channels at once (Sec. 6.3). */
 static void primal_query(const orc_tree* T, const float xf[3], const double x[3], int32_t t,
                          float beta, double* out, counters* k) {
     int C = T->C;
@@ -501,7 +501,7 @@ void orc_bh_forward(const orc_tree* T, int64_t q, const float* qry, float beta, 
     }
 }
 
-/* AdjointQuery(dD, x, node): stage 1 of the two-stage scheme (Sec. 5.2).
+/* AdjointQuery(dD, x, node): stage 1 of the two-stage scheme (Sec. 6.2).
  * dnt: [nn,3C] node gradients d n~_t; dmu: [n,C] sorted, for opened leaves. */
 static void adjoint_query(const orc_tree* T, const float xf[3], const double x[3],
                           const double* g, int32_t t, float beta, double* dnt, double* dmu) {

@@ -22,7 +22,7 @@ constexpr int kStatusBadArea = 4;
 constexpr int kStatusBadRadius = 8;
 
 // One octree node, 32 bytes = one L2 sector, read by every visiting warp.
-//   geo  = {p~.x, p~.y, p~.z, r~}            (Sec. 5.1, eq. farfield_dipole)
+//   geo  = {p~.x, p~.y, p~.z, r~}            (Sec. 6.1, eq. farfield_dipole)
 //   meta = {skip, first, leaf point count (0 for internal nodes), bits of 1/eps~}
 struct __align__(32) NodeRec {
     float4 geo;

@@ -9,7 +9,7 @@ namespace dip {
 // Floats per node moment row: 3 per channel, padded to whole float4s.
 __host__ __device__ constexpr int srow(int cp) { return (3 * cp + 3) & ~3; }
 
-// rho(t) = erf(t) - (2t/sqrt(pi)) exp(-t^2)  (Sec. 3.1, eq. regularized_poisson).
+// rho(t) = erf(t) - (2t/sqrt(pi)) exp(-t^2)  (Sec. 4.1, eq. regularized_poisson).
 // Above kTCut, 1 - rho < 1e-8 and rho rounds to 1 in float.  Below kTSeries
 // the two terms cancel, so rho(t)/t^3 is taken from its Maclaurin series,
 // obtained by integrating rho'(t) = (4/sqrt(pi)) t^2 exp(-t^2) term by term:

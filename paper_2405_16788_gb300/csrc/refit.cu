@@ -1,6 +1,6 @@
-// Tree update of the node moments (Sec. 5.1, eq. farfield_dipole_features;
-// Sec. 5.3: refreshed at the start of every iteration) and the second stage
-// of the adjoint (Sec. 5.2; App. C, eq. farfield_features_gradient).
+// Tree update of the node moments (Sec. 6.1, eq. farfield_dipole_features;
+// Sec. 6.3: refreshed at the start of every iteration) and the second stage
+// of the adjoint (Sec. 6.2; App. C, eq. farfield_features_gradient).
 //
 // Moments are stored as S_t^c = A~_t n~_t^c = sum_{m in t} A_m n_m mu_m^c, so the
 // far field needs no division by A~_t and stage 2 needs no multiplication by

@@ -1,5 +1,5 @@
 // Device-wide primitives: exclusive scan, stable LSD radix sort of (key, value)
-// pairs, and Morton codes of query points.  The octree of Sec. 5.1 is built
+// pairs, and Morton codes of query points.  The octree of Sec. 6.1 is built
 // over points sorted by 30-bit Morton code (ties kept in input order); the
 // queries are sorted the same way so that a warp holds nearby points.
 #include "common.cuh"

@@ -1,5 +1,5 @@
-// Barnes-Hut primal and adjoint queries (Alg. 1; Sec. 5.1, eq. farfield;
-// Sec. 5.2 and App. C, eq. farfield_gradient).
+// Barnes-Hut primal and adjoint queries (Alg. 1; Sec. 6.1, eq. farfield;
+// Sec. 6.2 and App. C, eq. farfield_gradient).
 //
 // Persistent, warp-cooperative, stackless traversal.  Queries are sorted by
 // Morton code, so the 32 queries of a warp are neighbours.  The tree is in

@@ -1,5 +1,5 @@
-// Octree construction and node geometry (Sec. 5.1, eq. farfield_dipole;
-// Sec. 5.3: the tree is built once because positions are not optimized).
+// Octree construction and node geometry (Sec. 6.1, eq. farfield_dipole;
+// Sec. 6.3: the tree is built once because positions are not optimized).
 //
 // Tree definition (the paper says only "octree"): 30-bit Morton codes over
 // the bounding cube, points sorted stably by code; a node at level l is a

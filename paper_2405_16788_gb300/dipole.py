@@ -6,7 +6,7 @@ CUDA stream, and turns status codes into exceptions.  There is no CPU path:
 if libdipole.so is missing or cannot be loaded, importing the functions raises.
 
 Method: Barnes-Hut fast summation of regularized dipole sums, forward and
-adjoint (Chen, Miller, Gkioulekas, arXiv 2405.16788, Sec. 5 and Alg. 1).
+adjoint (Chen, Miller, Gkioulekas, arXiv 2405.16788, Sec. 6 and Alg. 1).
 """
 from __future__ import annotations
 
@@ -294,7 +294,7 @@ class DipoleTree:
 class DipoleSum(torch.autograd.Function):
     """D = dipole sum of `attrs` at `queries` (Barnes-Hut, Alg. 1).  Forward runs
     the tree update then the primal queries; backward runs the two-stage adjoint
-    (Sec. 5.2), recomputing the traversal instead of storing interaction lists."""
+    (Sec. 6.2), recomputing the traversal instead of storing interaction lists."""
 
     @staticmethod
     def forward(ctx, attrs, tree: DipoleTree, queries, beta: float):

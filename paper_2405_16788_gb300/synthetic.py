@@ -6,13 +6,13 @@ upstream gradients.  It holds none of the dipole-sum arithmetic, so both the
 CUDA path and the CPU oracle take their inputs from here.
 
 The paper's scenes are dense structure-from-motion point clouds of the DTU and
-BlendedMVS datasets (Sec. 6), which are not available; the procedural clouds
+BlendedMVS datasets (Sec. 7), which are not available; the procedural clouds
 below stand in for them: a noisy torus and two spheres, outliers uniform in a
 box, jittered normals, and (for the largest workload) anisotropic density.
 Area weights are the component area divided by its point count (the paper
 estimates them as in Barill et al. 2018, which it does not restate); outliers
 take the median inlier weight.  Queries are stratified samples along camera
-rays (Sec. 6.1, "ray sampling").
+rays (Sec. 7.1, "ray sampling").
 
 All generators use ``numpy.random.Generator(PCG64(seed))``.
 """

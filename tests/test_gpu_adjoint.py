@@ -1,4 +1,4 @@
-"""GPU adjoint (two-stage, Sec. 5.2) vs the oracle: norm-wise error <= 1e-3
+"""GPU adjoint (two-stage, Sec. 6.2) vs the oracle: norm-wise error <= 1e-3
 against the oracle's double-precision Barnes-Hut adjoint on the same tree,
 against brute force when nothing is far, the adjoint identity on the GPU,
 and the autograd path against finite differences of a compositing loss
@@ -101,7 +101,7 @@ S_SCALE = 50.0
 
 
 def _render_loss_np(D, target, n_rays, n_samp):
-    """Harness loss of a volume-rendering shape (Sec. 2 eqs. vacancy and
+    """Harness loss of a volume-rendering shape (Sec. 3.1, eqs. vacancy and
     quadrature): phi = 1/2 - D_geo, v = Phi(s phi), per-sample opacity from the
     change of v along the ray, colour = sum T alpha RGB, L1 to a target."""
     from scipy.special import ndtr

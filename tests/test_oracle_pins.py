@@ -30,7 +30,7 @@ def _golden():
 def test_rho_is_gaussian_ball_mass():
     """rho(t) equals the mass of the Gaussian exp(-r^2/eps^2)/(pi^1.5 eps^3) inside
     radius r = t eps, i.e. the regularized lower incomplete gamma P(3/2, t^2)
-    (scipy).  Pins both terms of rho and their factors (Sec. 3.1)."""
+    (scipy).  Pins both terms of rho and their factors (Sec. 4.1)."""
     for t in np.concatenate([np.linspace(0.05, 6.0, 120), [0.3, 1.0, 2.5, 10.0]]):
         ref = sp.gammainc(1.5, t * t)
         assert abs(oracle.rho(t) - ref) < 1e-13 + 1e-11 * ref, t
@@ -46,7 +46,7 @@ def test_rho_derivative_identity():
 
 def test_rho_limits_from_paper():
     """rho(0) = 0, rho(inf) = 1, and the finite value at the origin printed in
-    Sec. 3.1: rho(r/eps) / (4 pi r^3) -> 3^-1 eps^-3 pi^-3/2 (golden fixture)."""
+    Sec. 4.1: rho(r/eps) / (4 pi r^3) -> 3^-1 eps^-3 pi^-3/2 (golden fixture)."""
     g = _golden()
     assert oracle.rho(0.0) == 0.0
     assert oracle.rho(50.0) == g["rho_limits"]["rho_infinity"]
@@ -84,7 +84,7 @@ def _gaussian_smeared_dipole(x, p, n, eps, ns=96, nth=48, nph=96):
 
 @pytest.mark.parametrize("t", [0.4, 1.0, 1.7, 3.0])
 def test_single_dipole_matches_gaussian_noise_expectation(t):
-    """Prop. 2 (Sec. 3.2): the expected singular kernel of a point whose position
+    """Prop. 2 (Sec. 4.2): the expected singular kernel of a point whose position
     is Gaussian equals the regularized kernel.  With rho as printed, the noise
     has per-axis variance eps^2/2 (reading of the eps convention)."""
     eps = 0.3
@@ -124,7 +124,7 @@ def _blurred_ball(s, R, eps):
 
 
 def test_sphere_regularized_winding_number_is_blurred_indicator():
-    """Prop. 1 (Sec. 3.1, App. A.1): the regularized winding number of a closed
+    """Prop. 1 (Sec. 4.1, App. A.1): the regularized winding number of a closed
     surface is its indicator blurred by a Gaussian.  A dense Fibonacci sphere
     (spacing 0.018 << eps = 0.15) reproduces the closed form at any distance,
     including on and near the surface."""
@@ -182,7 +182,7 @@ def test_flat_disk_solid_angle():
 
 
 def test_eps_to_zero_gives_poisson_kernel():
-    """Sec. 3.1: P_eps -> P as eps -> 0, pointwise away from the points."""
+    """Sec. 4.1: P_eps -> P as eps -> 0, pointwise away from the points."""
     cl = syn.sphere_cloud(3000, seed=9, eps=None)
     q = (syn._unit(np.random.default_rng(1).normal(size=(32, 3))) *
          np.random.default_rng(2).uniform(0.3, 0.8, (32, 1))).astype(np.float32)
@@ -212,7 +212,7 @@ def test_bh_equals_brute_force_when_nothing_is_far():
 
 
 def test_bh_single_point_leaves_far_field_is_exact_per_point():
-    """With single-point leaves (the paper's tree, Sec. 5.1) a leaf has radius 0,
+    """With single-point leaves (the paper's tree, Sec. 6.1) a leaf has radius 0,
     so it is always far and its far field (eq. farfield) is that point's exact
     term: a two-point cloud with leaf size 1, queried inside beta times the
     root radius, reproduces brute force."""
@@ -247,7 +247,7 @@ def test_bh_error_shrinks_with_beta():
 
 
 def test_bh_complexity_is_logarithmic():
-    """Sec. 5.2: O(log M) per query.  Mean tested nodes grows far slower than N."""
+    """Sec. 6.2: O(log M) per query.  Mean tested nodes grows far slower than N."""
     means = []
     for n in [2000, 16000, 128000]:
         cl = syn.sphere_cloud(n, seed=11, eps=0.02)

@@ -1,4 +1,4 @@
-"""Pins for the oracle's octree (Sec. 5.1 / 5.3, "tree construction").
+"""Pins for the oracle's octree (Sec. 6.1 / 6.3, "tree construction").
 
 The paper says only "octree" and "follow libigl"; the tree used here is the
 compressed 30-bit Morton octree stated in the oracle's header.  These tests
