@@ -140,6 +140,32 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
                    float* out, void* stream);
 
 /*
+ * dipole_forward without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc — code that
+ * runs under a fixed device-memory budget or inside a host application whose
+ * own allocator owns all device memory, and loops that must not allocate
+ * because cudaMalloc/cudaFree can synchronize the device or fail part way
+ * through under memory pressure.  dipole_forward allocates its query-sort
+ * buffers and work counter per call; this variant takes them from a
+ * file-scope device array instead.
+ *
+ *   Same arguments, results and errors as dipole_forward, and additionally
+ *   q <= 262144 (2^18): larger q returns DIPOLE_EINVAL with a message saying
+ *   so (split the queries, or use dipole_forward).
+ *
+ * The array (about 4.2 MB) exists on every GPU that loads this library and
+ * stays there until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) for that device; make
+ * that first call before any stream capture.  Every call uses the same array
+ * and leaves its contents behind; the work counter is cleared at the start of
+ * each call.  Calls that overlap on the GPU (different streams or threads,
+ * any tree) race on the array and give wrong results: serialize them.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ */
+int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           float* out, void* stream);
+
+/*
  * Adjoint queries, two-stage (Sec. 6.2, App. C).  Given grad_out[j, c] =
  * dL/dD^c(queries[j]):
  *   stage 1 (Alg. 1, AdjointQuery; eq. farfield_gradient): the same traversal

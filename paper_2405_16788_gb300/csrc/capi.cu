@@ -128,6 +128,23 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
                       as_stream(stream));
 }
 
+int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           float* out, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: tree is NULL");
+    if (tree->C == 0)
+        return dip_fail(DIPOLE_ESTATE, "dipole_forward_noalloc: call dipole_refit first");
+    if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: q must be >= 0");
+    if (q > 0 && (!queries || !out))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: queries and out are required");
+    if (q > dip::noalloc_max_queries())
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_forward_noalloc: q exceeds the static scratch limit of 262144 "
+                        "queries; split the queries or use dipole_forward");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    return dip::query_noalloc(tree, queries, q, beta, out, as_stream(stream));
+}
+
 int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float beta,
                    const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: tree is NULL");

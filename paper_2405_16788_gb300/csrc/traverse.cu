@@ -15,6 +15,8 @@
 // interaction lists.  The lanes taking a far node are all at that node in the
 // same step, so their contributions to dS_t are summed inside the warp before
 // one set of atomics; the same holds for the points of an opened leaf.
+#include <mutex>
+
 #include "kernels.cuh"
 #include "tree.cuh"
 
@@ -270,7 +272,84 @@ int dispatch(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
     }
 }
 
+// ---------------------------------------------------------------- no-alloc forward
+// Scratch of dipole_forward_noalloc: the query sort (codes, indices, their
+// ping-pong copies, the radix histograms with their scan space) and the work
+// counter, for at most kNoAllocMaxQueries queries.  A file-scope device array:
+// every GPU that loads this library holds it (about 4.2 MB) until the process
+// exits; nothing is allocated per call.
+constexpr int64_t kNoAllocMaxQueries = int64_t(1) << 18;
+constexpr int64_t kNoAllocHistEntries = (kNoAllocMaxQueries / 4096) * 256 + 4096;
+constexpr size_t kNoAllocBytes =
+    4 * sizeof(uint32_t) * (size_t)kNoAllocMaxQueries + sizeof(uint32_t) * (size_t)kNoAllocHistEntries + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device (host code must not use the symbol itself: it names a host stand-in).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    DIP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return dip_fail(-1, "dipole_forward_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        DIP_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return 0;
+}
+
 }  // namespace
+
+int64_t noalloc_max_queries() { return kNoAllocMaxQueries; }
+
+int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float beta, float* out,
+                  cudaStream_t s) {
+    if (q > kNoAllocMaxQueries || radix_hist_entries(q) > kNoAllocHistEntries)
+        return dip_fail(-1, "dipole_forward_noalloc: q exceeds the static scratch limit of "
+                            "262144 queries; split the queries or use dipole_forward");
+    void* base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    uint32_t* codes = static_cast<uint32_t*>(base);
+    uint32_t* idx = codes + kNoAllocMaxQueries;
+    uint32_t* ktmp = idx + kNoAllocMaxQueries;
+    uint32_t* vtmp = ktmp + kNoAllocMaxQueries;
+    uint32_t* hist = vtmp + kNoAllocMaxQueries;
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(hist + kNoAllocHistEntries);
+    // the previous call's contents stay in the array: only the counter must start at 0
+    DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
+    query_codes(queries, q, t->bbox, codes, idx, t->status, s);
+    radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, 30, s);
+    QueryArgs a;
+    a.nodes = t->nodes;
+    a.pts = t->pts;
+    a.nn = (unsigned)t->nn;
+    a.status = t->status;
+    a.q = queries;
+    a.nq = q;
+    a.qperm = idx;
+    a.beta = beta;
+    a.C = t->C;
+    a.mu = t->mu;
+    a.S = t->S;
+    a.out = out;
+    a.g = nullptr;
+    a.dS = nullptr;
+    a.dmu = nullptr;
+    a.counts = nullptr;
+    a.work = work;
+    rc = dispatch<kForward>(t, a, s);
+    if (rc) return rc;
+    DIP_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
 
 int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta, float* out,
           const float* g, float* grad, int accumulate, int32_t* counts, cudaStream_t s) {

@@ -78,6 +78,12 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
           float* out, const float* g, float* grad, int accumulate, int32_t* counts,
           cudaStream_t s);
 
+// Forward queries with all scratch in a static device array (no allocation);
+// q <= noalloc_max_queries().
+int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float beta, float* out,
+                  cudaStream_t s);
+int64_t noalloc_max_queries();
+
 // Stage 2 of the adjoint (eq. farfield_features_gradient) into grad [n, C].
 int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s);
 

@@ -33,7 +33,7 @@ DIPOLE_BF16 = 1
 EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
-            "dipole_kernel_launches"]
+            "dipole_kernel_launches", "dipole_forward_noalloc"]
 
 
 class DipoleError(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_build_tree": [P, P, P, P, I64, P, P, P],
             "dipole_refit": [P, P, I32, I32, P],
             "dipole_forward": [P, P, I64, F, P, P],
+            "dipole_forward_noalloc": [P, P, I64, F, P, P],
             "dipole_adjoint": [P, P, I64, F, P, P, I32, P],
             "dipole_query_counts": [P, P, I64, F, P, P],
             "dipole_sync_status": [P, P],
@@ -159,6 +160,16 @@ def dipole_forward(tree: int, queries: torch.Tensor, beta: float, out: torch.Ten
     q = int(queries.shape[0])
     _check(load_library().dipole_forward(ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)),
                                          q, float(beta), _dev(out, "out"), _stream(stream)))
+
+
+def dipole_forward_noalloc(tree: int, queries: torch.Tensor, beta: float, out: torch.Tensor,
+                           stream=None):
+    """dipole_forward with its scratch in a static device array: allocates
+    nothing, q <= 262144, overlapping calls race (see include/dipole.h)."""
+    q = int(queries.shape[0])
+    _check(load_library().dipole_forward_noalloc(ctypes.c_void_p(tree),
+                                                 _dev(queries, "queries", shape=(q, 3)), q,
+                                                 float(beta), _dev(out, "out"), _stream(stream)))
 
 
 def dipole_adjoint(tree: int, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
