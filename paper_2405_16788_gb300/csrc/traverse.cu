@@ -44,6 +44,7 @@ struct QueryArgs {
     float* dmu;
     int32_t* counts;
     unsigned long long* work;
+    const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
 };
 
 template <typename AT>
@@ -90,24 +91,40 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
         unsigned long long pk = 0;
         if (lane == 0) pk = atomicAdd(a.work, 1ull);
         pk = __shfl_sync(FULL, pk, 0);
-        const int64_t base = (int64_t)pk * 32;
-        if (base >= a.nq) break;
+        if ((int64_t)pk * 32 >= a.nq) break;
+        const int64_t base = (int64_t)(a.porder ? a.porder[pk] : pk) * 32;
         const int64_t qi = base + lane;
         const bool valid = qi < a.nq;
         const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
         if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
 
+        // Forward sums: plain float partial sums (part), folded every kFoldSteps
+        // warp steps into a Kahan-compensated sum (acc, cmp) for small channel
+        // counts; per-term Kahan for large ones (register budget).
+        constexpr bool kBlocked = CP <= 8;
+        constexpr unsigned kFoldSteps = 16;
         float acc[MODE == kForward ? CP : 1], cmp[MODE == kForward ? CP : 1];
+        float part[MODE == kForward && kBlocked ? CP : 1];
         float g[MODE == kAdjoint ? CP : 1];
         if (MODE == kForward) {
 #pragma unroll
             for (int c = 0; c < CP; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
+            if (kBlocked) {
+#pragma unroll
+                for (int c = 0; c < CP; ++c) part[c] = 0.f;
+            }
         }
         if (MODE == kAdjoint) {
 #pragma unroll
             for (int c = 0; c < CP; ++c) g[c] = (valid && c < a.C) ? a.g[qo * a.C + c] * kInv4Pi : 0.f;
         }
+        auto add_term = [&](int c, float v) {
+            if (MODE == kForward) {
+                if (kBlocked) part[c] += v;
+                else kahan_add(acc[c], cmp[c], v);
+            }
+        };
         int n_tested = 0, n_far = 0, n_pts = 0;
 
         unsigned next = valid ? 0u : nn;
@@ -139,82 +156,92 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
                     if (far) ++n_far;
                     else if (leaf) n_pts += meta.z;
                 }
-                continue;
-            }
-
-            if (__any_sync(FULL, far)) {
-                // far field, eq. farfield: rho(d/eps~) S.(p~ - x) / d^3 (1/4pi applied at the end)
-                float k = 0.f;
-                if (far) k = rho_over_d3(d2, __int_as_float(meta.w));
-                const float vx = -k * dx, vy = -k * dy, vz = -k * dz;
-                if (MODE == kForward) {
-                    const float* Sr = a.S + (size_t)n * SR;
-#pragma unroll
-                    for (int c0 = 0; c0 < CP; c0 += CH) {
-                        float s[3 * CH + 3];
-#pragma unroll
-                        for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
-                            const float4 q4 = __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
-                            s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
-                        }
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
-                            if (far) kahan_add(acc[c0 + c], cmp[c0 + c], term);
-                        }
-                    }
-                } else if (MODE == kAdjoint) {
-                    // eq. farfield_gradient: dS_t^c += rho (p~ - x)/d^3 g^c
-                    float* dst = a.dS + (size_t)n * SR;
-#pragma unroll
-                    for (int c0 = 0; c0 < CP; c0 += CH) {
-                        float v[3 * CH];
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            v[3 * c] = vx * g[c0 + c];
-                            v[3 * c + 1] = vy * g[c0 + c];
-                            v[3 * c + 2] = vz * g[c0 + c];
-                        }
-                        warp_reduce_add<3 * CH>(v, dst + 3 * c0, lane);
-                    }
-                }
-            }
-
-            if (__any_sync(FULL, open_leaf)) {
-                // opened leaf: exact sum over its points (eq. dipole_sum)
-                const int f = meta.y, cnt = meta.z;
-                for (int j = 0; j < cnt; ++j) {
-                    const PointRec pr = pts[f + j];
+            } else {
+                if (__any_sync(FULL, far)) {
+                    // far field, eq. farfield: rho(d/eps~) S.(p~ - x) / d^3 (1/4pi applied at the end)
                     float k = 0.f;
-                    if (open_leaf) {
-                        const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
-                        const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                        if (r2 > 0.f)
-                            k = rho_over_d3(r2, pr.geo.w) *
-                                fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
-                    }
+                    if (far) k = rho_over_d3(d2, __int_as_float(meta.w));
+                    const float vx = -k * dx, vy = -k * dy, vz = -k * dz;
                     if (MODE == kForward) {
-                        const AT* mrow = reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * CP;
+                        const float* Sr = a.S + (size_t)n * SR;
 #pragma unroll
                         for (int c0 = 0; c0 < CP; c0 += CH) {
-                            float m[CH];
-                            load_row<AT>(mrow + c0, m, CH);
+                            float s[3 * CH + 3];
 #pragma unroll
-                            for (int c = 0; c < CH; ++c)
-                                if (open_leaf) kahan_add(acc[c0 + c], cmp[c0 + c], k * m[c]);
+                            for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
+                                const float4 q4 = __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
+                                s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
+                            }
+#pragma unroll
+                            for (int c = 0; c < CH; ++c) {
+                                const float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
+                                if (far) add_term(c0 + c, term);
+                            }
                         }
                     } else if (MODE == kAdjoint) {
-                        float* dst = a.dmu + (size_t)(f + j) * CP;
+                        // eq. farfield_gradient: dS_t^c += rho (p~ - x)/d^3 g^c
+                        float* dst = a.dS + (size_t)n * SR;
 #pragma unroll
                         for (int c0 = 0; c0 < CP; c0 += CH) {
-                            float v[CH];
+                            float v[3 * CH];
 #pragma unroll
-                            for (int c = 0; c < CH; ++c) v[c] = k * g[c0 + c];
-                            warp_reduce_add<CH>(v, dst + c0, lane);
+                            for (int c = 0; c < CH; ++c) {
+                                v[3 * c] = vx * g[c0 + c];
+                                v[3 * c + 1] = vy * g[c0 + c];
+                                v[3 * c + 2] = vz * g[c0 + c];
+                            }
+                            warp_reduce_add<3 * CH>(v, dst + 3 * c0, lane);
                         }
                     }
                 }
+
+                if (__any_sync(FULL, open_leaf)) {
+                    // opened leaf: exact sum over its points (eq. dipole_sum)
+                    const int f = meta.y, cnt = meta.z;
+                    for (int j = 0; j < cnt; ++j) {
+                        const PointRec pr = pts[f + j];
+                        float k = 0.f;
+                        if (open_leaf) {
+                            const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
+                            const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                            if (r2 > 0.f)
+                                k = rho_over_d3(r2, pr.geo.w) *
+                                    fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
+                        }
+                        if (MODE == kForward) {
+                            const AT* mrow = reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * CP;
+#pragma unroll
+                            for (int c0 = 0; c0 < CP; c0 += CH) {
+                                float m[CH];
+                                load_row<AT>(mrow + c0, m, CH);
+#pragma unroll
+                                for (int c = 0; c < CH; ++c)
+                                    if (open_leaf) add_term(c0 + c, k * m[c]);
+                            }
+                        } else if (MODE == kAdjoint) {
+                            float* dst = a.dmu + (size_t)(f + j) * CP;
+#pragma unroll
+                            for (int c0 = 0; c0 < CP; c0 += CH) {
+                                float v[CH];
+#pragma unroll
+                                for (int c = 0; c < CH; ++c) v[c] = k * g[c0 + c];
+                                warp_reduce_add<CH>(v, dst + c0, lane);
+                            }
+                        }
+                    }
+                }
+                if (MODE == kForward && kBlocked && (steps % kFoldSteps) == 0u) {
+#pragma unroll
+                    for (int c = 0; c < CP; ++c) {
+                        kahan_add(acc[c], cmp[c], part[c]);
+                        part[c] = 0.f;
+                    }
+                }
             }
+        }
+        if (MODE == kForward && kBlocked) {
+#pragma unroll
+            for (int c = 0; c < CP; ++c) kahan_add(acc[c], cmp[c], part[c]);
         }
 
         if (valid) {
@@ -230,6 +257,55 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
         }
     }
 }
+
+// Cost estimate of each 32-query packet for longest-first scheduling: four of
+// its queries (lanes 0, 10, 21, 31) walk the tree alone with the same far test;
+// each counts its steps plus twice its leaf points and the packet takes the
+// largest.  Key = 65535 - cost, so an ascending sort puts the most expensive
+// packets first.  Four consecutive threads handle one packet.
+__global__ void k_packet_cost(const NodeRec* __restrict__ nodes, unsigned nn,
+                              const float* __restrict__ q, const uint32_t* __restrict__ qperm,
+                              int64_t nq, float beta, uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ val) {
+    const int64_t np = (nq + 31) / 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < 4 * np; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;  // the whole warp iterates together
+        const int64_t p = i >> 2;
+        unsigned cost = 0;
+        if (p < np) {
+            const int sub = (int)(i & 3);
+            int64_t qi = p * 32 + (sub == 0 ? 0 : sub == 1 ? 10 : sub == 2 ? 21 : 31);
+            if (qi >= nq) qi = nq - 1;
+            const int64_t qo = qperm[qi];
+            const float x0 = q[3 * qo], x1 = q[3 * qo + 1], x2 = q[3 * qo + 2];
+            unsigned n = 0;
+            while (n < nn && cost < 65535u) {
+                const float4 geo = __ldg(&nodes[n].geo);
+                const int4 meta = __ldg(&nodes[n].meta);
+                const float dx = __fsub_rn(x0, geo.x), dy = __fsub_rn(x1, geo.y), dz = __fsub_rn(x2, geo.z);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const float R = __fmul_rn(beta, geo.w);
+                const bool far = d2 > __fmul_rn(R, R);
+                ++cost;
+                if (!far && meta.z > 0) cost += 2u * (unsigned)meta.z;
+                const unsigned nx = (far || meta.z > 0) ? (unsigned)meta.x : n + 1u;
+                if (nx <= n) break;  // corrupt tree: the traversal kernel reports it
+                n = nx;
+            }
+            if (cost > 65535u) cost = 65535u;
+        }
+        cost = max(cost, __shfl_xor_sync(0xffffffffu, cost, 1));
+        cost = max(cost, __shfl_xor_sync(0xffffffffu, cost, 2));
+        if (p < np && (i & 3) == 0) {
+            key[p] = 65535u - cost;
+            val[p] = (uint32_t)p;
+        }
+    }
+}
+
+// Packets below this count are too few for the queue's tail to matter.
+constexpr int64_t kOrderMinPackets = 2048;
 
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
@@ -345,6 +421,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.dmu = nullptr;
     a.counts = nullptr;
     a.work = work;
+    a.porder = nullptr;  // Morton packet order: no scratch for the longest-first sort
     rc = dispatch<kForward>(t, a, s);
     if (rc) return rc;
     DIP_CUDA_TRY(cudaGetLastError());
@@ -366,6 +443,17 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
         query_codes(queries, q, t->bbox, codes, idx, t->status, s);
         radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, 30, s);
+    }
+    // Longest-first packet order (the codes/ktmp/vtmp buffers are free again).
+    const int64_t np = (q + 31) / 32;
+    const uint32_t* porder = nullptr;
+    if (np >= kOrderMinPackets && mode != kCount) {
+        int64_t blocks = (4 * np + 127) / 128;
+        note_launch();
+        k_packet_cost<<<(unsigned)blocks, 128, 0, s>>>(t->nodes, (unsigned)t->nn, queries, idx, q,
+                                                        beta, codes, ktmp);
+        radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
+        porder = ktmp;
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (mode == kAdjoint) {
@@ -392,6 +480,7 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         a.dmu = t->dmu;
         a.counts = counts;
         a.work = work;
+        a.porder = porder;
         if (mode == kForward) rc = dispatch<kForward>(t, a, s);
         else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
         else rc = dispatch<kCount>(t, a, s);
