@@ -153,7 +153,7 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
  *   q <= 262144 (2^18): larger q returns DIPOLE_EINVAL with a message saying
  *   so (split the queries, or use dipole_forward).
  *
- * The array (about 4.2 MB) exists on every GPU that loads this library and
+ * The array (about 4.5 MB) exists on every GPU that loads this library and
  * stays there until the process exits.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) for that device; make
  * that first call before any stream capture.  Every call uses the same array

@@ -64,10 +64,15 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
 int64_t scan_tmp_entries(int64_t n);
 void exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s);
 
-// Morton code of each query in the tree's bounding cube (clamped to it) and the
-// identity permutation; codes/idx hold q entries.
-void query_codes(const float* queries, int64_t q, const float* bbox, uint32_t* codes,
+// 30-bit Morton code (shifted right by `shift`) of each point in the tree's
+// bounding cube (clamped to it) and the identity permutation; codes/idx hold
+// q entries.
+void query_codes(const float* queries, int64_t q, const float* bbox, int shift, uint32_t* codes,
                  uint32_t* idx, int* status, cudaStream_t s);
+
+// Query sort key: the top 16 bits of the Morton code keep warps as coherent
+// as all 30 bits do and take two radix passes instead of four.
+constexpr int kQueryKeyBits = 16;
 
 int num_sms();
 

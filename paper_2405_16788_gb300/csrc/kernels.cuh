@@ -91,4 +91,94 @@ __device__ __forceinline__ void warp_reduce_add(float (&v)[V], float* dst, int l
     }
 }
 
+// Adjoint warp sums without data-dependent selects.  Within a chunk of CH
+// channels (1, 2 or 4) the lanes split the channels by their lane bits: after
+// exchanging with lane^16 (and lane^8 for CH = 4) a lane holds the running
+// sums of exactly one channel, kept(lane); a butterfly over the remaining lane
+// bits completes that channel's sum, and the lowest lane of each group issues
+// the atomics.  Because the channel a lane keeps or hands on at each exchange
+// depends only on its lane bits, the upstream gradient is permuted once per
+// packet (lane_channel_order) and every exchange is a plain shuffle and add.
+//
+// lane_channel_order: ord[0] = the channel kept to the end, ord[1] = the one
+// handed to lane^8 (CH = 4), then the two handed to lane^16.
+template <int CH>
+__device__ __forceinline__ void lane_channel_order(int lane, int (&ord)[CH]) {
+    if constexpr (CH == 4) {
+        const int p0 = (lane & 16) ? 2 : 0, b3 = (lane >> 3) & 1;
+        ord[0] = p0 + b3;        // kept
+        ord[1] = p0 + 1 - b3;    // kept at the first exchange, handed on at the second
+        ord[2] = ord[0] ^ 2;     // handed to lane^16
+        ord[3] = ord[1] ^ 2;
+    } else if constexpr (CH == 2) {
+        ord[0] = (lane & 16) ? 1 : 0;
+        ord[1] = ord[0] ^ 1;
+    } else {
+        ord[0] = 0;
+    }
+}
+
+// Lanes in a reduction group of the final channel: the lowest one owns it.
+template <int CH>
+__device__ __forceinline__ bool lane_owns(int lane) {
+    return (lane & (CH == 4 ? 7 : CH == 2 ? 15 : 31)) == 0;
+}
+
+// Far node: gp = this chunk's gradient in lane_channel_order; adds
+// sum over lanes of v (x) g^c into dst[3c + axis] for the chunk's channels.
+template <int CH>
+__device__ __forceinline__ void adjoint_far_reduce(float vx, float vy, float vz, const float* gp,
+                                                   float* dst, int kept, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float a0 = vx * gp[0], a1 = vy * gp[0], a2 = vz * gp[0];
+    if constexpr (CH == 4) {
+        float a3 = vx * gp[1], a4 = vy * gp[1], a5 = vz * gp[1];
+        a0 += __shfl_xor_sync(FULL, vx * gp[2], 16);
+        a1 += __shfl_xor_sync(FULL, vy * gp[2], 16);
+        a2 += __shfl_xor_sync(FULL, vz * gp[2], 16);
+        a3 += __shfl_xor_sync(FULL, vx * gp[3], 16);
+        a4 += __shfl_xor_sync(FULL, vy * gp[3], 16);
+        a5 += __shfl_xor_sync(FULL, vz * gp[3], 16);
+        a0 += __shfl_xor_sync(FULL, a3, 8);
+        a1 += __shfl_xor_sync(FULL, a4, 8);
+        a2 += __shfl_xor_sync(FULL, a5, 8);
+    } else if constexpr (CH == 2) {
+        a0 += __shfl_xor_sync(FULL, vx * gp[1], 16);
+        a1 += __shfl_xor_sync(FULL, vy * gp[1], 16);
+        a2 += __shfl_xor_sync(FULL, vz * gp[1], 16);
+    }
+#pragma unroll
+    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(FULL, a0, off);
+        a1 += __shfl_xor_sync(FULL, a1, off);
+        a2 += __shfl_xor_sync(FULL, a2, off);
+    }
+    if (lane_owns<CH>(lane)) {
+        float* d = dst + 3 * kept;
+        if (a0 != 0.0f) atomicAdd(d, a0);
+        if (a1 != 0.0f) atomicAdd(d + 1, a1);
+        if (a2 != 0.0f) atomicAdd(d + 2, a2);
+    }
+}
+
+// Opened-leaf point: adds sum over lanes of k g^c into dst[c] for the chunk.
+template <int CH>
+__device__ __forceinline__ void adjoint_point_reduce(float k, const float* gp, float* dst, int kept,
+                                                     int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float a0 = k * gp[0];
+    if constexpr (CH == 4) {
+        float a1 = k * gp[1];
+        a0 += __shfl_xor_sync(FULL, k * gp[2], 16);
+        a1 += __shfl_xor_sync(FULL, k * gp[3], 16);
+        a0 += __shfl_xor_sync(FULL, a1, 8);
+    } else if constexpr (CH == 2) {
+        a0 += __shfl_xor_sync(FULL, k * gp[1], 16);
+    }
+#pragma unroll
+    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1)
+        a0 += __shfl_xor_sync(FULL, a0, off);
+    if (lane_owns<CH>(lane) && a0 != 0.0f) atomicAdd(dst + kept, a0);
+}
+
 }  // namespace dip

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(uint32_t* data, int64
 
 // ------------------------------------------------------------- radix sort
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 4;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -145,7 +145,8 @@ __device__ __forceinline__ uint32_t spread_bits10(uint32_t v) {
 }
 
 __global__ void k_query_codes(const float* __restrict__ q, int64_t nq, const float* __restrict__ bbox,
-                              uint32_t* __restrict__ codes, uint32_t* __restrict__ idx, int* status) {
+                              int shift, uint32_t* __restrict__ codes, uint32_t* __restrict__ idx,
+                              int* status) {
     const float lo0 = bbox[0], lo1 = bbox[1], lo2 = bbox[2], s = bbox[4];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -155,7 +156,7 @@ __global__ void k_query_codes(const float* __restrict__ q, int64_t nq, const flo
         uint32_t qx = min(__float2uint_rz(__fmul_rn(__fsub_rn(x, lo0), s)), 1023u);
         uint32_t qy = min(__float2uint_rz(__fmul_rn(__fsub_rn(y, lo1), s)), 1023u);
         uint32_t qz = min(__float2uint_rz(__fmul_rn(__fsub_rn(z, lo2), s)), 1023u);
-        codes[i] = (spread_bits10(qx) << 2) | (spread_bits10(qy) << 1) | spread_bits10(qz);
+        codes[i] = ((spread_bits10(qx) << 2) | (spread_bits10(qy) << 1) | spread_bits10(qz)) >> shift;
         idx[i] = (uint32_t)i;
     }
 }
@@ -227,13 +228,13 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
     }
 }
 
-void query_codes(const float* queries, int64_t q, const float* bbox, uint32_t* codes,
+void query_codes(const float* queries, int64_t q, const float* bbox, int shift, uint32_t* codes,
                  uint32_t* idx, int* status, cudaStream_t s) {
     if (q <= 0) return;
     int64_t blocks = (q + 255) / 256;
     int64_t cap = (int64_t)num_sms() * 8;
-    note_launch(); k_query_codes<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(queries, q, bbox, codes,
-                                                                           idx, status);
+    note_launch(); k_query_codes<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(queries, q, bbox, shift,
+                                                                           codes, idx, status);
 }
 
 }  // namespace dip

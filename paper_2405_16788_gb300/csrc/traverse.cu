@@ -78,7 +78,8 @@ __device__ __forceinline__ void load_row<__nv_bfloat16>(const __nv_bfloat16* p, 
 }
 
 template <int CP, typename AT, int MODE>
-__global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
+__global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
+k_query(const QueryArgs a) {
     constexpr int SR = srow(CP);
     constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
     constexpr unsigned FULL = 0xffffffffu;
@@ -115,9 +116,25 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
                 for (int c = 0; c < CP; ++c) part[c] = 0.f;
             }
         }
+        // adjoint: the upstream gradient, scaled by 1/(4 pi) and put into each
+        // chunk's lane_channel_order (see adjoint_far_reduce)
+        int ord[CH];
+        lane_channel_order<CH>(lane, ord);
         if (MODE == kAdjoint) {
 #pragma unroll
-            for (int c = 0; c < CP; ++c) g[c] = (valid && c < a.C) ? a.g[qo * a.C + c] * kInv4Pi : 0.f;
+            for (int c0 = 0; c0 < CP; c0 += CH) {
+                float gc[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    gc[c] = (valid && c0 + c < a.C) ? a.g[qo * a.C + c0 + c] * kInv4Pi : 0.f;
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    float v = gc[0];
+#pragma unroll
+                    for (int c = 1; c < CH; ++c) v = (ord[i] == c) ? gc[c] : v;
+                    g[c0 + i] = v;
+                }
+            }
         }
         auto add_term = [&](int c, float v) {
             if (MODE == kForward) {
@@ -182,16 +199,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
                         // eq. farfield_gradient: dS_t^c += rho (p~ - x)/d^3 g^c
                         float* dst = a.dS + (size_t)n * SR;
 #pragma unroll
-                        for (int c0 = 0; c0 < CP; c0 += CH) {
-                            float v[3 * CH];
-#pragma unroll
-                            for (int c = 0; c < CH; ++c) {
-                                v[3 * c] = vx * g[c0 + c];
-                                v[3 * c + 1] = vy * g[c0 + c];
-                                v[3 * c + 2] = vz * g[c0 + c];
-                            }
-                            warp_reduce_add<3 * CH>(v, dst + 3 * c0, lane);
-                        }
+                        for (int c0 = 0; c0 < CP; c0 += CH)
+                            adjoint_far_reduce<CH>(vx, vy, vz, g + c0, dst + 3 * c0, ord[0], lane);
                     }
                 }
 
@@ -221,12 +230,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(const QueryArgs a) {
                         } else if (MODE == kAdjoint) {
                             float* dst = a.dmu + (size_t)(f + j) * CP;
 #pragma unroll
-                            for (int c0 = 0; c0 < CP; c0 += CH) {
-                                float v[CH];
-#pragma unroll
-                                for (int c = 0; c < CH; ++c) v[c] = k * g[c0 + c];
-                                warp_reduce_add<CH>(v, dst + c0, lane);
-                            }
+                            for (int c0 = 0; c0 < CP; c0 += CH)
+                                adjoint_point_reduce<CH>(k, g + c0, dst + c0, ord[0], lane);
                         }
                     }
                 }
@@ -352,10 +357,10 @@ int dispatch(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
 // Scratch of dipole_forward_noalloc: the query sort (codes, indices, their
 // ping-pong copies, the radix histograms with their scan space) and the work
 // counter, for at most kNoAllocMaxQueries queries.  A file-scope device array:
-// every GPU that loads this library holds it (about 4.2 MB) until the process
+// every GPU that loads this library holds it (about 4.5 MB) until the process
 // exits; nothing is allocated per call.
 constexpr int64_t kNoAllocMaxQueries = int64_t(1) << 18;
-constexpr int64_t kNoAllocHistEntries = (kNoAllocMaxQueries / 4096) * 256 + 4096;
+constexpr int64_t kNoAllocHistEntries = (kNoAllocMaxQueries / 1024) * 256 + 4096;
 constexpr size_t kNoAllocBytes =
     4 * sizeof(uint32_t) * (size_t)kNoAllocMaxQueries + sizeof(uint32_t) * (size_t)kNoAllocHistEntries + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -401,8 +406,8 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     unsigned long long* work = reinterpret_cast<unsigned long long*>(hist + kNoAllocHistEntries);
     // the previous call's contents stay in the array: only the counter must start at 0
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
-    query_codes(queries, q, t->bbox, codes, idx, t->status, s);
-    radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, 30, s);
+    query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+    radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
     QueryArgs a;
     a.nodes = t->nodes;
     a.pts = t->pts;
@@ -441,8 +446,8 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         DIP_CUDA_TRY(cudaMallocAsync((void**)&ktmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
-        query_codes(queries, q, t->bbox, codes, idx, t->status, s);
-        radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, 30, s);
+        query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+        radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
     }
     // Longest-first packet order (the codes/ktmp/vtmp buffers are free again).
     const int64_t np = (q + 31) / 32;

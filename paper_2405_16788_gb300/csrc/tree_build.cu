@@ -383,7 +383,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
 
     note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
     note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
-    query_codes(points, n, t->bbox, t->code, t->perm, t->status, s);
+    query_codes(points, n, t->bbox, 0, t->code, t->perm, t->status, s);
     radix_sort_pairs(t->code, t->perm, ktmp, vtmp, hist, n, 30, s);
     note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
                                                       t->pts);
