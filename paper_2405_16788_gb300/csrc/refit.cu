@@ -25,18 +25,17 @@ __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// Bottom-up: a leaf thread gathers its points' attributes into Morton order,
-// sums its moments in float, then climbs while it is the last child to finish;
-// an internal node sums its children in order, in double when it holds at
-// least kBigNode points.
+// Bottom-up in two kinds of launches: every leaf gathers its points'
+// attributes into Morton order and sums its moments in float; then, level by
+// level from the deepest, every internal node sums its children in order, in
+// double when it holds at least kBigNode points.
 template <int CP, typename AT>
-__global__ void __launch_bounds__(128) k_refit(
+__global__ void __launch_bounds__(128) k_refit_leaves(
     int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-    const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ parent,
-    const int32_t* __restrict__ nchild, const int32_t* __restrict__ skip,
-    const int32_t* __restrict__ big_idx, const AT* __restrict__ attrs, int C,
-    unsigned int* arrive, AT* __restrict__ mu, float* S, double* S64) {
+    const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ big_idx,
+    const AT* __restrict__ attrs, int C, AT* __restrict__ mu, float* __restrict__ S,
+    double* __restrict__ S64) {
     constexpr int SR = srow(CP);
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < nn;
          t0 += (int64_t)gridDim.x * blockDim.x) {
@@ -50,77 +49,81 @@ __global__ void __launch_bounds__(128) k_refit(
         const int32_t bl = big_idx[t0];
 #pragma unroll
         for (int c0 = 0; c0 < CP; c0 += 4) {
-            float s[12];
+            float sacc[12];
 #pragma unroll
-            for (int j = 0; j < 12; ++j) s[j] = 0.0f;
+            for (int j = 0; j < 12; ++j) sacc[j] = 0.0f;
             for (int64_t m = f; m < f + k; ++m) {
                 const float4 w = pts[m].w;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c0 + c >= CP) break;
                     const float v = to_f<AT>(mu[m * CP + c0 + c]);
-                    s[3 * c] = fmaf(w.x, v, s[3 * c]);
-                    s[3 * c + 1] = fmaf(w.y, v, s[3 * c + 1]);
-                    s[3 * c + 2] = fmaf(w.z, v, s[3 * c + 2]);
+                    sacc[3 * c] = fmaf(w.x, v, sacc[3 * c]);
+                    sacc[3 * c + 1] = fmaf(w.y, v, sacc[3 * c + 1]);
+                    sacc[3 * c + 2] = fmaf(w.z, v, sacc[3 * c + 2]);
                 }
             }
 #pragma unroll
             for (int j = 0; j < 12; ++j) {
                 if (3 * c0 + j >= 3 * CP) break;
-                S[t0 * SR + 3 * c0 + j] = s[j];
-                if (bl >= 0) S64[(int64_t)bl * SR + 3 * c0 + j] = (double)s[j];
+                S[t0 * SR + 3 * c0 + j] = sacc[j];
+                if (bl >= 0) S64[(int64_t)bl * SR + 3 * c0 + j] = (double)sacc[j];
             }
         }
-        __threadfence();
-        int64_t t = t0;
-        for (;;) {
-            const int32_t p = parent[t];
-            if (p < 0) break;
-            if (atomicAdd(&arrive[p], 1u) != (unsigned)(nchild[p] - 1)) break;
-            __threadfence();
-            const int32_t bp = big_idx[p];
-            const int32_t end = skip[p];
+    }
+}
+
+template <int CP>
+__global__ void __launch_bounds__(128) k_refit_level(int l, const int32_t* __restrict__ lvl_off,
+                                                     const int32_t* __restrict__ lvl_list,
+                                                     const int32_t* __restrict__ skip,
+                                                     const int32_t* __restrict__ big_idx,
+                                                     float* __restrict__ S, double* __restrict__ S64) {
+    constexpr int SR = srow(CP);
+    const int32_t b = lvl_off[l], e = lvl_off[l + 1];
+    for (int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = lvl_list[i];
+        const int32_t bp = big_idx[p];
+        const int32_t end = skip[p];
 #pragma unroll 1
-            for (int j0 = 0; j0 < 3 * CP; j0 += 12) {
-                if (bp >= 0) {
-                    double q[12];
+        for (int j0 = 0; j0 < 3 * CP; j0 += 12) {
+            if (bp >= 0) {
+                double q[12];
 #pragma unroll
-                    for (int j = 0; j < 12; ++j) q[j] = 0.0;
-                    for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
-                        const int32_t bc = big_idx[ch];
-#pragma unroll
-                        for (int j = 0; j < 12; ++j) {
-                            if (j0 + j >= 3 * CP) break;
-                            q[j] += bc >= 0 ? __ldcg(&S64[(int64_t)bc * SR + j0 + j])
-                                            : (double)__ldcg(&S[(int64_t)ch * SR + j0 + j]);
-                        }
-                    }
+                for (int j = 0; j < 12; ++j) q[j] = 0.0;
+                for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
+                    const int32_t bc = big_idx[ch];
 #pragma unroll
                     for (int j = 0; j < 12; ++j) {
                         if (j0 + j >= 3 * CP) break;
-                        S64[(int64_t)bp * SR + j0 + j] = q[j];
-                        S[(int64_t)p * SR + j0 + j] = (float)q[j];
-                    }
-                } else {
-                    float q[12];
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) q[j] = 0.0f;
-                    for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
-#pragma unroll
-                        for (int j = 0; j < 12; ++j) {
-                            if (j0 + j >= 3 * CP) break;
-                            q[j] += __ldcg(&S[(int64_t)ch * SR + j0 + j]);
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        if (j0 + j >= 3 * CP) break;
-                        S[(int64_t)p * SR + j0 + j] = q[j];
+                        q[j] += bc >= 0 ? S64[(int64_t)bc * SR + j0 + j]
+                                        : (double)S[(int64_t)ch * SR + j0 + j];
                     }
                 }
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    if (j0 + j >= 3 * CP) break;
+                    S64[(int64_t)bp * SR + j0 + j] = q[j];
+                    S[(int64_t)p * SR + j0 + j] = (float)q[j];
+                }
+            } else {
+                float q[12];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) q[j] = 0.0f;
+                for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        if (j0 + j >= 3 * CP) break;
+                        q[j] += S[(int64_t)ch * SR + j0 + j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    if (j0 + j >= 3 * CP) break;
+                    S[(int64_t)p * SR + j0 + j] = q[j];
+                }
             }
-            __threadfence();
-            t = p;
         }
     }
 }
@@ -174,9 +177,16 @@ template <int CP, typename AT>
 void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     int64_t blocks = (t->nn + 127) / 128;
     int64_t cap = (int64_t)num_sms() * 16;
-    note_launch(); k_refit<CP, AT><<<(unsigned)(blocks < cap ? blocks : cap), 128, 0, s>>>(
-        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, t->nchild, t->skip,
-        t->big_idx, (const AT*)attrs, t->C, t->arrive, (AT*)t->mu, t->S, t->S64);
+    const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+    note_launch();
+    k_refit_leaves<CP, AT><<<grid, 128, 0, s>>>(t->nn, t->pts, t->perm, t->first, t->count,
+                                                t->is_leaf, t->big_idx, (const AT*)attrs, t->C,
+                                                (AT*)t->mu, t->S, t->S64);
+    for (int l = t->max_depth - 1; l >= 0; --l) {
+        note_launch();
+        k_refit_level<CP><<<grid, 128, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip, t->big_idx,
+                                                t->S, t->S64);
+    }
 }
 
 template <int CP>
@@ -205,18 +215,16 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
     const int SR = srow(Cp);
     if (t->attr_Cp_alloc != Cp || t->attr_dtype_alloc != dtype) {
         // (re)allocate the attribute state; previous buffers are freed in stream order
-        void* bufs[] = {t->mu, t->S, t->S64, t->dS, t->dmu, t->arrive};
+        void* bufs[] = {t->mu, t->S, t->S64, t->dS, t->dmu};
         for (void* b : bufs)
             if (b) cudaFreeAsync(b, s);
         t->mu = nullptr; t->S = nullptr; t->S64 = nullptr; t->dS = nullptr; t->dmu = nullptr;
-        t->arrive = nullptr;
         const size_t esz = dtype == 1 ? 2 : 4;
         DIP_CUDA_TRY(cudaMallocAsync(&t->mu, esz * (size_t)t->n * Cp, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S64, sizeof(double) * (size_t)(t->nbig + 1) * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dS, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dmu, sizeof(float) * (size_t)t->n * Cp, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->arrive, sizeof(unsigned int) * (size_t)t->nn, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)t->nn * SR, s));
         t->attr_Cp_alloc = Cp;
         t->attr_dtype_alloc = dtype;
@@ -224,7 +232,6 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
     t->C = C;
     t->Cp = Cp;
     t->dtype = dtype;
-    DIP_CUDA_TRY(cudaMemsetAsync(t->arrive, 0, sizeof(unsigned int) * (size_t)t->nn, s));
 #define DIP_REFIT_CASE(K)                                                          \
     case K:                                                                        \
         if (dtype == 1) launch_refit<K, __nv_bfloat16>(t, attrs, s);               \

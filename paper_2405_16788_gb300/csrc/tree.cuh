@@ -27,6 +27,8 @@ struct dipole_tree {
     int32_t* is_leaf = nullptr;
     int32_t* nchild = nullptr;
     int32_t* big_idx = nullptr;  // index into S64 for nodes with >= kBigNode points, else -1
+    int32_t* lvl_list = nullptr; // internal nodes grouped by level
+    int32_t* lvl_off = nullptr;  // [kMaxLevel + 2] start of each level in lvl_list
     int64_t nbig = 0;
     double* agg64 = nullptr;     // [nn, 5] sum A, sum A p (3), sum A eps
     float* eps_node = nullptr;   // [nn]
@@ -43,7 +45,6 @@ struct dipole_tree {
     double* S64 = nullptr;       // [nbig, 3 Cp]
     float* dS = nullptr;         // [nn, 3 Cp] adjoint node accumulators
     float* dmu = nullptr;        // [n, Cp] adjoint opened-leaf accumulators
-    uint32_t* arrive = nullptr;  // [nn] bottom-up arrival counters
     int attr_Cp_alloc = 0;
     int attr_dtype_alloc = -1;
 

@@ -75,15 +75,17 @@ __global__ void __launch_bounds__(kThreads) k_bbox_partial(const float* __restri
 
 // Bounding cube: lo = per-axis minimum; ext = largest per-axis extent (float
 // subtraction), 1 if 0; scale = 1024 / ext (correctly rounded division).
+// One warp reduces the per-block partials.
 __global__ void k_bbox_final(const float* partial, int nb, float* bbox) {
-    if (threadIdx.x != 0) return;
-    float lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) { lo[a] = partial[a]; hi[a] = partial[3 + a]; }
-    for (int b = 1; b < nb; ++b)
+    const int lane = threadIdx.x & 31;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int b = lane; b < nb; b += 32)
         for (int a = 0; a < 3; ++a) {
             lo[a] = fminf(lo[a], partial[b * 6 + a]);
             hi[a] = fmaxf(hi[a], partial[b * 6 + 3 + a]);
         }
+    for (int a = 0; a < 3; ++a) { lo[a] = warp_min(lo[a]); hi[a] = warp_max(hi[a]); }
+    if (lane != 0) return;
     float ext = 0.0f;
     for (int a = 0; a < 3; ++a) {
         float e = __fsub_rn(hi[a], lo[a]);
@@ -235,10 +237,42 @@ __global__ void k_children(int64_t nn, const int32_t* __restrict__ skip,
     }
 }
 
+// Internal nodes grouped by level (the order inside a level is arbitrary):
+// count, offsets, then one slot per node.  Bottom-up passes process the leaves
+// first, then the internal levels from the deepest to the root, one launch per
+// level, so a node's children are always complete before it is summed.
+__global__ void k_level_count(int64_t nn, const int32_t* __restrict__ level,
+                              const int32_t* __restrict__ is_leaf, unsigned int* lvl_cnt) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x)
+        if (!is_leaf[t]) atomicAdd(&lvl_cnt[level[t]], 1u);
+}
+
+__global__ void k_level_offsets(const unsigned int* lvl_cnt, int32_t* lvl_off, unsigned int* lvl_fill) {
+    if (threadIdx.x != 0) return;
+    int32_t run = 0;
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        lvl_off[l] = run;
+        lvl_fill[l] = 0;
+        run += (int32_t)lvl_cnt[l];
+    }
+    lvl_off[kMaxLevel + 1] = run;
+}
+
+__global__ void k_level_fill(int64_t nn, const int32_t* __restrict__ level,
+                             const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ lvl_off,
+                             unsigned int* lvl_fill, int32_t* __restrict__ lvl_list) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (is_leaf[t]) continue;
+        const int l = level[t];
+        lvl_list[lvl_off[l] + (int32_t)atomicAdd(&lvl_fill[l], 1u)] = (int32_t)t;
+    }
+}
+
 // Node sums in double: point by point inside a leaf, child by child inside an
 // internal node, both in Morton order, so that the float centroid is the
-// same on any machine.  Each leaf thread climbs while it is the last child to
-// finish (arrival counters).
+// same on any machine.
 __device__ __forceinline__ void finalize_geom(int64_t t, const double* s, float4* cen4,
                                               float* eps_node) {
     double sa = s[0];
@@ -248,17 +282,16 @@ __device__ __forceinline__ void finalize_geom(int64_t t, const double* s, float4
     eps_node[t] = __double2float_rn(__ddiv_rn(s[4], sa));
 }
 
-__global__ void k_geom(int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
-                       const float* __restrict__ radii, const int32_t* __restrict__ first,
-                       const int32_t* __restrict__ count, const int32_t* __restrict__ is_leaf,
-                       const int32_t* __restrict__ parent, const int32_t* __restrict__ nchild,
-                       const int32_t* __restrict__ skip, unsigned int* arrive, double* agg,
-                       float4* cen4, float* eps_node) {
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < nn;
-         t0 += (int64_t)gridDim.x * blockDim.x) {
-        if (!is_leaf[t0]) continue;
+__global__ void k_geom_leaves(int64_t nn, const PointRec* __restrict__ pts,
+                              const uint32_t* __restrict__ perm, const float* __restrict__ radii,
+                              const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+                              const int32_t* __restrict__ is_leaf, double* __restrict__ agg,
+                              float4* __restrict__ cen4, float* __restrict__ eps_node) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (!is_leaf[t]) continue;
         double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        const int64_t f = first[t0], k = count[t0];
+        const int64_t f = first[t], k = count[t];
         for (int64_t m = f; m < f + k; ++m) {
             const float4 g = pts[m].geo;
             const double a = (double)pts[m].w.w;
@@ -270,26 +303,27 @@ __global__ void k_geom(int64_t nn, const PointRec* __restrict__ pts, const uint3
             s[4] = __dadd_rn(s[4], __dmul_rn(a, e));
         }
 #pragma unroll
-        for (int j = 0; j < 5; ++j) agg[t0 * 5 + j] = s[j];
-        finalize_geom(t0, s, cen4, eps_node);
-        __threadfence();
-        int64_t t = t0;
-        for (;;) {
-            const int32_t p = parent[t];
-            if (p < 0) break;
-            if (atomicAdd(&arrive[p], 1u) != (unsigned)(nchild[p] - 1)) break;
-            __threadfence();
-            double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int32_t ch = p + 1; ch < skip[p]; ch = skip[ch]) {
+        for (int j = 0; j < 5; ++j) agg[t * 5 + j] = s[j];
+        finalize_geom(t, s, cen4, eps_node);
+    }
+}
+
+__global__ void k_geom_level(int l, const int32_t* __restrict__ lvl_off,
+                             const int32_t* __restrict__ lvl_list, const int32_t* __restrict__ skip,
+                             double* __restrict__ agg, float4* __restrict__ cen4,
+                             float* __restrict__ eps_node) {
+    const int32_t b = lvl_off[l], e = lvl_off[l + 1];
+    for (int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = lvl_list[i];
+        double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int32_t ch = p + 1; ch < skip[p]; ch = skip[ch]) {
 #pragma unroll
-                for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], __ldcg(&agg[(int64_t)ch * 5 + j]));
-            }
-#pragma unroll
-            for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
-            finalize_geom(p, q, cen4, eps_node);
-            __threadfence();
-            t = p;
+            for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], agg[(int64_t)ch * 5 + j]);
         }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
+        finalize_geom(p, q, cen4, eps_node);
     }
 }
 
@@ -373,7 +407,8 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     // temporaries
     uint32_t *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr, *off = nullptr, *scan_tmp = nullptr;
     float* partial = nullptr;
-    const unsigned nbb = grid_for(n, kThreads);
+    const unsigned nbb = grid_for(n, kThreads) < 2u * (unsigned)num_sms() ? grid_for(n, kThreads)
+                                                                          : 2u * (unsigned)num_sms();
     DIP_CUDA_TRY(dalloc(&ktmp, n, s));
     DIP_CUDA_TRY(dalloc(&vtmp, n, s));
     DIP_CUDA_TRY(dalloc(&hist, radix_hist_entries(n), s));
@@ -430,11 +465,13 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
     DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
     float4* cen4 = nullptr;
-    unsigned int *rbits = nullptr, *arrive = nullptr, *nbig = nullptr;
+    unsigned int *rbits = nullptr, *nbig = nullptr, *lvl_cnt = nullptr;
     DIP_CUDA_TRY(dalloc(&cen4, nn, s));
     DIP_CUDA_TRY(dalloc(&rbits, nn, s));
-    DIP_CUDA_TRY(dalloc(&arrive, nn, s));
     DIP_CUDA_TRY(dalloc(&nbig, 1, s));
+    DIP_CUDA_TRY(dalloc(&lvl_cnt, 2 * (kMaxLevel + 1), s));
+    DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
 
     note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size, t->max_depth,
                                                            off, t->first, t->count, t->level,
@@ -442,11 +479,19 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
     note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
                                                            t->nchild, t->status);
-    DIP_CUDA_TRY(cudaMemsetAsync(arrive, 0, sizeof(unsigned int) * nn, s));
-    note_launch(); k_geom<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->pts, t->perm, radii, t->first,
-                                                       t->count, t->is_leaf, t->parent, t->nchild,
-                                                       t->skip, arrive, t->agg64, cen4,
-                                                       t->eps_node);
+    DIP_CUDA_TRY(cudaMemsetAsync(lvl_cnt, 0, sizeof(unsigned int) * (kMaxLevel + 1), s));
+    note_launch(); k_level_count<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->level, t->is_leaf,
+                                                                            lvl_cnt);
+    note_launch(); k_level_offsets<<<1, 32, 0, s>>>(lvl_cnt, t->lvl_off, lvl_cnt + kMaxLevel + 1);
+    note_launch(); k_level_fill<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
+        nn, t->level, t->is_leaf, t->lvl_off, lvl_cnt + kMaxLevel + 1, t->lvl_list);
+    note_launch(); k_geom_leaves<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
+        nn, t->pts, t->perm, radii, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
+    for (int l = t->max_depth - 1; l >= 0; --l) {
+        note_launch();
+        k_geom_level<<<grid_for(nn, kThreads), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
+                                                                 t->agg64, cen4, t->eps_node);
+    }
     DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
     note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
                                                         rbits);
@@ -458,7 +503,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     free_tmp();
     cudaFreeAsync(cen4, s);
     cudaFreeAsync(rbits, s);
-    cudaFreeAsync(arrive, s);
+    cudaFreeAsync(lvl_cnt, s);
     cudaFreeAsync(nbig, s);
     DIP_CUDA_TRY(cudaGetLastError());
     // Nodes of one level are disjoint, so each level has at most n / kBigNode
