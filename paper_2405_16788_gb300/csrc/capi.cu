@@ -37,6 +37,8 @@ void free_tree_memory(dipole_tree* t) {
                     t->S,      t->S64,     t->dS,     t->dmu,     t->lvl_list, t->lvl_off};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    delete t->sched;
+    t->sched = nullptr;
 }
 
 int status_to_code(int st) {

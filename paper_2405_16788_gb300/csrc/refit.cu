@@ -184,7 +184,7 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
                                                 (AT*)t->mu, t->S, t->S64);
     for (int l = t->max_depth - 1; l >= 0; --l) {
         note_launch();
-        k_refit_level<CP><<<grid, 128, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip, t->big_idx,
+        k_refit_level<CP><<<4u * (unsigned)num_sms(), 128, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip, t->big_idx,
                                                 t->S, t->S64);
     }
 }

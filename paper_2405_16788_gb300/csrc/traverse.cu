@@ -45,6 +45,7 @@ struct QueryArgs {
     int32_t* counts;
     unsigned long long* work;
     const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
+    uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
 };
 
 template <typename AT>
@@ -93,7 +94,8 @@ k_query(const QueryArgs a) {
         if (lane == 0) pk = atomicAdd(a.work, 1ull);
         pk = __shfl_sync(FULL, pk, 0);
         if ((int64_t)pk * 32 >= a.nq) break;
-        const int64_t base = (int64_t)(a.porder ? a.porder[pk] : pk) * 32;
+        const int64_t pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
+        const int64_t base = pm * 32;
         const int64_t qi = base + lane;
         const bool valid = qi < a.nq;
         const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
@@ -249,6 +251,7 @@ k_query(const QueryArgs a) {
             for (int c = 0; c < CP; ++c) kahan_add(acc[c], cmp[c], part[c]);
         }
 
+        if (a.pcost && lane == 0) a.pcost[pm] = 0xffffu - (steps < 0xffffu ? steps : 0xffffu);
         if (valid) {
             if (MODE == kForward) {
 #pragma unroll
@@ -263,50 +266,10 @@ k_query(const QueryArgs a) {
     }
 }
 
-// Cost estimate of each 32-query packet for longest-first scheduling: four of
-// its queries (lanes 0, 10, 21, 31) walk the tree alone with the same far test;
-// each counts its steps plus twice its leaf points and the packet takes the
-// largest.  Key = 65535 - cost, so an ascending sort puts the most expensive
-// packets first.  Four consecutive threads handle one packet.
-__global__ void k_packet_cost(const NodeRec* __restrict__ nodes, unsigned nn,
-                              const float* __restrict__ q, const uint32_t* __restrict__ qperm,
-                              int64_t nq, float beta, uint32_t* __restrict__ key,
-                              uint32_t* __restrict__ val) {
-    const int64_t np = (nq + 31) / 32;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < 4 * np; i0 += stride) {
-        const int64_t i = i0 + threadIdx.x;  // the whole warp iterates together
-        const int64_t p = i >> 2;
-        unsigned cost = 0;
-        if (p < np) {
-            const int sub = (int)(i & 3);
-            int64_t qi = p * 32 + (sub == 0 ? 0 : sub == 1 ? 10 : sub == 2 ? 21 : 31);
-            if (qi >= nq) qi = nq - 1;
-            const int64_t qo = qperm[qi];
-            const float x0 = q[3 * qo], x1 = q[3 * qo + 1], x2 = q[3 * qo + 2];
-            unsigned n = 0;
-            while (n < nn && cost < 65535u) {
-                const float4 geo = __ldg(&nodes[n].geo);
-                const int4 meta = __ldg(&nodes[n].meta);
-                const float dx = __fsub_rn(x0, geo.x), dy = __fsub_rn(x1, geo.y), dz = __fsub_rn(x2, geo.z);
-                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                const float R = __fmul_rn(beta, geo.w);
-                const bool far = d2 > __fmul_rn(R, R);
-                ++cost;
-                if (!far && meta.z > 0) cost += 2u * (unsigned)meta.z;
-                const unsigned nx = (far || meta.z > 0) ? (unsigned)meta.x : n + 1u;
-                if (nx <= n) break;  // corrupt tree: the traversal kernel reports it
-                n = nx;
-            }
-            if (cost > 65535u) cost = 65535u;
-        }
-        cost = max(cost, __shfl_xor_sync(0xffffffffu, cost, 1));
-        cost = max(cost, __shfl_xor_sync(0xffffffffu, cost, 2));
-        if (p < np && (i & 3) == 0) {
-            key[p] = 65535u - cost;
-            val[p] = (uint32_t)p;
-        }
-    }
+__global__ void k_iota(uint32_t* v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (uint32_t)i;
 }
 
 // Packets below this count are too few for the queue's tail to matter.
@@ -426,7 +389,8 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.dmu = nullptr;
     a.counts = nullptr;
     a.work = work;
-    a.porder = nullptr;  // Morton packet order: no scratch for the longest-first sort
+    a.porder = nullptr;  // Morton packet order
+    a.pcost = nullptr;
     rc = dispatch<kForward>(t, a, s);
     if (rc) return rc;
     DIP_CUDA_TRY(cudaGetLastError());
@@ -449,16 +413,29 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
         radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
     }
-    // Longest-first packet order (the codes/ktmp/vtmp buffers are free again).
+    // Scheduling.  The forward runs packets in Morton order and records each
+    // packet's warp steps; an adjoint on the same queries (the case in every
+    // training step) runs the packets longest first from that record.  A stale
+    // record only changes the order, never a result.
     const int64_t np = (q + 31) / 32;
     const uint32_t* porder = nullptr;
+    uint32_t* pcost = nullptr;
     if (np >= kOrderMinPackets && mode != kCount) {
-        int64_t blocks = (4 * np + 127) / 128;
-        note_launch();
-        k_packet_cost<<<(unsigned)blocks, 128, 0, s>>>(t->nodes, (unsigned)t->nn, queries, idx, q,
-                                                        beta, codes, ktmp);
-        radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
-        porder = ktmp;
+        std::lock_guard<std::mutex> lock(t->sched->mu);
+        if (mode == kForward) {
+            if (t->sched->ensure(np)) {
+                pcost = t->sched->cost;
+                t->sched->queries = queries;
+                t->sched->q = q;
+            }
+        } else if (t->sched->queries == queries && t->sched->q == q && t->sched->cost) {
+            DIP_CUDA_TRY(cudaMemcpyAsync(codes, t->sched->cost, sizeof(uint32_t) * np,
+                                         cudaMemcpyDeviceToDevice, s));
+            note_launch();
+            k_iota<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(ktmp, np);
+            radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
+            porder = ktmp;
+        }
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (mode == kAdjoint) {
@@ -486,6 +463,7 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         a.counts = counts;
         a.work = work;
         a.porder = porder;
+        a.pcost = pcost;
         if (mode == kForward) rc = dispatch<kForward>(t, a, s);
         else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
         else rc = dispatch<kCount>(t, a, s);

@@ -2,7 +2,40 @@
 // of the build, refit and query kernels.
 #pragma once
 
+#include <mutex>
+
 #include "common.cuh"
+
+namespace dip {
+// Scheduling record of the last forward query batch: per-packet warp steps,
+// written by the forward kernel, read by an adjoint on the same queries.  A
+// performance hint only; guarded for concurrent forward calls.
+struct SchedRecord {
+    std::mutex mu;
+    uint32_t* cost = nullptr;  // allocated at tree build (stream ordered), grown synchronously
+    int64_t cap = 0;
+    const float* queries = nullptr;
+    int64_t q = -1;
+    // Capacity for np packets.  Growing frees the old buffer with cudaFree,
+    // which first waits for the device, so no kernel still reads it.
+    bool ensure(int64_t np) {
+        if (np <= cap) return true;
+        if (cost) cudaFree(cost);
+        cost = nullptr;
+        cap = 0;
+        queries = nullptr;
+        if (cudaMalloc((void**)&cost, sizeof(uint32_t) * (size_t)np) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cap = np;
+        return true;
+    }
+    ~SchedRecord() {
+        if (cost) cudaFree(cost);
+    }
+};
+}  // namespace dip
 
 struct dipole_tree {
     int device = 0;
@@ -35,6 +68,7 @@ struct dipole_tree {
     float* bbox = nullptr;       // device: lo.xyz, ext, 1024/ext
     float bbox_host[5] = {0, 0, 0, 1, 1024};
     int* status = nullptr;       // device status word
+    dip::SchedRecord* sched = new dip::SchedRecord();
 
     // attributes (set by refit)
     int C = 0;

@@ -17,6 +17,8 @@
 
 #include <float.h>
 
+#include <algorithm>
+
 namespace dip {
 namespace {
 
@@ -243,9 +245,14 @@ __global__ void k_children(int64_t nn, const int32_t* __restrict__ skip,
 // level, so a node's children are always complete before it is summed.
 __global__ void k_level_count(int64_t nn, const int32_t* __restrict__ level,
                               const int32_t* __restrict__ is_leaf, unsigned int* lvl_cnt) {
+    __shared__ unsigned int sc[kMaxLevel + 1];
+    if (threadIdx.x <= kMaxLevel) sc[threadIdx.x] = 0;
+    __syncthreads();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
          t += (int64_t)gridDim.x * blockDim.x)
-        if (!is_leaf[t]) atomicAdd(&lvl_cnt[level[t]], 1u);
+        if (!is_leaf[t]) atomicAdd(&sc[level[t]], 1u);
+    __syncthreads();
+    if (threadIdx.x <= kMaxLevel && sc[threadIdx.x]) atomicAdd(&lvl_cnt[threadIdx.x], sc[threadIdx.x]);
 }
 
 __global__ void k_level_offsets(const unsigned int* lvl_cnt, int32_t* lvl_off, unsigned int* lvl_fill) {
@@ -259,14 +266,31 @@ __global__ void k_level_offsets(const unsigned int* lvl_cnt, int32_t* lvl_off, u
     lvl_off[kMaxLevel + 1] = run;
 }
 
+// Each block reserves one range per level, then hands out slots inside it.
+// The grid-stride loop runs the same number of rounds in every thread of a
+// block so that the barriers are uniform.
 __global__ void k_level_fill(int64_t nn, const int32_t* __restrict__ level,
                              const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ lvl_off,
                              unsigned int* lvl_fill, int32_t* __restrict__ lvl_list) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (is_leaf[t]) continue;
-        const int l = level[t];
-        lvl_list[lvl_off[l] + (int32_t)atomicAdd(&lvl_fill[l], 1u)] = (int32_t)t;
+    __shared__ unsigned int sc[kMaxLevel + 1];
+    __shared__ unsigned int sb[kMaxLevel + 1];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nn; base += stride) {
+        if (threadIdx.x <= kMaxLevel) sc[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t t = base + threadIdx.x;
+        int l = -1;
+        unsigned int r = 0;
+        if (t < nn && !is_leaf[t]) {
+            l = level[t];
+            r = atomicAdd(&sc[l], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x <= kMaxLevel && sc[threadIdx.x])
+            sb[threadIdx.x] = atomicAdd(&lvl_fill[threadIdx.x], sc[threadIdx.x]);
+        __syncthreads();
+        if (l >= 0) lvl_list[lvl_off[l] + (int32_t)(sb[l] + r)] = (int32_t)t;
+        __syncthreads();
     }
 }
 
@@ -402,6 +426,10 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(dalloc(&t->leaf_of, n, s));
     DIP_CUDA_TRY(dalloc(&t->bbox, 8, s));
     DIP_CUDA_TRY(dalloc(&t->status, 1, s));
+    // scheduling record of the query kernels: one entry per 32 points covers
+    // query batches up to the point count without growing
+    t->sched->cap = std::max<int64_t>(4096, (n + 31) / 32);
+    DIP_CUDA_TRY(dalloc(&t->sched->cost, t->sched->cap, s));
     DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
 
     // temporaries
@@ -489,7 +517,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
         nn, t->pts, t->perm, radii, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
     for (int l = t->max_depth - 1; l >= 0; --l) {
         note_launch();
-        k_geom_level<<<grid_for(nn, kThreads), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
+        k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
                                                                  t->agg64, cen4, t->eps_node);
     }
     DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
