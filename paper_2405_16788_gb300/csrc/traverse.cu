@@ -158,6 +158,15 @@ k_query(const QueryArgs a) {
             const float4 geo = __ldg(&nodes[n].geo);
             const int4 meta = __ldg(&nodes[n].meta);
             const bool act = next == n;
+            // forward: the node's first moment chunk is loaded before the far test
+            // so that its latency overlaps the test (most visited nodes are far
+            // for some lane)
+            float4 s_first[MODE == kForward ? (3 * CH + 3) / 4 : 1];
+            if (MODE == kForward) {
+                const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR);
+#pragma unroll
+                for (int j = 0; j < (3 * CH + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
+            }
             // far test of Alg. 1 in a fixed float operation order
             const float dx = __fsub_rn(x0, geo.x);
             const float dy = __fsub_rn(x1, geo.y);
@@ -188,7 +197,7 @@ k_query(const QueryArgs a) {
                             float s[3 * CH + 3];
 #pragma unroll
                             for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
-                                const float4 q4 = __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
+                                const float4 q4 = c0 == 0 ? s_first[j] : __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
                                 s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
                             }
 #pragma unroll
