@@ -223,21 +223,23 @@ def measured_traffic(kernel: str):
     return None
 
 
-def l2_probe(torch, dev):
-    """Best-of-10 read bandwidth of one reduction kernel that reads a 32 MB
-    buffer 32 times (a stride-0 view), so the data comes from L2."""
-    a = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device=dev).uniform_()
-    v = a.expand(32, a.numel())
+def l2_probe(torch, dev, dp):
+    """Best-of-10 L2 read bandwidth: one kernel reads a 48 MB buffer (inside the
+    L2) 20 times with L2-only loads (dipole_probe_l2), timed with CUDA events."""
+    buf = torch.empty(12 * 1024 * 1024, dtype=torch.float32, device=dev).uniform_()
+    sink = torch.empty(1024 * torch.cuda.get_device_properties(dev).multi_processor_count,
+                       dtype=torch.float32, device=dev)
+    passes = 20
     for _ in range(3):
-        v.sum()
+        dp.dipole_probe_l2(buf, passes, sink)
     best = 0.0
     for _ in range(10):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        v.sum()
+        dp.dipole_probe_l2(buf, passes, sink)
         e1.record()
         e1.synchronize()
-        best = max(best, v.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        best = max(best, passes * buf.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
     return best
 
 
@@ -352,7 +354,7 @@ def run_ours(args):
     achieved = alg_bytes / (t_dom * 1e-3) / 1e9
     kern = f"k_query<{dp_cp(C)},float,{dom}>"
     tr = measured_traffic(kern)
-    l2 = l2_probe(torch, dev) if rank == 0 else None
+    l2 = l2_probe(torch, dev, dp) if rank == 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,

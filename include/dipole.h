@@ -217,6 +217,16 @@ int dipole_tree_export(const dipole_tree* tree, uint32_t* codes, uint32_t* perm,
                        int32_t* is_leaf, float* centroid, float* radius, double* area,
                        float* eps, float* moments, void* stream);
 
+/*
+ * Diagnostics, not part of the method (the paper has no counterpart): reads
+ * `bytes` of `buf` `passes` times with L2-only loads in one kernel, so that
+ * the caller can time it (a buffer smaller than L2 measures L2 read
+ * bandwidth).  buf 16-byte aligned, bytes a positive multiple of 16; sink is
+ * a device float array of 1024 * (multiprocessor count) entries that receives
+ * one value per thread.  Asynchronous on `stream`.
+ */
+int dipole_probe_l2(const void* buf, int64_t bytes, int32_t passes, float* sink, void* stream);
+
 /* Release the tree and its device memory (synchronizes the device).  NULL is a no-op. */
 void dipole_tree_destroy(dipole_tree* tree);
 

@@ -33,9 +33,10 @@
  *       implementation take identical decisions.  All values are double.
  *   R7  Node sums (area, area-weighted position, area-weighted eps) are formed
  *       in double, point by point inside a leaf and child by child inside an
- *       internal node, both in Morton order.  The node centroid is that ratio
- *       rounded to float; the node radius is the largest float distance from
- *       that float centroid to a point of the node.
+ *       internal node, both in Morton order.  The ratios are taken as the sums
+ *       times the correctly rounded reciprocal of the area; the node centroid
+ *       is that product rounded to float; the node radius is the largest float
+ *       distance from that float centroid to a point of the node.
  *   R8  AS(m) in eq. (farfield_features_gradient) includes the leaf holding m.
  *
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
@@ -281,10 +282,11 @@ static void node_sums(orc_tree* T, int32_t t) {
     T->s_area[t] = sa;
     T->s_ap[3 * t] = sx; T->s_ap[3 * t + 1] = sy; T->s_ap[3 * t + 2] = sz;
     T->s_ae[t] = se;
-    /* eq. (farfield_dipole): A~ = sum A; p~ = sum A p / A~ */
+    /* eq. (farfield_dipole): A~ = sum A; p~ = sum A p / A~, as (sum A p) * (1/A~) (R7) */
     T->area[t] = sa;
-    T->cen[3 * t] = sx / sa; T->cen[3 * t + 1] = sy / sa; T->cen[3 * t + 2] = sz / sa;
-    T->epsn[t] = se / sa; /* R5 */
+    double rs = 1.0 / sa;
+    T->cen[3 * t] = sx * rs; T->cen[3 * t + 1] = sy * rs; T->cen[3 * t + 2] = sz * rs;
+    T->epsn[t] = se * rs; /* R5 */
     for (int a = 0; a < 3; ++a) T->cen32[3 * t + a] = (float)T->cen[3 * t + a];
     /* r~ = max_m |p_m - p~| over the node's points, in float (R7) */
     float r = 0.0f;

@@ -267,6 +267,17 @@ int dipole_tree_export(const dipole_tree* tree, uint32_t* codes, uint32_t* perm,
     return DIPOLE_OK;
 }
 
+int dipole_probe_l2(const void* buf, int64_t bytes, int32_t passes, float* sink, void* stream) {
+    if (!buf || !sink) return dip_fail(DIPOLE_EINVAL, "dipole_probe_l2: buf and sink are required");
+    if (bytes < 16 || (bytes % 16) != 0 || (reinterpret_cast<uintptr_t>(buf) % 16) != 0)
+        return dip_fail(DIPOLE_EINVAL, "dipole_probe_l2: bytes must be a positive multiple of 16 "
+                                       "and buf 16-byte aligned");
+    if (passes < 1) return dip_fail(DIPOLE_EINVAL, "dipole_probe_l2: passes must be >= 1");
+    dip::probe_l2(buf, bytes, passes, sink, as_stream(stream));
+    DIP_CUDA_TRY(cudaGetLastError());
+    return DIPOLE_OK;
+}
+
 void dipole_tree_destroy(dipole_tree* tree) {
     if (!tree) return;
     cudaDeviceSynchronize();

@@ -76,6 +76,9 @@ constexpr int kQueryKeyBits = 16;
 
 int num_sms();
 
+// Read `bytes` of buf `passes` times with L2-only loads (sink: 1024 * SMs floats).
+void probe_l2(const void* buf, int64_t bytes, int passes, float* sink, cudaStream_t s);
+
 // Counts the library's kernel launches (dipole_kernel_launches).
 void note_launch();
 

@@ -161,7 +161,28 @@ __global__ void k_query_codes(const float* __restrict__ q, int64_t nq, const flo
     }
 }
 
+// Bandwidth probe: every thread reads its grid-stride share of `buf` `passes`
+// times with L2-only loads and writes one value so the loads stay live.
+__global__ void k_probe_l2(const float4* __restrict__ buf, int64_t n4, int passes,
+                           float* __restrict__ sink) {
+    float acc = 0.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int p = 0; p < passes; ++p)
+        for (int64_t i = t; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+    sink[t] = acc;
+}
+
 }  // namespace
+
+void probe_l2(const void* buf, int64_t bytes, int passes, float* sink, cudaStream_t s) {
+    note_launch();
+    k_probe_l2<<<4 * num_sms(), 256, 0, s>>>(static_cast<const float4*>(buf), bytes / 16, passes,
+                                             sink);
+}
 
 int num_sms() {
     static int sms = 0;

@@ -101,7 +101,8 @@ __global__ void k_bbox_final(const float* partial, int nb, float* bbox) {
 
 __global__ void k_pack(const uint32_t* __restrict__ perm, const float* __restrict__ p,
                        const float* __restrict__ nrm, const float* __restrict__ A,
-                       const float* __restrict__ eps, int64_t n, PointRec* __restrict__ pts) {
+                       const float* __restrict__ eps, int64_t n, PointRec* __restrict__ pts,
+                       float* __restrict__ eps_sorted) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t m = perm[i];
@@ -112,6 +113,7 @@ __global__ void k_pack(const uint32_t* __restrict__ perm, const float* __restric
         r.w = make_float4(__fmul_rn(a, nrm[3 * m]), __fmul_rn(a, nrm[3 * m + 1]),
                           __fmul_rn(a, nrm[3 * m + 2]), a);
         pts[i] = r;
+        eps_sorted[i] = e;
     }
 }
 
@@ -183,37 +185,47 @@ __device__ uint32_t analyze_point(const uint32_t* __restrict__ c, int64_t n, int
     return mask;
 }
 
+// Per sorted point: the number of nodes whose runs start there (into cnt), the
+// node/internal masks (mask | imask << 16) and, for every level with a node,
+// the end of its run (estage[11 i + l]), so that the emit pass need not search
+// again.
 __global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf_size,
-                             int max_depth, uint32_t* __restrict__ cnt) {
+                             int max_depth, uint32_t* __restrict__ cnt, uint32_t* __restrict__ tmask,
+                             int32_t* __restrict__ estage) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int64_t e[kMaxLevel + 2];
         uint32_t im;
-        cnt[i] = __popc(analyze_point(c, n, i, leaf_size, max_depth, e, &im));
+        const uint32_t mask = analyze_point(c, n, i, leaf_size, max_depth, e, &im);
+        cnt[i] = __popc(mask);
+        tmask[i] = mask | (im << 16);
+        for (int l = 0; l <= max_depth; ++l)
+            if (mask & (1u << l)) estage[i * (kMaxLevel + 1) + l] = (int32_t)e[l];
     }
 }
 
-__global__ void k_topo_emit(const uint32_t* __restrict__ c, int64_t n, int leaf_size,
-                            int max_depth, const uint32_t* __restrict__ off,
+__global__ void k_topo_emit(int64_t n, int max_depth, const uint32_t* __restrict__ off,
+                            const uint32_t* __restrict__ tmask, const int32_t* __restrict__ estage,
                             int32_t* __restrict__ first, int32_t* __restrict__ count,
                             int32_t* __restrict__ level, int32_t* __restrict__ skip,
                             int32_t* __restrict__ is_leaf, int32_t* __restrict__ leaf_of) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t e[kMaxLevel + 2];
-        uint32_t im;
-        uint32_t mask = analyze_point(c, n, i, leaf_size, max_depth, e, &im);
+        const uint32_t mk = tmask[i];
+        const uint32_t mask = mk & 0xffffu, im = mk >> 16;
+        if (!mask) continue;
         uint32_t t = off[i];
         for (int l = 0; l <= max_depth; ++l) {
             if (!(mask & (1u << l))) continue;
+            const int64_t e = estage[i * (kMaxLevel + 1) + l];
             first[t] = (int32_t)i;
-            count[t] = (int32_t)(e[l] - i);
+            count[t] = (int32_t)(e - i);
             level[t] = l;
-            skip[t] = (int32_t)off[e[l]];
+            skip[t] = (int32_t)off[e];
             const bool leaf = !(im & (1u << l));
             is_leaf[t] = leaf ? 1 : 0;
             if (leaf)
-                for (int64_t m = i; m < e[l]; ++m) leaf_of[m] = (int32_t)t;
+                for (int64_t m = i; m < e; ++m) leaf_of[m] = (int32_t)t;
             ++t;
         }
     }
@@ -296,18 +308,19 @@ __global__ void k_level_fill(int64_t nn, const int32_t* __restrict__ level,
 
 // Node sums in double: point by point inside a leaf, child by child inside an
 // internal node, both in Morton order, so that the float centroid is the
-// same on any machine.
+// same on any machine.  The ratios use one correctly rounded reciprocal of
+// the area: p~ = (sum A p) * (1 / sum A), eps~ = (sum A eps) * (1 / sum A).
 __device__ __forceinline__ void finalize_geom(int64_t t, const double* s, float4* cen4,
                                               float* eps_node) {
-    double sa = s[0];
-    double cx = __ddiv_rn(s[1], sa), cy = __ddiv_rn(s[2], sa), cz = __ddiv_rn(s[3], sa);
+    const double r = __drcp_rn(s[0]);
+    const double cx = __dmul_rn(s[1], r), cy = __dmul_rn(s[2], r), cz = __dmul_rn(s[3], r);
     cen4[t] = make_float4(__double2float_rn(cx), __double2float_rn(cy), __double2float_rn(cz),
                           0.0f);
-    eps_node[t] = __double2float_rn(__ddiv_rn(s[4], sa));
+    eps_node[t] = __double2float_rn(__dmul_rn(s[4], r));
 }
 
 __global__ void k_geom_leaves(int64_t nn, const PointRec* __restrict__ pts,
-                              const uint32_t* __restrict__ perm, const float* __restrict__ radii,
+                              const float* __restrict__ eps_sorted,
                               const int32_t* __restrict__ first, const int32_t* __restrict__ count,
                               const int32_t* __restrict__ is_leaf, double* __restrict__ agg,
                               float4* __restrict__ cen4, float* __restrict__ eps_node) {
@@ -319,7 +332,7 @@ __global__ void k_geom_leaves(int64_t nn, const PointRec* __restrict__ pts,
         for (int64_t m = f; m < f + k; ++m) {
             const float4 g = pts[m].geo;
             const double a = (double)pts[m].w.w;
-            const double e = radii ? (double)radii[perm[m]] : 0.0;
+            const double e = (double)eps_sorted[m];
             s[0] = __dadd_rn(s[0], a);
             s[1] = __dadd_rn(s[1], __dmul_rn(a, (double)g.x));  // products are exact
             s[2] = __dadd_rn(s[2], __dmul_rn(a, (double)g.y));
@@ -443,15 +456,21 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(dalloc(&off, n + 1, s));
     DIP_CUDA_TRY(dalloc(&scan_tmp, scan_tmp_entries(n + 1), s));
     DIP_CUDA_TRY(dalloc(&partial, (int64_t)nbb * 6, s));
+    float* eps_sorted = nullptr;
+    uint32_t* tmask = nullptr;
+    int32_t* estage = nullptr;
+    DIP_CUDA_TRY(dalloc(&eps_sorted, n, s));
+    DIP_CUDA_TRY(dalloc(&tmask, n, s));
+    DIP_CUDA_TRY(dalloc(&estage, n * (kMaxLevel + 1), s));
 
     note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
     note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
     query_codes(points, n, t->bbox, 0, t->code, t->perm, t->status, s);
     radix_sort_pairs(t->code, t->perm, ktmp, vtmp, hist, n, 30, s);
     note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
-                                                      t->pts);
+                                                      t->pts, eps_sorted);
     note_launch(); k_topo_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size,
-                                                            t->max_depth, off);
+                                                            t->max_depth, off, tmask, estage);
     DIP_CUDA_TRY(cudaMemsetAsync(off + n, 0, sizeof(uint32_t), s));
     exclusive_scan_u32(off, n + 1, scan_tmp, s);
     uint32_t nn_host = 0;
@@ -465,6 +484,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     auto free_tmp = [&]() {
         cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s); cudaFreeAsync(hist, s);
         cudaFreeAsync(off, s); cudaFreeAsync(scan_tmp, s); cudaFreeAsync(partial, s);
+        cudaFreeAsync(eps_sorted, s); cudaFreeAsync(tmask, s); cudaFreeAsync(estage, s);
     };
     if (status_host & kStatusNonFinite) {
         free_tmp();
@@ -501,8 +521,8 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
     DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
 
-    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size, t->max_depth,
-                                                           off, t->first, t->count, t->level,
+    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, tmask, estage,
+                                                           t->first, t->count, t->level,
                                                            t->skip, t->is_leaf, t->leaf_of);
     DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
     note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
@@ -514,7 +534,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     note_launch(); k_level_fill<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
         nn, t->level, t->is_leaf, t->lvl_off, lvl_cnt + kMaxLevel + 1, t->lvl_list);
     note_launch(); k_geom_leaves<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
-        nn, t->pts, t->perm, radii, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
+        nn, t->pts, eps_sorted, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
     for (int l = t->max_depth - 1; l >= 0; --l) {
         note_launch();
         k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,

@@ -33,7 +33,7 @@ DIPOLE_BF16 = 1
 EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
-            "dipole_kernel_launches", "dipole_forward_noalloc"]
+            "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2"]
 
 
 class DipoleError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_sync_status": [P, P],
             "dipole_tree_info_get": [P, P],
             "dipole_tree_export": [P] * 15,
+            "dipole_probe_l2": [P, I64, I32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -220,6 +221,13 @@ def dipole_tree_export(tree: int, moments: bool = False, stream=None) -> dict:
     ptrs = [o[k].ctypes.data_as(ctypes.c_void_p) if k in o else None for k in keys]
     _check(load_library().dipole_tree_export(ctypes.c_void_p(tree), *ptrs, _stream(stream)))
     return o
+
+
+def dipole_probe_l2(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=None):
+    """Diagnostics: read `buf` `passes` times with L2-only loads (for timing)."""
+    _check(load_library().dipole_probe_l2(ctypes.c_void_p(buf.data_ptr()),
+                                          buf.numel() * buf.element_size(), int(passes),
+                                          ctypes.c_void_p(sink.data_ptr()), _stream(stream)))
 
 
 def dipole_tree_destroy(tree: int):
