@@ -68,6 +68,21 @@ def rank_workload(name: str, rank: int):
     return w
 
 
+def max_over_ranks(value: float, td=None, device=None) -> float:
+    """The largest value over all ranks (the job is as slow as its slowest rank)."""
+    if td is None or not td.is_available() or not td.is_initialized() or td.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, steps: int, max_ms: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's timed span."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
+
+
 def config_of(w, flush: str):
     return {"workload": w.name, "points": w.cloud.n, "queries": int(len(w.queries)),
             "channels": int(w.mu.shape[1]), "attr_dtype": "f32", "beta": BETA,
@@ -304,11 +319,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * Q * args.steps / (max_ms * 1e-3)
+    max_ms = max_over_ranks(total_ms, td, dev)
+    value = job_throughput(world, Q, args.steps, max_ms)
     ms_per_step = max_ms / args.steps
 
     # ---- phase breakdown and roofline (untimed for `value`) ----
@@ -415,10 +427,8 @@ def run_ours(args):
             hh = e2e_step()
             el += time.perf_counter() - t0
             dp.dipole_tree_destroy(hh)
-        te = torch.tensor([el], device=dev)
-        if world > 1:
-            td.all_reduce(te, op=td.ReduceOp.MAX)
-        e2e = {"value": world * Q * k_e2e / float(te.item()), "unit": UNIT,
+        el_max = max_over_ranks(el, td, dev)
+        e2e = {"value": job_throughput(world, Q, k_e2e, el_max * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": k_e2e, "timing": "host wall clock, pinned host buffers, sync per step"}
 
