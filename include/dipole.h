@@ -227,6 +227,29 @@ int dipole_tree_export(const dipole_tree* tree, uint32_t* codes, uint32_t* perm,
  */
 int dipole_probe_l2(const void* buf, int64_t bytes, int32_t passes, float* sink, void* stream);
 
+/*
+ * Rebuild a tree from an export (checkpoint / resume): the point inputs as for
+ * dipole_build_tree (DEVICE, caller order) and the topology arrays written by
+ * dipole_tree_export (HOST): perm [n], first/count/level/skip/is_leaf
+ * [n_nodes], codes [n] (informational, may be NULL).  No sorting and no
+ * topology construction: the node geometry (eq. farfield_dipole) and node
+ * records are recomputed from the given ranges, so an export of the result
+ * equals the original export.  Synchronizes `stream` once.
+ *
+ * Validation (host, before any device work): perm is a permutation of
+ * [0, n); for every node 0 <= first < n, 1 <= count <= n - first,
+ * 0 <= level <= max_depth, 0 <= skip <= n_nodes, is_leaf in {0, 1}; else
+ * DIPOLE_EINVAL.  Every index a kernel follows is therefore in range.  The
+ * structure (nesting, preorder) is not checked: queries on a corrupt
+ * structure stop at their step bound and dipole_sync_status() reports
+ * DIPOLE_ETRAVERSAL.
+ */
+int dipole_tree_import(const float* points, const float* normals, const float* areas,
+                       const float* radii, int64_t n, const uint32_t* codes, const uint32_t* perm,
+                       const int32_t* first, const int32_t* count, const int32_t* level,
+                       const int32_t* skip, const int32_t* is_leaf, int64_t n_nodes,
+                       const dipole_build_params* params, void* stream, dipole_tree** out);
+
 /* Release the tree and its device memory (synchronizes the device).  NULL is a no-op. */
 void dipole_tree_destroy(dipole_tree* tree);
 

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/dipole.h"
 #include "kernels.cuh"
@@ -96,6 +97,61 @@ int dipole_build_tree(const float* points, const float* normals, const float* ar
     t->leaf_size = leaf_size;
     t->max_depth = max_depth;
     int rc = dip::build_tree(t, points, normals, areas, radii, as_stream(stream));
+    if (rc != 0) {
+        cudaStreamSynchronize(as_stream(stream));
+        free_tree_memory(t);
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return DIPOLE_OK;
+}
+
+int dipole_tree_import(const float* points, const float* normals, const float* areas,
+                       const float* radii, int64_t n, const uint32_t* codes, const uint32_t* perm,
+                       const int32_t* first, const int32_t* count, const int32_t* level,
+                       const int32_t* skip, const int32_t* is_leaf, int64_t n_nodes,
+                       const dipole_build_params* params, void* stream, dipole_tree** out) {
+    if (!out) return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: out is NULL");
+    *out = nullptr;
+    if (!points || !normals || !areas || !perm || !first || !count || !level || !skip || !is_leaf)
+        return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: a required pointer is NULL");
+    if (n < 1 || n > (int64_t)INT32_MAX / 2)
+        return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: n must be in [1, 2^30)");
+    if (n_nodes < 1 || n_nodes > 2 * n + 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: n_nodes must be in [1, 2n+1]");
+    int leaf_size = params ? params->leaf_size : 8, max_depth = params ? params->max_depth : 10;
+    if (leaf_size < 1 || leaf_size > 64 || max_depth < 0 || max_depth > 10)
+        return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: bad leaf_size or max_depth");
+    // Every index a kernel will follow must stay in range; the structure itself
+    // (nesting, order) is not checked: a traversal of a corrupt structure ends
+    // at its step bound with DIPOLE_ETRAVERSAL.
+    std::vector<char> seen((size_t)n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (perm[i] >= (uint64_t)n || seen[perm[i]])
+            return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: perm is not a permutation");
+        seen[perm[i]] = 1;
+    }
+    for (int64_t t = 0; t < n_nodes; ++t) {
+        if (is_leaf[t] != 0 && is_leaf[t] != 1)
+            return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: is_leaf must be 0 or 1");
+        if (level[t] < 0 || level[t] > max_depth)
+            return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: level out of range");
+        if (first[t] < 0 || first[t] >= n || count[t] < 1 || (int64_t)count[t] > n - first[t])
+            return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: node point range out of range");
+        if (skip[t] < 0 || (int64_t)skip[t] > n_nodes)
+            return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: skip out of range");
+    }
+    configure_pool_once();
+    dipole_tree* t = new (std::nothrow) dipole_tree();
+    if (!t) return dip_fail(DIPOLE_ENOMEM, "dipole_tree_import: out of host memory");
+    cudaGetDevice(&t->device);
+    t->n = n;
+    t->nn = n_nodes;
+    t->leaf_size = leaf_size;
+    t->max_depth = max_depth;
+    int rc = dip::import_tree(t, points, normals, areas, radii, codes, perm, first, count, level,
+                              skip, is_leaf, as_stream(stream));
     if (rc != 0) {
         cudaStreamSynchronize(as_stream(stream));
         free_tree_memory(t);

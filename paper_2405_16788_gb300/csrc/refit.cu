@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(128) k_refit_level(int l, const int32_t* __res
                 double q[12];
 #pragma unroll
                 for (int j = 0; j < 12; ++j) q[j] = 0.0;
-                for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
+                int kc = 0;
+                for (int32_t ch = p + 1; ch < end && kc < 8; ++kc) {
                     const int32_t bc = big_idx[ch];
 #pragma unroll
                     for (int j = 0; j < 12; ++j) {
@@ -100,6 +101,9 @@ __global__ void __launch_bounds__(128) k_refit_level(int l, const int32_t* __res
                         q[j] += bc >= 0 ? S64[(int64_t)bc * SR + j0 + j]
                                         : (double)S[(int64_t)ch * SR + j0 + j];
                     }
+                    const int32_t nx = skip[ch];
+                    if (nx <= ch) break;  // only an imported, corrupt tree gets here
+                    ch = nx;
                 }
 #pragma unroll
                 for (int j = 0; j < 12; ++j) {
@@ -111,12 +115,16 @@ __global__ void __launch_bounds__(128) k_refit_level(int l, const int32_t* __res
                 float q[12];
 #pragma unroll
                 for (int j = 0; j < 12; ++j) q[j] = 0.0f;
-                for (int32_t ch = p + 1; ch < end; ch = skip[ch]) {
+                int kc = 0;
+                for (int32_t ch = p + 1; ch < end && kc < 8; ++kc) {
 #pragma unroll
                     for (int j = 0; j < 12; ++j) {
                         if (j0 + j >= 3 * CP) break;
                         q[j] += S[(int64_t)ch * SR + j0 + j];
                     }
+                    const int32_t nx = skip[ch];
+                    if (nx <= ch) break;  // only an imported, corrupt tree gets here
+                    ch = nx;
                 }
 #pragma unroll
                 for (int j = 0; j < 12; ++j) {

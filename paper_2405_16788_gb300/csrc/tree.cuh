@@ -105,6 +105,13 @@ namespace dip {
 int build_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
                const float* radii, cudaStream_t s);
 
+// Rebuild a tree from exported topology (host arrays) and point inputs (device),
+// t->n, t->nn and the parameters already set; the host arrays are validated.
+int import_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
+                const float* radii, const uint32_t* codes_h, const uint32_t* perm_h,
+                const int32_t* first_h, const int32_t* count_h, const int32_t* level_h,
+                const int32_t* skip_h, const int32_t* is_leaf_h, cudaStream_t s);
+
 // Tree update of node moments (eq. farfield_dipole_features).
 int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
 

@@ -354,9 +354,13 @@ __global__ void k_geom_level(int l, const int32_t* __restrict__ lvl_off,
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = lvl_list[i];
         double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int32_t ch = p + 1; ch < skip[p]; ch = skip[ch]) {
+        int k = 0;
+        for (int32_t ch = p + 1; ch < skip[p] && k < 8; ++k) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], agg[(int64_t)ch * 5 + j]);
+            const int32_t nx = skip[ch];
+            if (nx <= ch) break;  // only an imported, corrupt tree gets here
+            ch = nx;
         }
 #pragma unroll
         for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
@@ -400,7 +404,8 @@ __global__ void k_finalize_nodes(int64_t nn, const float4* __restrict__ cen4,
                                  const int32_t* __restrict__ count,
                                  const int32_t* __restrict__ is_leaf,
                                  const float* __restrict__ eps_node, NodeRec* __restrict__ nodes,
-                                 int32_t* __restrict__ big_idx, unsigned int* nbig) {
+                                 int32_t* __restrict__ big_idx, unsigned int* nbig,
+                                 unsigned int nbig_cap) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
          t += (int64_t)gridDim.x * blockDim.x) {
         const float4 c = cen4[t];
@@ -409,7 +414,22 @@ __global__ void k_finalize_nodes(int64_t nn, const float4* __restrict__ cen4,
         r.meta = make_int4(skip[t], first[t], is_leaf[t] ? count[t] : 0,
                            __float_as_int(__frcp_rn(eps_node[t])));
         nodes[t] = r;
-        big_idx[t] = (count[t] >= kBigNode) ? (int32_t)atomicAdd(nbig, 1u) : -1;
+        int32_t b = -1;
+        if (count[t] >= kBigNode) {
+            const unsigned int slot = atomicAdd(nbig, 1u);
+            if (slot < nbig_cap) b = (int32_t)slot;  // an imported tree may overlap nodes
+        }
+        big_idx[t] = b;
+    }
+}
+
+__global__ void k_leaf_of(int64_t nn, const int32_t* __restrict__ first,
+                          const int32_t* __restrict__ count, const int32_t* __restrict__ is_leaf,
+                          int32_t* __restrict__ leaf_of) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (!is_leaf[t]) continue;
+        for (int64_t m = first[t]; m < (int64_t)first[t] + count[t]; ++m) leaf_of[m] = (int32_t)t;
     }
 }
 
@@ -427,12 +447,10 @@ cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
     return cudaMallocAsync((void**)p, bytes, s);
 }
 
-}  // namespace
 
-int build_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
-               const float* radii, cudaStream_t s) {
+// Point arrays, status word, bounding box and scheduling record of a new tree.
+int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     const int64_t n = t->n;
-    // persistent point arrays
     DIP_CUDA_TRY(dalloc(&t->pts, n, s));
     DIP_CUDA_TRY(dalloc(&t->code, n, s));
     DIP_CUDA_TRY(dalloc(&t->perm, n, s));
@@ -444,6 +462,81 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     t->sched->cap = std::max<int64_t>(4096, (n + 31) / 32);
     DIP_CUDA_TRY(dalloc(&t->sched->cost, t->sched->cap, s));
     DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
+    return 0;
+}
+
+int status_error(int status_host, const char* who) {
+    if (status_host & kStatusNonFinite)
+        return dip_fail(-4, std::string(who) + ": non-finite point, normal, area or radius");
+    if (status_host & kStatusBadArea)
+        return dip_fail(-1, std::string(who) + ": every area weight must be > 0");
+    if (status_host & kStatusBadRadius) return dip_fail(-1, std::string(who) + ": radii must be >= 0");
+    return 0;
+}
+
+// Everything that follows from the node ranges (first, count, level, skip,
+// is_leaf, already on the device) and leaf_of: parents, level lists, node
+// geometry (eq. farfield_dipole), radius, node records.
+int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
+    const int64_t n = t->n, nn = t->nn;
+    DIP_CUDA_TRY(dalloc(&t->nodes, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->parent, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->nchild, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->big_idx, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
+    DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
+    float4* cen4 = nullptr;
+    unsigned int *rbits = nullptr, *nbig = nullptr, *lvl_cnt = nullptr;
+    DIP_CUDA_TRY(dalloc(&cen4, nn, s));
+    DIP_CUDA_TRY(dalloc(&rbits, nn, s));
+    DIP_CUDA_TRY(dalloc(&nbig, 1, s));
+    DIP_CUDA_TRY(dalloc(&lvl_cnt, 2 * (kMaxLevel + 1), s));
+    // Nodes of one level are disjoint, so each level has at most n / kBigNode
+    // big nodes: an upper bound that needs no second synchronization.
+    t->nbig = (int64_t)(t->max_depth + 1) * (n / kBigNode + 1);
+
+    DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
+    note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
+                                                           t->nchild, t->status);
+    DIP_CUDA_TRY(cudaMemsetAsync(lvl_cnt, 0, sizeof(unsigned int) * (kMaxLevel + 1), s));
+    note_launch(); k_level_count<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->level, t->is_leaf,
+                                                                            lvl_cnt);
+    note_launch(); k_level_offsets<<<1, 32, 0, s>>>(lvl_cnt, t->lvl_off, lvl_cnt + kMaxLevel + 1);
+    note_launch(); k_level_fill<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
+        nn, t->level, t->is_leaf, t->lvl_off, lvl_cnt + kMaxLevel + 1, t->lvl_list);
+    note_launch(); k_geom_leaves<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
+        nn, t->pts, eps_sorted, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
+    for (int l = t->max_depth - 1; l >= 0; --l) {
+        note_launch();
+        k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
+                                                                 t->agg64, cen4, t->eps_node);
+    }
+    DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
+    note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
+                                                        rbits);
+    DIP_CUDA_TRY(cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s));
+    note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
+                                                                 t->first, t->count, t->is_leaf,
+                                                                 t->eps_node, t->nodes,
+                                                                 t->big_idx, nbig,
+                                                                 (unsigned int)t->nbig);
+    cudaFreeAsync(cen4, s);
+    cudaFreeAsync(rbits, s);
+    cudaFreeAsync(lvl_cnt, s);
+    cudaFreeAsync(nbig, s);
+    DIP_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace
+
+int build_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
+               const float* radii, cudaStream_t s) {
+    const int64_t n = t->n;
+    int rc = alloc_point_state(t, s);
+    if (rc) return rc;
 
     // temporaries
     uint32_t *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr, *off = nullptr, *scan_tmp = nullptr;
@@ -486,78 +579,69 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
         cudaFreeAsync(off, s); cudaFreeAsync(scan_tmp, s); cudaFreeAsync(partial, s);
         cudaFreeAsync(eps_sorted, s); cudaFreeAsync(tmask, s); cudaFreeAsync(estage, s);
     };
-    if (status_host & kStatusNonFinite) {
+    rc = status_error(status_host, "dipole_build_tree");
+    if (rc) {
         free_tmp();
-        return dip_fail(-4, "dipole_build_tree: non-finite point, normal, area or radius");
-    }
-    if (status_host & kStatusBadArea) {
-        free_tmp();
-        return dip_fail(-1, "dipole_build_tree: every area weight must be > 0");
-    }
-    if (status_host & kStatusBadRadius) {
-        free_tmp();
-        return dip_fail(-1, "dipole_build_tree: radii must be >= 0");
+        return rc;
     }
     const int64_t nn = nn_host;
     t->nn = nn;
-
-    DIP_CUDA_TRY(dalloc(&t->nodes, nn, s));
     DIP_CUDA_TRY(dalloc(&t->first, nn, s));
     DIP_CUDA_TRY(dalloc(&t->count, nn, s));
     DIP_CUDA_TRY(dalloc(&t->level, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->parent, nn, s));
     DIP_CUDA_TRY(dalloc(&t->skip, nn, s));
     DIP_CUDA_TRY(dalloc(&t->is_leaf, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->nchild, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->big_idx, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
-    DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
-    float4* cen4 = nullptr;
-    unsigned int *rbits = nullptr, *nbig = nullptr, *lvl_cnt = nullptr;
-    DIP_CUDA_TRY(dalloc(&cen4, nn, s));
-    DIP_CUDA_TRY(dalloc(&rbits, nn, s));
-    DIP_CUDA_TRY(dalloc(&nbig, 1, s));
-    DIP_CUDA_TRY(dalloc(&lvl_cnt, 2 * (kMaxLevel + 1), s));
-    DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
-
     note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, tmask, estage,
                                                            t->first, t->count, t->level,
                                                            t->skip, t->is_leaf, t->leaf_of);
-    DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
-    note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
-                                                           t->nchild, t->status);
-    DIP_CUDA_TRY(cudaMemsetAsync(lvl_cnt, 0, sizeof(unsigned int) * (kMaxLevel + 1), s));
-    note_launch(); k_level_count<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->level, t->is_leaf,
-                                                                            lvl_cnt);
-    note_launch(); k_level_offsets<<<1, 32, 0, s>>>(lvl_cnt, t->lvl_off, lvl_cnt + kMaxLevel + 1);
-    note_launch(); k_level_fill<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
-        nn, t->level, t->is_leaf, t->lvl_off, lvl_cnt + kMaxLevel + 1, t->lvl_list);
-    note_launch(); k_geom_leaves<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
-        nn, t->pts, eps_sorted, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
-    for (int l = t->max_depth - 1; l >= 0; --l) {
-        note_launch();
-        k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
-                                                                 t->agg64, cen4, t->eps_node);
-    }
-    DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
-    note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
-                                                        rbits);
-    DIP_CUDA_TRY(cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s));
-    note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
-                                                                 t->first, t->count, t->is_leaf,
-                                                                 t->eps_node, t->nodes,
-                                                                 t->big_idx, nbig);
+    rc = derive_nodes(t, eps_sorted, s);
     free_tmp();
-    cudaFreeAsync(cen4, s);
-    cudaFreeAsync(rbits, s);
-    cudaFreeAsync(lvl_cnt, s);
-    cudaFreeAsync(nbig, s);
+    return rc;
+}
+
+int import_tree(dipole_tree* t, const float* points, const float* normals, const float* areas,
+                const float* radii, const uint32_t* codes_h, const uint32_t* perm_h,
+                const int32_t* first_h, const int32_t* count_h, const int32_t* level_h,
+                const int32_t* skip_h, const int32_t* is_leaf_h, cudaStream_t s) {
+    const int64_t n = t->n, nn = t->nn;
+    int rc = alloc_point_state(t, s);
+    if (rc) return rc;
+    float* partial = nullptr;
+    float* eps_sorted = nullptr;
+    const unsigned nbb = grid_for(n, kThreads) < 2u * (unsigned)num_sms() ? grid_for(n, kThreads)
+                                                                          : 2u * (unsigned)num_sms();
+    DIP_CUDA_TRY(dalloc(&partial, (int64_t)nbb * 6, s));
+    DIP_CUDA_TRY(dalloc(&eps_sorted, n, s));
+    DIP_CUDA_TRY(dalloc(&t->first, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->count, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->level, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->skip, nn, s));
+    DIP_CUDA_TRY(dalloc(&t->is_leaf, nn, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->perm, perm_h, 4 * n, cudaMemcpyHostToDevice, s));
+    if (codes_h) DIP_CUDA_TRY(cudaMemcpyAsync(t->code, codes_h, 4 * n, cudaMemcpyHostToDevice, s));
+    else DIP_CUDA_TRY(cudaMemsetAsync(t->code, 0, 4 * n, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->first, first_h, 4 * nn, cudaMemcpyHostToDevice, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->count, count_h, 4 * nn, cudaMemcpyHostToDevice, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->level, level_h, 4 * nn, cudaMemcpyHostToDevice, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->skip, skip_h, 4 * nn, cudaMemcpyHostToDevice, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->is_leaf, is_leaf_h, 4 * nn, cudaMemcpyHostToDevice, s));
+    note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
+    note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
+    note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
+                                                      t->pts, eps_sorted);
+    DIP_CUDA_TRY(cudaMemsetAsync(t->leaf_of, 0xff, sizeof(int32_t) * n, s));
+    note_launch(); k_leaf_of<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->first, t->count, t->is_leaf,
+                                                          t->leaf_of);
+    int status_host = 0;
+    DIP_CUDA_TRY(cudaMemcpyAsync(&status_host, t->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DIP_CUDA_TRY(cudaMemcpyAsync(t->bbox_host, t->bbox, 5 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    DIP_CUDA_TRY(cudaStreamSynchronize(s));
     DIP_CUDA_TRY(cudaGetLastError());
-    // Nodes of one level are disjoint, so each level has at most n / kBigNode
-    // big nodes: an upper bound that needs no second synchronization.
-    t->nbig = (int64_t)(t->max_depth + 1) * (n / kBigNode + 1);
-    return 0;
+    rc = status_error(status_host, "dipole_tree_import");
+    if (rc == 0) rc = derive_nodes(t, eps_sorted, s);
+    cudaFreeAsync(partial, s);
+    cudaFreeAsync(eps_sorted, s);
+    return rc;
 }
 
 }  // namespace dip

@@ -33,7 +33,8 @@ DIPOLE_BF16 = 1
 EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
-            "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2"]
+            "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
+            "dipole_tree_import"]
 
 
 class DipoleError(RuntimeError):
@@ -79,6 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_tree_info_get": [P, P],
             "dipole_tree_export": [P] * 15,
             "dipole_probe_l2": [P, I64, I32, P, P],
+            "dipole_tree_import": [P, P, P, P, I64, P, P, P, P, P, P, P, I64, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -230,6 +232,31 @@ def dipole_probe_l2(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=N
                                           ctypes.c_void_p(sink.data_ptr()), _stream(stream)))
 
 
+def dipole_tree_import(points, normals, areas, radii, exported: dict, leaf_size=8, max_depth=10,
+                       stream=None) -> int:
+    """Rebuild a tree from dipole_tree_export's arrays (host numpy) and the
+    point inputs (CUDA tensors); returns the tree handle."""
+    lib = load_library()
+    n = int(points.shape[0])
+    host = {k: np.ascontiguousarray(exported[k], dtype=np.int32)
+            for k in ("first", "count", "level", "skip", "is_leaf")}
+    perm = np.ascontiguousarray(exported["perm"], dtype=np.uint32)
+    code = exported.get("code")
+    code = None if code is None else np.ascontiguousarray(code, dtype=np.uint32)
+    nn = int(host["first"].shape[0])
+    hp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    params = _BuildParams(int(leaf_size), int(max_depth))
+    h = ctypes.c_void_p()
+    _check(lib.dipole_tree_import(_dev(points, "points", shape=(n, 3)),
+                                  _dev(normals, "normals", shape=(n, 3)),
+                                  _dev(areas, "areas", shape=(n,)),
+                                  None if radii is None else _dev(radii, "radii", shape=(n,)), n,
+                                  hp(code), hp(perm), hp(host["first"]), hp(host["count"]),
+                                  hp(host["level"]), hp(host["skip"]), hp(host["is_leaf"]), nn,
+                                  ctypes.byref(params), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
 def dipole_tree_destroy(tree: int):
     if tree:
         load_library().dipole_tree_destroy(ctypes.c_void_p(tree))
@@ -250,6 +277,19 @@ class DipoleTree:
                                         stream)
         self.C = 0
         self.device = points.device
+
+    @classmethod
+    def from_export(cls, points, normals, areas, radii, exported: dict, leaf_size=8, max_depth=10,
+                    stream=None) -> "DipoleTree":
+        """A tree rebuilt from dipole_tree_export's arrays (checkpoint / resume)."""
+        self = cls.__new__(cls)
+        self.n = int(points.shape[0])
+        self._inputs = (points, normals, areas, radii)
+        self.handle = dipole_tree_import(points, normals, areas, radii, exported, leaf_size,
+                                         max_depth, stream)
+        self.C = 0
+        self.device = points.device
+        return self
 
     def close(self):
         if getattr(self, "handle", None):

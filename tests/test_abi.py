@@ -71,3 +71,33 @@ def test_oracle_and_library_share_nothing():
     for f in ["dipole.py", "_build.py", "__init__.py"]:
         txt = open(os.path.join(ROOT, "paper_2405_16788_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt
+
+
+def test_tree_import_validates_host_arrays_before_device_work(lib_path):
+    """dipole_tree_import rejects out-of-range topology on the host (no GPU
+    needed: the device pointers below are never dereferenced)."""
+    import numpy as np
+    from paper_2405_16788_gb300 import dipole
+    lib = dipole.load_library()
+    n, nn = 4, 3
+    fake = ctypes.c_void_p(16)  # stands in for device pointers; validation fails first
+    perm = np.array([0, 1, 2, 3], np.uint32)
+    first = np.array([0, 0, 2], np.int32)
+    count = np.array([4, 2, 2], np.int32)
+    level = np.array([0, 1, 1], np.int32)
+    skip = np.array([3, 2, 3], np.int32)
+    leaf = np.array([0, 1, 1], np.int32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+
+    def call(perm=perm, first=first, count=count, level=level, skip=skip, leaf=leaf, nn=nn):
+        out = ctypes.c_void_p()
+        return lib.dipole_tree_import(fake, fake, fake, None, n, None, p(perm), p(first), p(count),
+                                      p(level), p(skip), p(leaf), nn, None, None, ctypes.byref(out))
+
+    assert call(perm=np.array([0, 1, 1, 3], np.uint32)) == dipole.DIPOLE_EINVAL
+    assert "permutation" in dipole.dipole_last_error()
+    assert call(skip=np.array([3, 2, 4], np.int32)) == dipole.DIPOLE_EINVAL
+    assert call(count=np.array([4, 2, 3], np.int32)) == dipole.DIPOLE_EINVAL
+    assert call(level=np.array([0, 11, 1], np.int32)) == dipole.DIPOLE_EINVAL
+    assert call(leaf=np.array([0, 2, 1], np.int32)) == dipole.DIPOLE_EINVAL
+    assert call(nn=0) == dipole.DIPOLE_EINVAL
