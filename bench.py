@@ -87,6 +87,7 @@ def config_of(w, flush: str):
     return {"workload": w.name, "points": w.cloud.n, "queries": int(len(w.queries)),
             "channels": int(w.mu.shape[1]), "attr_dtype": "f32", "beta": BETA,
             "leaf_size": LEAF, "tree": "built every step",
+            "api": "dipole_build_tree, dipole_refit, dipole_forward_planned, dipole_adjoint_planned",
             "l2": flush, "step": "build + refit + forward + adjoint (stage 1 + 2)"}
 
 
@@ -285,11 +286,13 @@ def run_ours(args):
     GRAD = torch.empty((N, C), device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # 512 MB > L2
 
+    PLAN = dp.QueryPlan(Q, dev)
+
     def step(mu=MU):
         h = dp.dipole_build_tree(P, Nr, A, E, LEAF, 10)
         dp.dipole_refit(h, mu)
-        dp.dipole_forward(h, X, BETA, OUT)
-        dp.dipole_adjoint(h, X, BETA, G, GRAD, False)
+        dp.dipole_forward_planned(h, X, BETA, OUT, PLAN)
+        dp.dipole_adjoint_planned(h, X, BETA, G, GRAD, PLAN, False)
         return h
 
     for _ in range(args.warmup):
@@ -334,9 +337,9 @@ def run_ours(args):
             ev[1].record(stream)
             dp.dipole_refit(hh, mu)
             ev[2].record(stream)
-            dp.dipole_forward(hh, X, BETA, OUT)
+            dp.dipole_forward_planned(hh, X, BETA, OUT, PLAN)
             ev[3].record(stream)
-            dp.dipole_adjoint(hh, X, BETA, G, GRAD, False)
+            dp.dipole_adjoint_planned(hh, X, BETA, G, GRAD, PLAN, False)
             ev[4].record(stream)
             ev[4].synchronize()
             acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
@@ -410,8 +413,8 @@ def run_ours(args):
                 d_.copy_(h_, non_blocking=True)
             hh = dp.dipole_build_tree(dbuf[0], dbuf[1], dbuf[2], dbuf[3], LEAF, 10)
             dp.dipole_refit(hh, dbuf[4])
-            dp.dipole_forward(hh, dbuf[5], BETA, OUT)
-            dp.dipole_adjoint(hh, dbuf[5], BETA, dbuf[6], GRAD, False)
+            dp.dipole_forward_planned(hh, dbuf[5], BETA, OUT, PLAN)
+            dp.dipole_adjoint_planned(hh, dbuf[5], BETA, dbuf[6], GRAD, PLAN, False)
             out_h.copy_(OUT, non_blocking=True)
             grad_h.copy_(GRAD, non_blocking=True)
             torch.cuda.synchronize()

@@ -187,6 +187,28 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
                    const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream);
 
 /*
+ * Forward and adjoint sharing a query plan (caller-owned device buffers):
+ *   plan_perm [q]              uint32, written by dipole_forward_planned: the Morton
+ *                              order of the queries (a permutation of [0, q))
+ *   plan_cost [ceil(q / 32)]   uint32, written by dipole_forward_planned: the traversal
+ *                              steps of every 32-query packet
+ * dipole_forward_planned = dipole_forward that also writes the plan.
+ * dipole_adjoint_planned = dipole_adjoint that reads the plan of a forward on the
+ *   same queries (the order of every training step: primal queries, then their
+ *   adjoint, Sec. 6.2) instead of sorting them again, and schedules the
+ *   longest packets first.  Results do not depend on the plan; it must come
+ *   from dipole_forward_planned with the same q (plan_perm must be a
+ *   permutation of [0, q)), and the forward must be complete on `stream` or
+ *   ordered before the adjoint.
+ * Same arguments, results and errors as dipole_forward / dipole_adjoint otherwise.
+ */
+int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           float* out, uint32_t* plan_perm, uint32_t* plan_cost, void* stream);
+int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           const float* grad_out, float* grad_attrs, int32_t accumulate,
+                           const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream);
+
+/*
  * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,
  * leaf points summed} (int32 [q,3], device).  Same traversal and decisions as
  * dipole_forward; used for the roofline's algorithmic bytes and to check the

@@ -38,8 +38,6 @@ void free_tree_memory(dipole_tree* t) {
                     t->S,      t->S64,     t->dS,     t->dmu,     t->lvl_list, t->lvl_off};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    delete t->sched;
-    t->sched = nullptr;
 }
 
 int status_to_code(int st) {
@@ -182,8 +180,8 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
     if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_forward: q must be < 2^31");
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward: beta must be > 0");
     if (q == 0) return DIPOLE_OK;
-    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr,
-                      as_stream(stream));
+    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr, nullptr,
+                      nullptr, false, as_stream(stream));
 }
 
 int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -216,7 +214,39 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
     if (accumulate != 0 && accumulate != 1)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: accumulate must be 0 or 1");
     return dip::query(tree, 1, queries, q, beta, nullptr, grad_out, grad_attrs, accumulate,
-                      nullptr, as_stream(stream));
+                      nullptr, nullptr, nullptr, false, as_stream(stream));
+}
+
+int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           float* out, uint32_t* plan_perm, uint32_t* plan_cost, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_planned: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: q must be in [0, 2^31)");
+    if (q > 0 && (!queries || !out || !plan_perm || !plan_cost))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: queries, out and the plan are required");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr, plan_perm,
+                      plan_cost, false, as_stream(stream));
+}
+
+int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           const float* grad_out, float* grad_attrs, int32_t accumulate,
+                           const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_planned: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: q must be in [0, 2^31)");
+    if (!grad_attrs) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: grad_attrs is required");
+    if (q > 0 && (!queries || !grad_out || !plan_perm || !plan_cost))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: queries, grad_out and the plan are required");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: accumulate must be 0 or 1");
+    return dip::query(tree, 1, queries, q, beta, nullptr, grad_out, grad_attrs, accumulate, nullptr,
+                      const_cast<uint32_t*>(plan_perm), const_cast<uint32_t*>(plan_cost), true,
+                      as_stream(stream));
 }
 
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -228,8 +258,8 @@ int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q
     if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: q must be < 2^31");
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: beta must be > 0");
     if (q == 0) return DIPOLE_OK;
-    return dip::query(tree, 2, queries, q, beta, nullptr, nullptr, nullptr, 0, counts,
-                      as_stream(stream));
+    return dip::query(tree, 2, queries, q, beta, nullptr, nullptr, nullptr, 0, counts, nullptr,
+                      nullptr, false, as_stream(stream));
 }
 
 int dipole_sync_status(dipole_tree* tree, void* stream) {

@@ -407,43 +407,44 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
 }
 
 int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta, float* out,
-          const float* g, float* grad, int accumulate, int32_t* counts, cudaStream_t s) {
+          const float* g, float* grad, int accumulate, int32_t* counts, uint32_t* plan_perm,
+          uint32_t* plan_cost, bool plan_in, cudaStream_t s) {
     const int SR = srow(t->Cp > 0 ? t->Cp : 1);
-    // Morton order of the queries: codes in the tree's cube, sorted with their indices.
+    const int64_t np = (q + 31) / 32;
     uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
     unsigned long long* work = nullptr;
     DIP_CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(unsigned long long), s));
     if (q > 0) {
         DIP_CUDA_TRY(cudaMallocAsync((void**)&codes, sizeof(uint32_t) * q, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&ktmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
-        query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
-        radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
+        if (plan_in) {
+            idx = plan_perm;  // the Morton order computed by the forward on these queries
+        } else {
+            // Morton order of the queries: codes in the tree's cube, sorted with their indices
+            if (plan_perm) idx = plan_perm;
+            else DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
+            query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+            radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
+        }
     }
-    // Scheduling.  The forward runs packets in Morton order and records each
-    // packet's warp steps; an adjoint on the same queries (the case in every
-    // training step) runs the packets longest first from that record.  A stale
-    // record only changes the order, never a result.
-    const int64_t np = (q + 31) / 32;
+    // Scheduling.  Packets run in Morton order, each recording its warp steps
+    // into the plan when one is given; a call that reads a plan runs the
+    // packets longest first from those records.  The record only changes the
+    // order of the packets, never a result.
     const uint32_t* porder = nullptr;
     uint32_t* pcost = nullptr;
-    if (np >= kOrderMinPackets && mode != kCount) {
-        std::lock_guard<std::mutex> lock(t->sched->mu);
-        if (mode == kForward) {
-            if (t->sched->ensure(np)) {
-                pcost = t->sched->cost;
-                t->sched->queries = queries;
-                t->sched->q = q;
-            }
-        } else if (t->sched->queries == queries && t->sched->q == q && t->sched->cost) {
-            DIP_CUDA_TRY(cudaMemcpyAsync(codes, t->sched->cost, sizeof(uint32_t) * np,
+    if (q > 0 && np >= kOrderMinPackets && mode != kCount) {
+        if (plan_in && plan_cost) {
+            DIP_CUDA_TRY(cudaMemcpyAsync(codes, plan_cost, sizeof(uint32_t) * np,
                                          cudaMemcpyDeviceToDevice, s));
             note_launch();
             k_iota<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(ktmp, np);
             radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
             porder = ktmp;
+        } else if (!plan_in && plan_cost) {
+            pcost = plan_cost;
         }
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
@@ -480,8 +481,9 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
     if (rc == 0 && mode == kAdjoint) rc = stage2(t, grad, accumulate, s);
     cudaFreeAsync(work, s);
     if (codes) {
-        cudaFreeAsync(codes, s); cudaFreeAsync(idx, s); cudaFreeAsync(ktmp, s);
-        cudaFreeAsync(vtmp, s); cudaFreeAsync(hist, s);
+        cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);
+        cudaFreeAsync(hist, s);
+        if (idx && idx != plan_perm) cudaFreeAsync(idx, s);
     }
     if (rc) return rc;
     DIP_CUDA_TRY(cudaGetLastError());

@@ -6,36 +6,6 @@
 
 #include "common.cuh"
 
-namespace dip {
-// Scheduling record of the last forward query batch: per-packet warp steps,
-// written by the forward kernel, read by an adjoint on the same queries.  A
-// performance hint only; guarded for concurrent forward calls.
-struct SchedRecord {
-    std::mutex mu;
-    uint32_t* cost = nullptr;  // allocated at tree build (stream ordered), grown synchronously
-    int64_t cap = 0;
-    const float* queries = nullptr;
-    int64_t q = -1;
-    // Capacity for np packets.  Growing frees the old buffer with cudaFree,
-    // which first waits for the device, so no kernel still reads it.
-    bool ensure(int64_t np) {
-        if (np <= cap) return true;
-        if (cost) cudaFree(cost);
-        cost = nullptr;
-        cap = 0;
-        queries = nullptr;
-        if (cudaMalloc((void**)&cost, sizeof(uint32_t) * (size_t)np) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        cap = np;
-        return true;
-    }
-    ~SchedRecord() {
-        if (cost) cudaFree(cost);
-    }
-};
-}  // namespace dip
 
 struct dipole_tree {
     int device = 0;
@@ -68,7 +38,6 @@ struct dipole_tree {
     float* bbox = nullptr;       // device: lo.xyz, ext, 1024/ext
     float bbox_host[5] = {0, 0, 0, 1, 1024};
     int* status = nullptr;       // device status word
-    dip::SchedRecord* sched = new dip::SchedRecord();
 
     // attributes (set by refit)
     int C = 0;
@@ -115,10 +84,13 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
 // Tree update of node moments (eq. farfield_dipole_features).
 int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
 
-// Queries.  mode: 0 forward (out), 1 adjoint (g -> grad), 2 counts.
+// Queries.  mode: 0 forward (out), 1 adjoint (g -> grad), 2 counts.  Query plan
+// (caller-owned, optional): plan_in = false writes the Morton permutation into
+// plan_perm [q] and each packet's warp steps into plan_cost [ceil(q/32)];
+// plan_in = true reads them instead of sorting, and runs packets longest first.
 int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta,
           float* out, const float* g, float* grad, int accumulate, int32_t* counts,
-          cudaStream_t s);
+          uint32_t* plan_perm, uint32_t* plan_cost, bool plan_in, cudaStream_t s);
 
 // Forward queries with all scratch in a static device array (no allocation);
 // q <= noalloc_max_queries().

@@ -448,7 +448,7 @@ cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
 }
 
 
-// Point arrays, status word, bounding box and scheduling record of a new tree.
+// Point arrays, status word and bounding box of a new tree.
 int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     const int64_t n = t->n;
     DIP_CUDA_TRY(dalloc(&t->pts, n, s));
@@ -457,10 +457,6 @@ int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     DIP_CUDA_TRY(dalloc(&t->leaf_of, n, s));
     DIP_CUDA_TRY(dalloc(&t->bbox, 8, s));
     DIP_CUDA_TRY(dalloc(&t->status, 1, s));
-    // scheduling record of the query kernels: one entry per 32 points covers
-    // query batches up to the point count without growing
-    t->sched->cap = std::max<int64_t>(4096, (n + 31) / 32);
-    DIP_CUDA_TRY(dalloc(&t->sched->cost, t->sched->cap, s));
     DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
     return 0;
 }

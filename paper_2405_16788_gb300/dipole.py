@@ -34,7 +34,7 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
             "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
-            "dipole_tree_import"]
+            "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned"]
 
 
 class DipoleError(RuntimeError):
@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_refit": [P, P, I32, I32, P],
             "dipole_forward": [P, P, I64, F, P, P],
             "dipole_forward_noalloc": [P, P, I64, F, P, P],
+            "dipole_forward_planned": [P, P, I64, F, P, P, P, P],
+            "dipole_adjoint_planned": [P, P, I64, F, P, P, I32, P, P, P],
             "dipole_adjoint": [P, P, I64, F, P, P, I32, P],
             "dipole_query_counts": [P, P, I64, F, P, P],
             "dipole_sync_status": [P, P],
@@ -182,6 +184,41 @@ def dipole_adjoint(tree: int, queries: torch.Tensor, beta: float, grad_out: torc
                                          q, float(beta), _dev(grad_out, "grad_out"),
                                          _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)),
                                          _stream(stream)))
+
+
+class QueryPlan:
+    """Caller-owned query plan: the Morton order of a query batch and each
+    32-query packet's traversal steps, written by dipole_forward_planned and
+    read by dipole_adjoint_planned on the same queries."""
+
+    def __init__(self, q: int, device):
+        self.q = int(q)
+        self.perm = torch.empty(max(self.q, 1), dtype=torch.int32, device=device)
+        self.cost = torch.empty(max((self.q + 31) // 32, 1), dtype=torch.int32, device=device)
+
+
+def dipole_forward_planned(tree: int, queries: torch.Tensor, beta: float, out: torch.Tensor,
+                           plan: QueryPlan, stream=None):
+    q = int(queries.shape[0])
+    if plan.q != q:
+        raise ValueError("plan was made for another query count")
+    _check(load_library().dipole_forward_planned(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _dev(out, "out"), ctypes.c_void_p(plan.perm.data_ptr()),
+        ctypes.c_void_p(plan.cost.data_ptr()), _stream(stream)))
+
+
+def dipole_adjoint_planned(tree: int, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                           grad_attrs: torch.Tensor, plan: QueryPlan, accumulate: bool = False,
+                           stream=None):
+    q = int(queries.shape[0])
+    if plan.q != q:
+        raise ValueError("plan was made for another query count")
+    _check(load_library().dipole_adjoint_planned(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _dev(grad_out, "grad_out"), _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)),
+        ctypes.c_void_p(plan.perm.data_ptr()), ctypes.c_void_p(plan.cost.data_ptr()),
+        _stream(stream)))
 
 
 def dipole_query_counts(tree: int, queries: torch.Tensor, beta: float, counts: torch.Tensor,
@@ -317,25 +354,35 @@ class DipoleTree:
         self._attrs = attrs
 
     def forward(self, queries: torch.Tensor, beta: float, out: torch.Tensor | None = None,
-                stream=None) -> torch.Tensor:
+                plan: QueryPlan | None = None, stream=None) -> torch.Tensor:
+        """Primal queries; with `plan`, also record the query plan for the adjoint."""
         if self.C == 0:
             raise DipoleError(DIPOLE_ESTATE, "refit first")
         if out is None:
             out = torch.empty((queries.shape[0], self.C), device=queries.device,
                               dtype=torch.float32)
-        dipole_forward(self.handle, queries, beta, out, stream)
+        if plan is None:
+            dipole_forward(self.handle, queries, beta, out, stream)
+        else:
+            dipole_forward_planned(self.handle, queries, beta, out, plan, stream)
         return out
 
     def adjoint(self, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
                 grad_attrs: torch.Tensor | None = None, accumulate: bool = False,
-                stream=None) -> torch.Tensor:
+                plan: QueryPlan | None = None, stream=None) -> torch.Tensor:
+        """Two-stage adjoint; with `plan` from a forward on the same queries,
+        reuse its query order and schedule the longest packets first."""
         if self.C == 0:
             raise DipoleError(DIPOLE_ESTATE, "refit first")
         if grad_attrs is None:
             grad_attrs = torch.empty((self.n, self.C), device=queries.device, dtype=torch.float32)
             accumulate = False
-        dipole_adjoint(self.handle, queries, beta, grad_out.contiguous(), grad_attrs, accumulate,
-                       stream)
+        if plan is None:
+            dipole_adjoint(self.handle, queries, beta, grad_out.contiguous(), grad_attrs,
+                           accumulate, stream)
+        else:
+            dipole_adjoint_planned(self.handle, queries, beta, grad_out.contiguous(), grad_attrs,
+                                   plan, accumulate, stream)
         return grad_attrs
 
     def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
@@ -358,7 +405,9 @@ class DipoleSum(torch.autograd.Function):
     @staticmethod
     def forward(ctx, attrs, tree: DipoleTree, queries, beta: float):
         tree.refit(attrs)
-        out = tree.forward(queries, beta)
+        plan = QueryPlan(queries.shape[0], queries.device)
+        out = tree.forward(queries, beta, plan=plan)
+        ctx.plan = plan
         ctx.tree = tree
         ctx.beta = float(beta)
         ctx.C = tree.C
@@ -374,7 +423,8 @@ class DipoleSum(torch.autograd.Function):
         if tree.C != ctx.C:
             raise DipoleError(DIPOLE_ESTATE, "the tree was refit with another channel count "
                                              "between forward and backward")
-        g = tree.adjoint(queries, ctx.beta, grad_out.to(torch.float32).contiguous())
+        g = tree.adjoint(queries, ctx.beta, grad_out.to(torch.float32).contiguous(),
+                         plan=ctx.plan)
         return g.to(ctx.attr_dtype).reshape(ctx.attr_shape), None, None, None
 
 

@@ -197,3 +197,30 @@ def test_full_size_scene_1m_sampled_adjoint():
     ot.update(w.mu)
     ref = ot.adjoint(w.queries[idx], 2.0, g[idx].astype(np.float64))
     assert np.all(normwise(ga, ref) <= TOL), normwise(ga, ref)
+
+
+def test_planned_forward_and_adjoint_match_unplanned():
+    """The query plan (Morton order + packet costs written by the forward)
+    changes only the order of work: results equal the plain calls', also when
+    the plan came from a different query batch of the same size."""
+    from paper_2405_16788_gb300 import dipole
+    w = syn.workload("scene-200k", scale=0.3)  # enough packets for longest-first scheduling
+    q = to_dev(w.queries[:120000])
+    g = to_dev(syn.upstream_grad(120000, 4, seed=12))
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    y = gt.forward(q, 2.0).cpu().numpy()
+    a = gt.adjoint(q, 2.0, g).cpu().numpy()
+    plan = dipole.QueryPlan(120000, q.device)
+    yp = gt.forward(q, 2.0, plan=plan).cpu().numpy()
+    ap = gt.adjoint(q, 2.0, g, plan=plan).cpu().numpy()
+    assert np.array_equal(y, yp)
+    assert np.all(normwise(ap, a) <= 1e-5)
+    perm = plan.perm.cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(120000))
+    # a plan made on other queries of the same size
+    q2 = to_dev(w.queries[150000:270000])
+    gt.forward(q2, 2.0, plan=plan)
+    ap2 = gt.adjoint(q, 2.0, g, plan=plan).cpu().numpy()
+    assert np.all(normwise(ap2, a) <= 1e-5)
+    gt.sync_status()
