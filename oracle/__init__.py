@@ -72,6 +72,9 @@ def _load():
         lib.orc_tree_update.argtypes = [_P, _P, _I]
         lib.orc_bh_forward.argtypes = [_P, _I64, _P, _F, _P, _P]
         lib.orc_bh_adjoint.argtypes = [_P, _I64, _P, _F, _P, _P]
+        lib.orc_brute_forward_grad.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P]
+        lib.orc_bh_forward_grad.argtypes = [_P, _I64, _P, _F, _P]
+        lib.orc_bh_adjoint_grad.argtypes = [_P, _I64, _P, _F, _P, _P, _P]
         lib.orc_far_test.restype = _I
         lib.orc_far_test.argtypes = [_P, _P, _F, _F]
         _lib = lib
@@ -148,6 +151,21 @@ def brute_adjoint(points, normals, areas, eps, queries, g):
     return out
 
 
+def brute_forward_grad(points, normals, areas, eps, mu, queries):
+    """Plain O(NQ) spatial gradient of the dipole sum (reading R9): [Q, C, 3]."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    mu = _f32(mu)
+    if mu.ndim == 1:
+        mu = mu[:, None]
+    q = _f32(queries)
+    n, C, nq = p.shape[0], mu.shape[1], q.shape[0]
+    out = np.zeros((nq, C, 3), np.float64)
+    _load().orc_brute_forward_grad(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, _ptr(mu), nq,
+                                   _ptr(q), _ptr(out))
+    return out
+
+
 def far_test(x, c, r, beta) -> bool:
     """The far test of Alg. 1 in the float operation order the oracle uses."""
     xx, cc = _f32(x), _f32(c)
@@ -216,6 +234,29 @@ class Tree:
         cnt = np.zeros((nq, 3), np.int64) if counters else None
         _load().orc_bh_forward(self._h, nq, _ptr(q), float(beta), _ptr(out), _ptr(cnt))
         return (out, cnt) if counters else out
+
+    def forward_grad(self, queries, beta):
+        """Barnes-Hut spatial gradient of the dipole sum: [Q, C, 3] float64."""
+        if self.C is None:
+            raise RuntimeError("call update() first")
+        q = _f32(queries)
+        out = np.zeros((q.shape[0], self.C, 3), np.float64)
+        _load().orc_bh_forward_grad(self._h, q.shape[0], _ptr(q), float(beta), _ptr(out))
+        return out
+
+    def adjoint_grad(self, queries, beta, g=None, gg=None):
+        """dL/dmu [N, C] for dL/dD = g [Q, C] and dL/d(grad D) = gg [Q, C, 3] (either may
+        be None), two-stage (Sec. 6.2, App. C) extended to the gradient (R9)."""
+        if self.C is None:
+            raise RuntimeError("call update() first")
+        q = _f32(queries)
+        nq = q.shape[0]
+        g64 = None if g is None else _f64(np.asarray(g).reshape(nq, self.C))
+        gg64 = None if gg is None else _f64(np.asarray(gg).reshape(nq, self.C, 3))
+        out = np.zeros((self.n, self.C), np.float64)
+        _load().orc_bh_adjoint_grad(self._h, nq, _ptr(q), float(beta), _ptr(g64), _ptr(gg64),
+                                    _ptr(out))
+        return out
 
     def adjoint(self, queries, beta, g):
         """Two-stage adjoint (Sec. 6.2, App. C): dL/dmu [N, C] float64, input order."""

@@ -38,6 +38,13 @@
  *       is that product rounded to float; the node radius is the largest float
  *       distance from that float centroid to a point of the node.
  *   R8  AS(m) in eq. (farfield_features_gradient) includes the leaf holding m.
+ *   R9  Spatial gradient (the paper needs grad D for eq. surface_density and
+ *       the implicit normal of Sec. 5.1 but does not say how it is computed):
+ *       the gradient in x of each term, with u = p - x, r = |u|, t = r/eps,
+ *       is -A/(4 pi) [a n + b (n.u) u], a = rho/r^3,
+ *       b = rho'(t)/(eps r^4) - 3 rho/r^5, rho'(t) = (4/sqrt(pi)) t^2 exp(-t^2);
+ *       a far node uses the same with n -> n~^c, p -> p~, eps -> eps~, A -> A~.
+ *       A zero-distance term contributes nothing to D or to grad D.
  *
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
  * the radius are specified operation by operation.
@@ -89,6 +96,38 @@ static double point_weight(const double x[3], double px, double py, double pz,
     return A * rho_r(r, eps) * (nx * dx + ny * dy + nz * dz) / (4.0 * ORC_PI * r2 * r);
 }
 
+/* a = rho/r^3 and b = rho'(t)/(eps r^4) - 3 rho/r^5 of reading R9 (r > 0). */
+static void grad_factors(double r, double eps, double* a, double* b) {
+    double r3 = r * r * r;
+    if (eps == 0.0) {
+        *a = 1.0 / r3;
+        *b = -3.0 / (r3 * r * r);
+        return;
+    }
+    double t = r / eps;
+    double rho = orc_rho(t);
+    double drho = 4.0 / sqrt(ORC_PI) * t * t * exp(-t * t);
+    *a = rho / r3;
+    *b = drho / (eps * r3 * r) - 3.0 * rho / (r3 * r * r);
+}
+
+/* Gradient in x of A P_eps(x, p): -A/(4 pi) [a n + b (n.u) u], u = p - x (R9).
+ * g receives 3 values; zero when x == p. */
+static void point_grad(const double x[3], double px, double py, double pz, double nx,
+                       double ny, double nz, double A, double eps, double g[3]) {
+    double ux = px - x[0], uy = py - x[1], uz = pz - x[2];
+    double r2 = ux * ux + uy * uy + uz * uz;
+    g[0] = g[1] = g[2] = 0.0;
+    if (r2 == 0.0) return;
+    double a, b;
+    grad_factors(sqrt(r2), eps, &a, &b);
+    double nu = nx * ux + ny * uy + nz * uz;
+    double f = -A / (4.0 * ORC_PI);
+    g[0] = f * (a * nx + b * nu * ux);
+    g[1] = f * (a * ny + b * nu * uy);
+    g[2] = f * (a * nz + b * nu * uz);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Brute force: the plain definition, eq. (dipole_sum) / (appearance_features) */
 /* ------------------------------------------------------------------------ */
@@ -108,6 +147,26 @@ void orc_brute_forward(int64_t n, const float* pts, const float* nrm, const floa
                                     nrm[3 * m + 1], nrm[3 * m + 2], area[m],
                                     eps ? (double)eps[m] : 0.0);
             for (int c = 0; c < C; ++c) o[c] += w * (double)mu[m * C + c];
+        }
+    }
+}
+
+/* Spatial gradient of the dipole sum: grad[(j*C + c)*3 + k] = d D^c / d x_k at
+ * x_j (R9), the plain definition. */
+void orc_brute_forward_grad(int64_t n, const float* pts, const float* nrm, const float* area,
+                            const float* eps, int C, const float* mu, int64_t q,
+                            const float* qry, double* grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < q; ++j) {
+        double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double* o = grad + j * C * 3;
+        for (int k = 0; k < 3 * C; ++k) o[k] = 0.0;
+        for (int64_t m = 0; m < n; ++m) {
+            double g[3];
+            point_grad(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], nrm[3 * m], nrm[3 * m + 1],
+                       nrm[3 * m + 2], area[m], eps ? (double)eps[m] : 0.0, g);
+            for (int c = 0; c < C; ++c)
+                for (int k = 0; k < 3; ++k) o[3 * c + k] += g[k] * (double)mu[m * C + c];
         }
     }
 }
@@ -552,6 +611,144 @@ void orc_bh_adjoint(const orc_tree* T, int64_t q, const float* qry, float beta, 
         float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
         double x[3] = {xf[0], xf[1], xf[2]};
         adjoint_query(T, xf, x, g + j * C, 0, beta, dnt, dmu);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < n; ++m) {
+        double* gm = grad + (int64_t)T->perm[m] * C;
+        for (int c = 0; c < C; ++c) gm[c] = dmu[m * C + c];
+        for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
+            double f = (double)T->A[m] / T->area[t];
+            const double* d = dnt + (int64_t)t * 3 * C;
+            for (int c = 0; c < C; ++c)
+                gm[c] += f * (T->nrm[3 * m] * d[3 * c] + T->nrm[3 * m + 1] * d[3 * c + 1] +
+                              T->nrm[3 * m + 2] * d[3 * c + 2]);
+        }
+    }
+    free(dnt);
+    free(dmu);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial gradient with Barnes-Hut (R9) and its adjoint                      */
+/* ------------------------------------------------------------------------ */
+
+/* PrimalQuery for grad D: the same walk and far test; a far node adds
+ * -A~/(4 pi) [a n~^c + b (n~^c.v) v], v = p~ - x; an opened leaf adds its
+ * points' exact gradients. */
+static void primal_query_grad(const orc_tree* T, const float xf[3], const double x[3], int32_t t,
+                              float beta, double* g) {
+    int C = T->C;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
+        double vx = T->cen[3 * t] - x[0], vy = T->cen[3 * t + 1] - x[1], vz = T->cen[3 * t + 2] - x[2];
+        double d = sqrt(vx * vx + vy * vy + vz * vz);
+        double a, b;
+        grad_factors(d, T->epsn[t], &a, &b);
+        double f = -T->area[t] / (4.0 * ORC_PI);
+        const double* nt = T->nt + (int64_t)t * 3 * C;
+        for (int c = 0; c < C; ++c) {
+            double nv = nt[3 * c] * vx + nt[3 * c + 1] * vy + nt[3 * c + 2] * vz;
+            g[3 * c] += f * (a * nt[3 * c] + b * nv * vx);
+            g[3 * c + 1] += f * (a * nt[3 * c + 1] + b * nv * vy);
+            g[3 * c + 2] += f * (a * nt[3 * c + 2] + b * nv * vz);
+        }
+        return;
+    }
+    if (T->is_leaf[t]) {
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double pg[3];
+            point_grad(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2], T->nrm[3 * m],
+                       T->nrm[3 * m + 1], T->nrm[3 * m + 2], T->A[m], T->eps[m], pg);
+            for (int c = 0; c < C; ++c)
+                for (int k = 0; k < 3; ++k) g[3 * c + k] += pg[k] * T->mu[m * C + c];
+        }
+        return;
+    }
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c]) primal_query_grad(T, xf, x, c, beta, g);
+}
+
+/* grad[(j*C + c)*3 + k] = Barnes-Hut estimate of d D^c / d x_k at qry[j]. */
+void orc_bh_forward_grad(const orc_tree* T, int64_t q, const float* qry, float beta, double* grad) {
+    int C = T->C;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        double* o = grad + j * 3 * C;
+        for (int k = 0; k < 3 * C; ++k) o[k] = 0.0;
+        primal_query_grad(T, xf, x, 0, beta, o);
+    }
+}
+
+/* AdjointQuery for L(D, grad D): gv[c] = dL/dD^c, gg[3c + k] = dL/d(dD^c/dx_k)
+ * at this query (either may be NULL).  A far node gets
+ *   d n~^c += A~ rho v/(4 pi d^3) gv[c] + M gg^c,  M = -A~/(4 pi) (a I + b v v^T),
+ * an opened leaf's point m gets the exact derivative of its terms. */
+static void adjoint_query_grad(const orc_tree* T, const float xf[3], const double x[3],
+                               const double* gv, const double* gg, int32_t t, float beta,
+                               double* dnt, double* dmu) {
+    int C = T->C;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
+        double vx = T->cen[3 * t] - x[0], vy = T->cen[3 * t + 1] - x[1], vz = T->cen[3 * t + 2] - x[2];
+        double d = sqrt(vx * vx + vy * vy + vz * vz);
+        double a, b;
+        grad_factors(d, T->epsn[t], &a, &b);
+        double fa = T->area[t] / (4.0 * ORC_PI);
+        double* o = dnt + (int64_t)t * 3 * C;
+        for (int c = 0; c < C; ++c) {
+            double inc[3] = {0.0, 0.0, 0.0};
+            if (gv) { /* d/d n~ of A~ a n~.v / (4 pi) = A~ a v / (4 pi) */
+                inc[0] += fa * a * vx * gv[c]; inc[1] += fa * a * vy * gv[c]; inc[2] += fa * a * vz * gv[c];
+            }
+            if (gg) {
+                const double* G = gg + 3 * c;
+                double vg = vx * G[0] + vy * G[1] + vz * G[2];
+                inc[0] -= fa * (a * G[0] + b * vg * vx);
+                inc[1] -= fa * (a * G[1] + b * vg * vy);
+                inc[2] -= fa * (a * G[2] + b * vg * vz);
+            }
+            for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+                o[3 * c + k] += inc[k];
+            }
+        }
+        return;
+    }
+    if (T->is_leaf[t]) {
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double w = point_weight(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2], T->nrm[3 * m],
+                                    T->nrm[3 * m + 1], T->nrm[3 * m + 2], T->A[m], T->eps[m]);
+            double pg[3];
+            point_grad(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2], T->nrm[3 * m],
+                       T->nrm[3 * m + 1], T->nrm[3 * m + 2], T->A[m], T->eps[m], pg);
+            for (int c = 0; c < C; ++c) {
+                double inc = 0.0;
+                if (gv) inc += w * gv[c];
+                if (gg) inc += pg[0] * gg[3 * c] + pg[1] * gg[3 * c + 1] + pg[2] * gg[3 * c + 2];
+#pragma omp atomic
+                dmu[m * C + c] += inc;
+            }
+        }
+        return;
+    }
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c])
+        adjoint_query_grad(T, xf, x, gv, gg, c, beta, dnt, dmu);
+}
+
+/* dL/dmu [n, C] (input order) for dL/dD = g [q, C] (may be NULL) and
+ * dL/d(grad D) = gg [q, C, 3] (may be NULL): stage 1 as above, stage 2 by
+ * eq. (farfield_features_gradient). */
+void orc_bh_adjoint_grad(const orc_tree* T, int64_t q, const float* qry, float beta,
+                         const double* g, const double* gg, double* grad) {
+    int C = T->C;
+    int64_t n = T->n, nn = T->nn;
+    double* dnt = (double*)calloc((size_t)(nn * 3 * C), sizeof(double));
+    double* dmu = (double*)calloc((size_t)(n * C), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        adjoint_query_grad(T, xf, x, g ? g + j * C : NULL, gg ? gg + j * 3 * C : NULL, 0, beta,
+                           dnt, dmu);
     }
 #pragma omp parallel for schedule(static)
     for (int64_t m = 0; m < n; ++m) {
