@@ -209,6 +209,49 @@ int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, f
                            const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream);
 
 /*
+ * Spatial gradient of the dipole sum with respect to the query position.  The
+ * paper differentiates D only with respect to the point attributes (Sec. 6.2);
+ * the position gradient follows from the same kernel (Sec. 4.1, eq.
+ * regularized_poisson) and serves losses on the field's normal or slope.
+ * With u = p - x, r = |u|, a = rho(r/eps)/r^3 and b = a'(r)/r, a point adds
+ * -A mu (a n + b (n.u) u)/(4 pi); a far node (eq. farfield, v = p~ - x) adds
+ * -(a S + b (S.v) v)/(4 pi).  Same walk and far decisions as dipole_forward.
+ *
+ *   queries [q,3] float
+ *   out     [q, channels] float: D, as dipole_forward; may be NULL
+ *   grad_x  [q, channels, 3] float: grad_x[j, c, k] = dD^c/dx_k at queries[j]
+ *   plan_perm, plan_cost: a query plan as for dipole_forward_planned, written
+ *           here; both NULL (no plan) or both set
+ *
+ * Channels are walked in groups of up to 4 (one traversal per group).
+ * Errors: as dipole_forward; grad_x is required.
+ */
+int dipole_forward_grad(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        float* out, float* grad_x, uint32_t* plan_perm, uint32_t* plan_cost,
+                        void* stream);
+
+/*
+ * Adjoint of dipole_forward_grad: dL/dmu for a loss of D and grad D, given
+ * grad_out[j, c] = dL/dD^c and grad_grad[j, c, k] = dL/d(dD^c/dx_k) (either
+ * may be NULL, not both).  Stage 1 adds, at a far node,
+ *   [a g^c v - a G^c - b (v.G^c) v]/(4 pi)  to dS_t^c,
+ * and at a point of an opened leaf (w = A n)
+ *   [a (w.u) g^c - a (w.G^c) - b (w.u)(u.G^c)]/(4 pi)  to dmu_m^c;
+ * stage 2 is that of dipole_adjoint (eq. farfield_features_gradient).
+ *
+ *   grad_attrs [n, channels] float, caller's point order; accumulate 0 or 1
+ *   plan_perm, plan_cost: NULL, or the plan of a dipole_forward_grad on the
+ *           same queries (read, as in dipole_adjoint_planned)
+ *
+ * With grad_grad NULL the result equals dipole_adjoint's.  Uses the tree's
+ * adjoint scratch: adjoint calls on one tree must not overlap.
+ */
+int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        const float* grad_out, const float* grad_grad, float* grad_attrs,
+                        int32_t accumulate, const uint32_t* plan_perm, const uint32_t* plan_cost,
+                        void* stream);
+
+/*
  * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,
  * leaf points summed} (int32 [q,3], device).  Same traversal and decisions as
  * dipole_forward; used for the roofline's algorithmic bytes and to check the

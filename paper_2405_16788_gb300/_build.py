@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdipole.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["capi.cu", "sort.cu", "tree_build.cu", "refit.cu", "traverse.cu"]
+SOURCES = ["capi.cu", "sort.cu", "tree_build.cu", "refit.cu", "traverse.cu", "traverse_grad.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "tree.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

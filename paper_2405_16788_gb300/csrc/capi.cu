@@ -180,8 +180,10 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
     if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_forward: q must be < 2^31");
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward: beta must be > 0");
     if (q == 0) return DIPOLE_OK;
-    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr, nullptr,
-                      nullptr, false, as_stream(stream));
+    dip::QueryCall c;
+    c.mode = dip::kForward;
+    c.queries = queries; c.q = q; c.beta = beta; c.out = out;
+    return dip::query(tree, c, as_stream(stream));
 }
 
 int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -213,8 +215,11 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: beta must be > 0");
     if (accumulate != 0 && accumulate != 1)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: accumulate must be 0 or 1");
-    return dip::query(tree, 1, queries, q, beta, nullptr, grad_out, grad_attrs, accumulate,
-                      nullptr, nullptr, nullptr, false, as_stream(stream));
+    dip::QueryCall c;
+    c.mode = dip::kAdjoint;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.grad = grad_attrs; c.accumulate = accumulate;
+    return dip::query(tree, c, as_stream(stream));
 }
 
 int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -227,8 +232,11 @@ int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_
         return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: queries, out and the plan are required");
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: beta must be > 0");
     if (q == 0) return DIPOLE_OK;
-    return dip::query(tree, 0, queries, q, beta, out, nullptr, nullptr, 0, nullptr, plan_perm,
-                      plan_cost, false, as_stream(stream));
+    dip::QueryCall c;
+    c.mode = dip::kForward;
+    c.queries = queries; c.q = q; c.beta = beta; c.out = out;
+    c.plan_perm = plan_perm; c.plan_cost = plan_cost;
+    return dip::query(tree, c, as_stream(stream));
 }
 
 int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -244,9 +252,61 @@ int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, f
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: beta must be > 0");
     if (accumulate != 0 && accumulate != 1)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: accumulate must be 0 or 1");
-    return dip::query(tree, 1, queries, q, beta, nullptr, grad_out, grad_attrs, accumulate, nullptr,
-                      const_cast<uint32_t*>(plan_perm), const_cast<uint32_t*>(plan_cost), true,
-                      as_stream(stream));
+    dip::QueryCall c;
+    c.mode = dip::kAdjoint;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.grad = grad_attrs; c.accumulate = accumulate;
+    c.plan_perm = const_cast<uint32_t*>(plan_perm);
+    c.plan_cost = const_cast<uint32_t*>(plan_cost);
+    c.plan_in = true;
+    return dip::query(tree, c, as_stream(stream));
+}
+
+int dipole_forward_grad(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        float* out, float* grad_x, uint32_t* plan_perm, uint32_t* plan_cost,
+                        void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_grad: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: q must be in [0, 2^31)");
+    if (q > 0 && (!queries || !grad_x))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: queries and grad_x are required");
+    if ((plan_perm == nullptr) != (plan_cost == nullptr))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: plan_perm and plan_cost go together");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    dip::QueryCall c;
+    c.mode = dip::kForwardGrad;
+    c.queries = queries; c.q = q; c.beta = beta; c.out = out; c.gout = grad_x;
+    c.plan_perm = plan_perm; c.plan_cost = plan_cost;
+    return dip::query(tree, c, as_stream(stream));
+}
+
+int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        const float* grad_out, const float* grad_grad, float* grad_attrs,
+                        int32_t accumulate, const uint32_t* plan_perm, const uint32_t* plan_cost,
+                        void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_grad: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: q must be in [0, 2^31)");
+    if (!grad_attrs) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: grad_attrs is required");
+    if (q > 0 && (!queries || (!grad_out && !grad_grad)))
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_adjoint_grad: queries and one of grad_out, grad_grad are required");
+    if ((plan_perm == nullptr) != (plan_cost == nullptr))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: plan_perm and plan_cost go together");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: accumulate must be 0 or 1");
+    dip::QueryCall c;
+    c.mode = dip::kAdjointGrad;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.gg = grad_grad; c.grad = grad_attrs; c.accumulate = accumulate;
+    c.plan_perm = const_cast<uint32_t*>(plan_perm);
+    c.plan_cost = const_cast<uint32_t*>(plan_cost);
+    c.plan_in = plan_perm != nullptr;
+    return dip::query(tree, c, as_stream(stream));
 }
 
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -258,8 +318,10 @@ int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q
     if (q > (int64_t)INT32_MAX) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: q must be < 2^31");
     if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: beta must be > 0");
     if (q == 0) return DIPOLE_OK;
-    return dip::query(tree, 2, queries, q, beta, nullptr, nullptr, nullptr, 0, counts, nullptr,
-                      nullptr, false, as_stream(stream));
+    dip::QueryCall c;
+    c.mode = dip::kCount;
+    c.queries = queries; c.q = q; c.beta = beta; c.counts = counts;
+    return dip::query(tree, c, as_stream(stream));
 }
 
 int dipole_sync_status(dipole_tree* tree, void* stream) {

@@ -181,4 +181,58 @@ __device__ __forceinline__ void adjoint_point_reduce(float k, const float* gp, f
     if (lane_owns<CH>(lane) && a0 != 0.0f) atomicAdd(dst + kept, a0);
 }
 
+// Generalized forms of the two reductions above: the lane supplies its values
+// already in lane_channel_order (v[3i + k] for channel ord[i], axis k).
+template <int CH>
+__device__ __forceinline__ void adjoint_vec_reduce(const float (&v)[3 * CH], float* dst, int kept,
+                                                   int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float a0 = v[0], a1 = v[1], a2 = v[2];
+    if constexpr (CH == 4) {
+        float a3 = v[3] + __shfl_xor_sync(FULL, v[9], 16);
+        float a4 = v[4] + __shfl_xor_sync(FULL, v[10], 16);
+        float a5 = v[5] + __shfl_xor_sync(FULL, v[11], 16);
+        a0 += __shfl_xor_sync(FULL, v[6], 16);
+        a1 += __shfl_xor_sync(FULL, v[7], 16);
+        a2 += __shfl_xor_sync(FULL, v[8], 16);
+        a0 += __shfl_xor_sync(FULL, a3, 8);
+        a1 += __shfl_xor_sync(FULL, a4, 8);
+        a2 += __shfl_xor_sync(FULL, a5, 8);
+    } else if constexpr (CH == 2) {
+        a0 += __shfl_xor_sync(FULL, v[3], 16);
+        a1 += __shfl_xor_sync(FULL, v[4], 16);
+        a2 += __shfl_xor_sync(FULL, v[5], 16);
+    }
+#pragma unroll
+    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(FULL, a0, off);
+        a1 += __shfl_xor_sync(FULL, a1, off);
+        a2 += __shfl_xor_sync(FULL, a2, off);
+    }
+    if (lane_owns<CH>(lane)) {
+        float* d = dst + 3 * kept;
+        if (a0 != 0.0f) atomicAdd(d, a0);
+        if (a1 != 0.0f) atomicAdd(d + 1, a1);
+        if (a2 != 0.0f) atomicAdd(d + 2, a2);
+    }
+}
+
+template <int CH>
+__device__ __forceinline__ void adjoint_scalar_reduce(const float (&v)[CH], float* dst, int kept,
+                                                      int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float a0 = v[0];
+    if constexpr (CH == 4) {
+        const float a1 = v[1] + __shfl_xor_sync(FULL, v[3], 16);
+        a0 += __shfl_xor_sync(FULL, v[2], 16);
+        a0 += __shfl_xor_sync(FULL, a1, 8);
+    } else if constexpr (CH == 2) {
+        a0 += __shfl_xor_sync(FULL, v[1], 16);
+    }
+#pragma unroll
+    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1)
+        a0 += __shfl_xor_sync(FULL, a0, off);
+    if (lane_owns<CH>(lane) && a0 != 0.0f) atomicAdd(dst + kept, a0);
+}
+
 }  // namespace dip

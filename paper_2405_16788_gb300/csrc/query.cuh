@@ -1,0 +1,87 @@
+// Pieces shared by the query kernels of traverse.cu (dipole sum and its
+// adjoint) and traverse_grad.cu (spatial gradient and its adjoint): the
+// kernel arguments, attribute row loads and the persistent grid size.
+#pragma once
+
+#include "kernels.cuh"
+#include "tree.cuh"
+
+namespace dip {
+
+constexpr int kQThreads = 256;
+
+struct QueryArgs {
+    const NodeRec* nodes;
+    const PointRec* pts;
+    unsigned nn;
+    int* status;
+    const float* q;
+    int64_t nq;
+    const uint32_t* qperm;
+    float beta;
+    int C;
+    int Cp;
+    const void* mu;
+    const float* S;
+    float* out;         // D [q, C]
+    float* gout;        // grad D [q, C, 3]
+    const float* g;     // dL/dD [q, C]
+    const float* gg;    // dL/d(grad D) [q, C, 3]
+    float* dS;
+    float* dmu;
+    int32_t* counts;
+    unsigned long long* work;
+    const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
+    uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
+};
+
+// n attribute values (n = 1, 2 or 4; p aligned to n elements) as floats.
+template <typename AT>
+__device__ __forceinline__ void load_row(const AT* p, float* v, int n);
+
+template <>
+__device__ __forceinline__ void load_row<float>(const float* p, float* v, int n) {
+    if (n == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if (n == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_row<__nv_bfloat16>(const __nv_bfloat16* p, float* v, int n) {
+    if (n == 4) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+        v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
+        v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
+    } else if (n == 2) {
+        const unsigned a = __ldg(reinterpret_cast<const unsigned*>(p));
+        v[0] = __uint_as_float(a << 16); v[1] = __uint_as_float(a & 0xffff0000u);
+    } else {
+        v[0] = __bfloat162float(p[0]);
+    }
+}
+
+// Blocks of a persistent query grid: enough for one warp per 32-query packet,
+// at most what stays resident on all SMs (per_sm caches the occupancy).
+template <typename Kernel>
+inline unsigned query_grid(Kernel kernel, int64_t nq, int& per_sm) {
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t need = (nq + 31) / 32;
+    const int64_t blocks = (need + (kQThreads / 32) - 1) / (kQThreads / 32);
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+// Launch the gradient query kernels (traverse_grad.cu) for mode kForwardGrad
+// or kAdjointGrad.
+int dispatch_grad(const dipole_tree* t, int mode, const QueryArgs& a, cudaStream_t s);
+
+}  // namespace dip

@@ -17,66 +17,10 @@
 // one set of atomics; the same holds for the points of an opened leaf.
 #include <mutex>
 
-#include "kernels.cuh"
-#include "tree.cuh"
+#include "query.cuh"
 
 namespace dip {
 namespace {
-
-constexpr int kQThreads = 256;
-enum { kForward = 0, kAdjoint = 1, kCount = 2 };
-
-struct QueryArgs {
-    const NodeRec* nodes;
-    const PointRec* pts;
-    unsigned nn;
-    int* status;
-    const float* q;
-    int64_t nq;
-    const uint32_t* qperm;
-    float beta;
-    int C;
-    const void* mu;
-    const float* S;
-    float* out;
-    const float* g;
-    float* dS;
-    float* dmu;
-    int32_t* counts;
-    unsigned long long* work;
-    const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
-    uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
-};
-
-template <typename AT>
-__device__ __forceinline__ void load_row(const AT* p, float* v, int n);
-
-template <>
-__device__ __forceinline__ void load_row<float>(const float* p, float* v, int n) {
-    if (n == 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    } else if (n == 2) {
-        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
-        v[0] = a.x; v[1] = a.y;
-    } else {
-        v[0] = __ldg(p);
-    }
-}
-
-template <>
-__device__ __forceinline__ void load_row<__nv_bfloat16>(const __nv_bfloat16* p, float* v, int n) {
-    if (n == 4) {
-        const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
-        v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
-        v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
-    } else if (n == 2) {
-        const unsigned a = __ldg(reinterpret_cast<const unsigned*>(p));
-        v[0] = __uint_as_float(a << 16); v[1] = __uint_as_float(a & 0xffff0000u);
-    } else {
-        v[0] = __bfloat162float(p[0]);
-    }
-}
 
 template <int CP, typename AT, int MODE>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
@@ -287,14 +231,8 @@ constexpr int64_t kOrderMinPackets = 2048;
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
     static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query<CP, AT, MODE>, kQThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
-    int64_t need = (a.nq + 31) / 32;                       // warp packets
-    int64_t blocks = (need + (kQThreads / 32) - 1) / (kQThreads / 32);
-    int64_t cap = (int64_t)num_sms() * per_sm;
-    note_launch(); k_query<CP, AT, MODE><<<(unsigned)(blocks < cap ? blocks : cap), kQThreads, 0, s>>>(a);
+    const unsigned grid = query_grid(k_query<CP, AT, MODE>, a.nq, per_sm);
+    note_launch(); k_query<CP, AT, MODE><<<grid, kQThreads, 0, s>>>(a);
 }
 
 template <int MODE>
@@ -390,10 +328,13 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.qperm = idx;
     a.beta = beta;
     a.C = t->C;
+    a.Cp = t->Cp;
     a.mu = t->mu;
     a.S = t->S;
     a.out = out;
+    a.gout = nullptr;
     a.g = nullptr;
+    a.gg = nullptr;
     a.dS = nullptr;
     a.dmu = nullptr;
     a.counts = nullptr;
@@ -406,9 +347,13 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     return 0;
 }
 
-int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta, float* out,
-          const float* g, float* grad, int accumulate, int32_t* counts, uint32_t* plan_perm,
-          uint32_t* plan_cost, bool plan_in, cudaStream_t s) {
+int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
+    const int mode = call.mode;
+    const int64_t q = call.q;
+    uint32_t* plan_perm = call.plan_perm;
+    uint32_t* plan_cost = call.plan_cost;
+    const bool plan_in = call.plan_in;
+    const bool adjoint = mode == kAdjoint || mode == kAdjointGrad;
     const int SR = srow(t->Cp > 0 ? t->Cp : 1);
     const int64_t np = (q + 31) / 32;
     uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
@@ -425,7 +370,7 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
             // Morton order of the queries: codes in the tree's cube, sorted with their indices
             if (plan_perm) idx = plan_perm;
             else DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
-            query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+            query_codes(call.queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
             radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
         }
     }
@@ -448,7 +393,7 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         }
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
-    if (mode == kAdjoint) {
+    if (adjoint) {
         DIP_CUDA_TRY(cudaMemsetAsync(t->dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
     }
@@ -459,26 +404,30 @@ int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float
         a.pts = t->pts;
         a.nn = (unsigned)t->nn;
         a.status = t->status;
-        a.q = queries;
+        a.q = call.queries;
         a.nq = q;
         a.qperm = idx;
-        a.beta = beta;
+        a.beta = call.beta;
         a.C = t->C;
+        a.Cp = t->Cp;
         a.mu = t->mu;
         a.S = t->S;
-        a.out = out;
-        a.g = g;
+        a.out = call.out;
+        a.gout = call.gout;
+        a.g = call.g;
+        a.gg = call.gg;
         a.dS = t->dS;
         a.dmu = t->dmu;
-        a.counts = counts;
+        a.counts = call.counts;
         a.work = work;
         a.porder = porder;
         a.pcost = pcost;
         if (mode == kForward) rc = dispatch<kForward>(t, a, s);
         else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
-        else rc = dispatch<kCount>(t, a, s);
+        else if (mode == kCount) rc = dispatch<kCount>(t, a, s);
+        else rc = dispatch_grad(t, mode, a, s);
     }
-    if (rc == 0 && mode == kAdjoint) rc = stage2(t, grad, accumulate, s);
+    if (rc == 0 && adjoint) rc = stage2(t, call.grad, call.accumulate, s);
     cudaFreeAsync(work, s);
     if (codes) {
         cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);

@@ -1,0 +1,317 @@
+// Spatial gradient of the Barnes-Hut dipole sum and its adjoint.
+//
+// The paper differentiates the sum only with respect to the point attributes
+// (Sec. 6.2); the gradient with respect to the query position follows from
+// the same kernel (Sec. 4.1, eq. regularized_poisson).  With u = p - x,
+// r = |u|, a(r) = rho(r/eps)/r^3 and b(r) = a'(r)/r, the term
+// A mu a(r) n.u/(4 pi) of eq. dipole_sum has the x-gradient
+//   -A mu/(4 pi) [a n + b (n.u) u],
+// and the far-field term rho(d/eps~) S.(p~ - x)/(4 pi d^3) of eq. farfield,
+// with v = p~ - x, has the x-gradient -[a S + b (S.v) v]/(4 pi).
+// The walk, the far test and the warp cooperation are those of traverse.cu
+// (Alg. 1): a lane takes exactly the decisions of its own depth-first walk.
+//
+// A query needs four running sums per channel (D and its three derivatives),
+// so the kernel handles CG <= 4 channels per walk and walks the tree once per
+// group of CG channels.  The adjoint of both outputs (dL/dD = g and
+// dL/d grad D = G) gives, for a far node,
+//   dS^c += [a g^c v - a G^c - b (v.G^c) v]/(4 pi),
+// and for a point of an opened leaf, with w = A n,
+//   dmu^c += [a (w.u) g^c - a (w.G^c) - b (w.u)(u.G^c)]/(4 pi);
+// stage 2 (eq. farfield_features_gradient) is unchanged.
+#include "query.cuh"
+
+namespace dip {
+namespace {
+
+// Series of (t rho'(t) - 3 rho(t))/t^5 in u = t^2, from the series of rho:
+// coefficient k-1 = (-1)^k (4/sqrt(pi)) 2k/(k! (2k+3)), k >= 1.  Seven terms
+// leave a relative error below 1e-8 at t = 0.5.
+constexpr float kGSer0 = -0.9027033336764101f;
+constexpr float kGSer1 = 0.6447880954831501f;
+constexpr float kGSer2 = -0.250750926021225f;
+constexpr float kGSer3 = 0.06838661618760682f;
+constexpr float kGSer4 = -0.014466399578147597f;
+constexpr float kGSer5 = 0.0025075092602122504f;
+constexpr float kGSer6 = -0.00036875136179591913f;
+
+// a = rho(d/eps)/d^3 and b = a'(d)/d = (t rho'(t) - 3 rho(t))/d^5, t = d/eps,
+// rho'(t) = (4/sqrt(pi)) t^2 exp(-t^2); d^2 = d2 > 0, inv_eps = 1/eps (+inf
+// for eps = 0).  Same branches as rho_over_d3.
+__device__ __forceinline__ void grad_factors(float d2, float inv_eps, float& a, float& b) {
+    const float inv_d = rsqrtf(d2);
+    const float inv_d2 = inv_d * inv_d;
+    const float inv_d3 = inv_d2 * inv_d;
+    const float t = d2 * inv_d * inv_eps;
+    if (t >= kTCut) {
+        a = inv_d3;
+        b = -3.0f * inv_d3 * inv_d2;
+        return;
+    }
+    const float u = t * t;
+    if (t < kTSeries) {
+        float p = kSer6;
+        p = fmaf(p, u, kSer5);
+        p = fmaf(p, u, kSer4);
+        p = fmaf(p, u, kSer3);
+        p = fmaf(p, u, kSer2);
+        p = fmaf(p, u, kSer1);
+        p = fmaf(p, u, kSer0);
+        float r = kGSer6;
+        r = fmaf(r, u, kGSer5);
+        r = fmaf(r, u, kGSer4);
+        r = fmaf(r, u, kGSer3);
+        r = fmaf(r, u, kGSer2);
+        r = fmaf(r, u, kGSer1);
+        r = fmaf(r, u, kGSer0);
+        const float ie2 = inv_eps * inv_eps, ie3 = ie2 * inv_eps;
+        a = p * ie3;
+        b = r * (ie3 * ie2);
+        return;
+    }
+    const float e = __expf(-u);
+    const float rho = erff(t) - kTwoOverSqrtPi * t * e;
+    const float trho1 = 2.0f * kTwoOverSqrtPi * u * t * e;  // t rho'(t)
+    a = rho * inv_d3;
+    b = (trho1 - 3.0f * rho) * (inv_d3 * inv_d2);
+}
+
+template <int CG, typename AT, int MODE>
+__global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) {
+    static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
+    constexpr bool FWD = MODE == kForwardGrad;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr unsigned kFoldSteps = 16;
+    constexpr int NV = FWD ? 4 * CG : 1;  // D and grad D per channel: [4c] D, [4c+1+k] d/dx_k
+    const int lane = threadIdx.x & 31;
+    const NodeRec* __restrict__ nodes = a.nodes;
+    const PointRec* __restrict__ pts = a.pts;
+    const unsigned nn = a.nn;
+    const int Cp = a.Cp;
+    const int SR = srow(Cp);
+
+    for (;;) {
+        unsigned long long pk = 0;
+        if (lane == 0) pk = atomicAdd(a.work, 1ull);
+        pk = __shfl_sync(FULL, pk, 0);
+        if ((int64_t)pk * 32 >= a.nq) break;
+        const int64_t pm = (int64_t)(a.porder ? a.porder[pk] : pk);
+        const int64_t qi = pm * 32 + lane;
+        const bool valid = qi < a.nq;
+        const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
+        int ord[CG];
+        lane_channel_order<CG>(lane, ord);
+        unsigned steps = 0;
+
+        for (int c0 = 0; c0 < Cp; c0 += CG) {
+            // forward: blocked Kahan sums (plain partial sums folded every
+            // kFoldSteps warp steps into compensated ones)
+            float acc[NV], cmp[NV], part[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) { acc[i] = 0.f; cmp[i] = 0.f; part[i] = 0.f; }
+            // adjoint: upstream values and gradients of this group, scaled by
+            // 1/(4 pi), in lane_channel_order
+            float gl[FWD ? 1 : CG], Gl[FWD ? 1 : 3 * CG];
+            if (!FWD) {
+                float gc[CG], Gc[3 * CG];
+#pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    const bool on = valid && c0 + c < a.C;
+                    const int64_t o = qo * a.C + c0 + c;
+                    gc[c] = (on && a.g) ? a.g[o] * kInv4Pi : 0.f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) Gc[3 * c + k] = (on && a.gg) ? a.gg[3 * o + k] * kInv4Pi : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < CG; ++i) {
+                    float v = gc[0], v0 = Gc[0], v1 = Gc[1], v2 = Gc[2];
+#pragma unroll
+                    for (int c = 1; c < CG; ++c) {
+                        const bool m = ord[i] == c;
+                        v = m ? gc[c] : v;
+                        v0 = m ? Gc[3 * c] : v0;
+                        v1 = m ? Gc[3 * c + 1] : v1;
+                        v2 = m ? Gc[3 * c + 2] : v2;
+                    }
+                    gl[FWD ? 0 : i] = v;
+                    Gl[FWD ? 0 : 3 * i] = v0;
+                    Gl[FWD ? 0 : 3 * i + 1] = v1;
+                    Gl[FWD ? 0 : 3 * i + 2] = v2;
+                }
+            }
+
+            unsigned next = valid ? 0u : nn;
+            unsigned gsteps = 0;
+            for (;;) {
+                const unsigned n = __reduce_min_sync(FULL, next);
+                if (n >= nn) break;
+                if (++gsteps > nn) {  // a well-formed tree needs at most nn steps
+                    if (lane == 0) atomicOr(a.status, kStatusTraversal);
+                    break;
+                }
+                const float4 geo = __ldg(&nodes[n].geo);
+                const int4 meta = __ldg(&nodes[n].meta);
+                const bool act = next == n;
+                float4 s_first[FWD ? (3 * CG + 3) / 4 : 1];
+                if (FWD) {
+                    const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR + 3 * c0);
+#pragma unroll
+                    for (int j = 0; j < (3 * CG + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
+                }
+                // far test of Alg. 1 in the fixed float order of traverse.cu
+                const float dx = __fsub_rn(x0, geo.x);
+                const float dy = __fsub_rn(x1, geo.y);
+                const float dz = __fsub_rn(x2, geo.z);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const float R = __fmul_rn(a.beta, geo.w);
+                const bool far = act && (d2 > __fmul_rn(R, R));
+                const bool leaf = meta.z > 0;
+                const bool open_leaf = act && !far && leaf;
+                if (act) next = (far || leaf) ? (unsigned)meta.x : n + 1u;
+
+                if (__any_sync(FULL, far)) {
+                    float fa = 0.f, fb = 0.f;
+                    if (far) grad_factors(d2, __int_as_float(meta.w), fa, fb);
+                    const float vx = -dx, vy = -dy, vz = -dz;  // v = p~ - x
+                    if (FWD) {
+                        float s[4 * ((3 * CG + 3) / 4)];
+#pragma unroll
+                        for (int j = 0; j < (3 * CG + 3) / 4; ++j) {
+                            s[4 * j] = s_first[j].x; s[4 * j + 1] = s_first[j].y;
+                            s[4 * j + 2] = s_first[j].z; s[4 * j + 3] = s_first[j].w;
+                        }
+                        if (far) {
+#pragma unroll
+                            for (int c = 0; c < CG; ++c) {
+                                const float sx = s[3 * c], sy = s[3 * c + 1], sz = s[3 * c + 2];
+                                const float sv = fmaf(sx, vx, fmaf(sy, vy, sz * vz));
+                                const float bsv = fb * sv;
+                                part[4 * c] = fmaf(fa, sv, part[4 * c]);
+                                part[4 * c + 1] -= fmaf(fa, sx, bsv * vx);
+                                part[4 * c + 2] -= fmaf(fa, sy, bsv * vy);
+                                part[4 * c + 3] -= fmaf(fa, sz, bsv * vz);
+                            }
+                        }
+                    } else {
+                        float val[3 * CG];
+#pragma unroll
+                        for (int i = 0; i < CG; ++i) {
+                            const float G0 = Gl[3 * i], G1 = Gl[3 * i + 1], G2 = Gl[3 * i + 2];
+                            const float vG = fmaf(vx, G0, fmaf(vy, G1, vz * G2));
+                            const float coef = fmaf(fa, gl[i], -fb * vG);
+                            val[3 * i] = fmaf(coef, vx, -fa * G0);
+                            val[3 * i + 1] = fmaf(coef, vy, -fa * G1);
+                            val[3 * i + 2] = fmaf(coef, vz, -fa * G2);
+                        }
+                        adjoint_vec_reduce<CG>(val, a.dS + (size_t)n * SR + 3 * c0, ord[0], lane);
+                    }
+                }
+
+                if (__any_sync(FULL, open_leaf)) {
+                    // opened leaf: exact terms of its points (eq. dipole_sum)
+                    const int f = meta.y, cnt = meta.z;
+                    for (int j = 0; j < cnt; ++j) {
+                        const PointRec pr = pts[f + j];
+                        float fa = 0.f, fb = 0.f, wu = 0.f;
+                        const float ux = pr.geo.x - x0, uy = pr.geo.y - x1, uz = pr.geo.z - x2;
+                        if (open_leaf) {
+                            const float r2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+                            if (r2 > 0.f) {
+                                grad_factors(r2, pr.geo.w, fa, fb);
+                                wu = fmaf(pr.w.x, ux, fmaf(pr.w.y, uy, pr.w.z * uz));
+                            }
+                        }
+                        const float bwu = fb * wu;
+                        if (FWD) {
+                            // per unit mu: value a (w.u), gradient -(a w + b (w.u) u)
+                            const float kd = fa * wu;
+                            const float g0 = -fmaf(fa, pr.w.x, bwu * ux);
+                            const float g1 = -fmaf(fa, pr.w.y, bwu * uy);
+                            const float g2 = -fmaf(fa, pr.w.z, bwu * uz);
+                            float m[CG];
+                            load_row<AT>(reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * Cp + c0, m, CG);
+                            if (open_leaf) {
+#pragma unroll
+                                for (int c = 0; c < CG; ++c) {
+                                    part[4 * c] = fmaf(kd, m[c], part[4 * c]);
+                                    part[4 * c + 1] = fmaf(g0, m[c], part[4 * c + 1]);
+                                    part[4 * c + 2] = fmaf(g1, m[c], part[4 * c + 2]);
+                                    part[4 * c + 3] = fmaf(g2, m[c], part[4 * c + 3]);
+                                }
+                            }
+                        } else {
+                            float val[CG];
+#pragma unroll
+                            for (int i = 0; i < CG; ++i) {
+                                const float G0 = Gl[3 * i], G1 = Gl[3 * i + 1], G2 = Gl[3 * i + 2];
+                                const float wG = fmaf(pr.w.x, G0, fmaf(pr.w.y, G1, pr.w.z * G2));
+                                const float uG = fmaf(ux, G0, fmaf(uy, G1, uz * G2));
+                                val[i] = fmaf(fa, fmaf(wu, gl[i], -wG), -bwu * uG);
+                            }
+                            adjoint_scalar_reduce<CG>(val, a.dmu + (size_t)(f + j) * Cp + c0, ord[0], lane);
+                        }
+                    }
+                }
+                if (FWD && (gsteps % kFoldSteps) == 0u) {
+#pragma unroll
+                    for (int i = 0; i < NV; ++i) {
+                        kahan_add(acc[i], cmp[i], part[i]);
+                        part[i] = 0.f;
+                    }
+                }
+            }
+            steps += gsteps;
+            if (FWD) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) kahan_add(acc[i], cmp[i], part[i]);
+                if (valid) {
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        if (c0 + c >= a.C) continue;
+                        const int64_t o = qo * a.C + c0 + c;
+                        if (a.out) a.out[o] = __fsub_rn(acc[4 * c], cmp[4 * c]) * kInv4Pi;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            a.gout[3 * o + k] = __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi;
+                    }
+                }
+            }
+        }
+        if (a.pcost && lane == 0) a.pcost[pm] = 0xffffu - (steps < 0xffffu ? steps : 0xffffu);
+    }
+}
+
+template <int CG, typename AT, int MODE>
+void launch_grad(const QueryArgs& a, cudaStream_t s) {
+    static int per_sm = 0;
+    const unsigned grid = query_grid(k_query_grad<CG, AT, MODE>, a.nq, per_sm);
+    note_launch(); k_query_grad<CG, AT, MODE><<<grid, kQThreads, 0, s>>>(a);
+}
+
+template <int MODE>
+void launch_grad_cg(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
+    if (t->Cp == 1) {
+        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<1, float, MODE>(a, s);
+        else launch_grad<1, __nv_bfloat16, MODE>(a, s);
+    } else if (t->Cp == 2) {
+        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<2, float, MODE>(a, s);
+        else launch_grad<2, __nv_bfloat16, MODE>(a, s);
+    } else {
+        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<4, float, MODE>(a, s);
+        else launch_grad<4, __nv_bfloat16, MODE>(a, s);
+    }
+}
+
+}  // namespace
+
+int dispatch_grad(const dipole_tree* t, int mode, const QueryArgs& a, cudaStream_t s) {
+    if (t->Cp != 1 && t->Cp != 2 && t->Cp % 4 != 0) return dip_fail(-1, "unsupported channel count");
+    if (mode == kForwardGrad) launch_grad_cg<kForwardGrad>(t, a, s);
+    else if (mode == kAdjointGrad) launch_grad_cg<kAdjointGrad>(t, a, s);
+    else return dip_fail(-1, "dispatch_grad: not a gradient mode");
+    return 0;
+}
+
+}  // namespace dip

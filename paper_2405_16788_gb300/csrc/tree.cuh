@@ -84,13 +84,33 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
 // Tree update of node moments (eq. farfield_dipole_features).
 int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
 
-// Queries.  mode: 0 forward (out), 1 adjoint (g -> grad), 2 counts.  Query plan
-// (caller-owned, optional): plan_in = false writes the Morton permutation into
-// plan_perm [q] and each packet's warp steps into plan_cost [ceil(q/32)];
-// plan_in = true reads them instead of sorting, and runs packets longest first.
-int query(const dipole_tree* t, int mode, const float* queries, int64_t q, float beta,
-          float* out, const float* g, float* grad, int accumulate, int32_t* counts,
-          uint32_t* plan_perm, uint32_t* plan_cost, bool plan_in, cudaStream_t s);
+// Query modes: the dipole sum (eq. dipole_sum with Alg. 1), its adjoint, the
+// traversal counters, the sum with its spatial gradient, and the adjoint of
+// both.
+enum { kForward = 0, kAdjoint = 1, kCount = 2, kForwardGrad = 3, kAdjointGrad = 4 };
+
+// One query call.  Query plan (caller-owned, optional): plan_in = false writes
+// the Morton permutation into plan_perm [q] and each packet's warp steps into
+// plan_cost [ceil(q/32)]; plan_in = true reads them instead of sorting, and
+// runs packets longest first.
+struct QueryCall {
+    int mode = kForward;
+    const float* queries = nullptr;  // [q, 3]
+    int64_t q = 0;
+    float beta = 2.0f;
+    float* out = nullptr;            // D [q, C] (kForward; optional in kForwardGrad)
+    float* gout = nullptr;           // grad D [q, C, 3] (kForwardGrad)
+    const float* g = nullptr;        // dL/dD [q, C] (kAdjoint; optional in kAdjointGrad)
+    const float* gg = nullptr;       // dL/d(grad D) [q, C, 3] (optional in kAdjointGrad)
+    float* grad = nullptr;           // dL/dmu [n, C] (adjoint modes)
+    int accumulate = 0;
+    int32_t* counts = nullptr;       // [q, 3] (kCount)
+    uint32_t* plan_perm = nullptr;
+    uint32_t* plan_cost = nullptr;
+    bool plan_in = false;
+};
+
+int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s);
 
 // Forward queries with all scratch in a static device array (no allocation);
 // q <= noalloc_max_queries().

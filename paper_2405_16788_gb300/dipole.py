@@ -34,7 +34,8 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
             "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
-            "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned"]
+            "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned",
+            "dipole_forward_grad", "dipole_adjoint_grad"]
 
 
 class DipoleError(RuntimeError):
@@ -78,6 +79,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_adjoint_planned": [P, P, I64, F, P, P, I32, P, P, P],
             "dipole_adjoint": [P, P, I64, F, P, P, I32, P],
             "dipole_query_counts": [P, P, I64, F, P, P],
+            "dipole_forward_grad": [P, P, I64, F, P, P, P, P, P],
+            "dipole_adjoint_grad": [P, P, I64, F, P, P, P, I32, P, P, P],
             "dipole_sync_status": [P, P],
             "dipole_tree_info_get": [P, P],
             "dipole_tree_export": [P] * 15,
@@ -219,6 +222,42 @@ def dipole_adjoint_planned(tree: int, queries: torch.Tensor, beta: float, grad_o
         _dev(grad_out, "grad_out"), _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)),
         ctypes.c_void_p(plan.perm.data_ptr()), ctypes.c_void_p(plan.cost.data_ptr()),
         _stream(stream)))
+
+
+def _opt(t, name, shape=None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(None) if t is None else _dev(t, name, shape=shape)
+
+
+def _plan_ptrs(plan, q):
+    if plan is None:
+        return ctypes.c_void_p(None), ctypes.c_void_p(None)
+    if plan.q != q:
+        raise ValueError("plan was made for another query count")
+    return ctypes.c_void_p(plan.perm.data_ptr()), ctypes.c_void_p(plan.cost.data_ptr())
+
+
+def dipole_forward_grad(tree: int, queries: torch.Tensor, beta: float, out, grad_x: torch.Tensor,
+                        plan: QueryPlan | None = None, stream=None):
+    """D (into `out`, may be None) and its query-position gradient into
+    grad_x [q, C, 3]; with `plan`, also record the query plan."""
+    q = int(queries.shape[0])
+    pp, pc = _plan_ptrs(plan, q)
+    _check(load_library().dipole_forward_grad(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _opt(out, "out"), _dev(grad_x, "grad_x"), pp, pc, _stream(stream)))
+
+
+def dipole_adjoint_grad(tree: int, queries: torch.Tensor, beta: float, grad_out, grad_grad,
+                        grad_attrs: torch.Tensor, accumulate: bool = False,
+                        plan: QueryPlan | None = None, stream=None):
+    """dL/dmu for dL/dD = grad_out [q, C] and dL/d(grad D) = grad_grad [q, C, 3]
+    (either may be None); with `plan` from dipole_forward_grad on these queries."""
+    q = int(queries.shape[0])
+    pp, pc = _plan_ptrs(plan, q)
+    _check(load_library().dipole_adjoint_grad(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _opt(grad_out, "grad_out"), _opt(grad_grad, "grad_grad"), _dev(grad_attrs, "grad_attrs"),
+        int(bool(accumulate)), pp, pc, _stream(stream)))
 
 
 def dipole_query_counts(tree: int, queries: torch.Tensor, beta: float, counts: torch.Tensor,
@@ -385,6 +424,31 @@ class DipoleTree:
                                    plan, accumulate, stream)
         return grad_attrs
 
+    def forward_grad(self, queries: torch.Tensor, beta: float, value: bool = True,
+                     plan: QueryPlan | None = None, stream=None):
+        """(D [q, C] or None, grad_x D [q, C, 3]) at the queries."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        q = queries.shape[0]
+        out = torch.empty((q, self.C), device=queries.device, dtype=torch.float32) if value else None
+        gx = torch.empty((q, self.C, 3), device=queries.device, dtype=torch.float32)
+        dipole_forward_grad(self.handle, queries, beta, out, gx, plan, stream)
+        return out, gx
+
+    def adjoint_grad(self, queries: torch.Tensor, beta: float, grad_out=None, grad_grad=None,
+                     grad_attrs: torch.Tensor | None = None, accumulate: bool = False,
+                     plan: QueryPlan | None = None, stream=None) -> torch.Tensor:
+        """dL/dmu for upstream gradients of D and of grad_x D (either may be None)."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        if grad_attrs is None:
+            grad_attrs = torch.empty((self.n, self.C), device=queries.device, dtype=torch.float32)
+            accumulate = False
+        c = lambda t: None if t is None else t.to(torch.float32).contiguous()
+        dipole_adjoint_grad(self.handle, queries, beta, c(grad_out), c(grad_grad), grad_attrs,
+                            accumulate, plan, stream)
+        return grad_attrs
+
     def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
         counts = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.int32)
         dipole_query_counts(self.handle, queries, beta, counts, stream)
@@ -423,9 +487,55 @@ class DipoleSum(torch.autograd.Function):
         if tree.C != ctx.C:
             raise DipoleError(DIPOLE_ESTATE, "the tree was refit with another channel count "
                                              "between forward and backward")
-        g = tree.adjoint(queries, ctx.beta, grad_out.to(torch.float32).contiguous(),
-                         plan=ctx.plan)
+        go = grad_out.to(torch.float32).contiguous()
+        g = gq = None
+        if ctx.needs_input_grad[0]:
+            g = tree.adjoint(queries, ctx.beta, go, plan=ctx.plan)
+            g = g.to(ctx.attr_dtype).reshape(ctx.attr_shape)
+        if ctx.needs_input_grad[2]:
+            # dL/dx_j = sum_c dL/dD^c grad_x D^c(x_j); the tree still holds the
+            # forward's moments (refit in forward, not since)
+            _, gx = tree.forward_grad(queries.detach(), ctx.beta, value=False)
+            gq = torch.einsum("qc,qck->qk", go, gx).to(queries.dtype)
+        return g, None, gq, None
+
+
+class DipoleSumGrad(torch.autograd.Function):
+    """(D, grad_x D) of `attrs` at `queries`: the dipole sum and its spatial
+    gradient as functions of the attributes (both linear in them).  Backward
+    is the two-stage adjoint of both outputs; queries get no gradient."""
+
+    @staticmethod
+    def forward(ctx, attrs, tree: DipoleTree, queries, beta: float):
+        tree.refit(attrs)
+        plan = QueryPlan(queries.shape[0], queries.device)
+        out, gx = tree.forward_grad(queries, beta, value=True, plan=plan)
+        ctx.plan = plan
+        ctx.tree = tree
+        ctx.beta = float(beta)
+        ctx.C = tree.C
+        ctx.attr_dtype = attrs.dtype
+        ctx.attr_shape = attrs.shape
+        ctx.save_for_backward(queries)
+        return out, gx
+
+    @staticmethod
+    def backward(ctx, grad_out, grad_gx):
+        (queries,) = ctx.saved_tensors
+        tree = ctx.tree
+        if tree.C != ctx.C:
+            raise DipoleError(DIPOLE_ESTATE, "the tree was refit with another channel count "
+                                             "between forward and backward")
+        if grad_out is None and grad_gx is None:
+            return None, None, None, None
+        g = tree.adjoint_grad(queries, ctx.beta, grad_out, grad_gx, plan=ctx.plan)
         return g.to(ctx.attr_dtype).reshape(ctx.attr_shape), None, None, None
+
+
+def dipole_sum_and_grad(attrs: torch.Tensor, tree: DipoleTree, queries: torch.Tensor,
+                        beta: float = 2.0):
+    """(D [q, C], grad_x D [q, C, 3]), differentiable in attrs."""
+    return DipoleSumGrad.apply(attrs, tree, queries, beta)
 
 
 def dipole_sum(attrs: torch.Tensor, tree: DipoleTree, queries: torch.Tensor, beta: float = 2.0):

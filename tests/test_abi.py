@@ -57,6 +57,8 @@ def test_argument_errors_without_gpu(lib_path):
     assert lib.dipole_forward(None, None, 0, 2.0, None, None) == -1
     assert lib.dipole_refit(None, None, 4, 0, None) == -1
     assert lib.dipole_adjoint(None, None, 0, 2.0, None, None, 0, None) == -1
+    assert lib.dipole_forward_grad(None, None, 0, 2.0, None, None, None, None, None) == -1
+    assert lib.dipole_adjoint_grad(None, None, 0, 2.0, None, None, None, 0, None, None, None) == -1
     lib.dipole_tree_destroy(None)  # a no-op
 
 
