@@ -75,6 +75,9 @@ def _load():
         lib.orc_brute_forward_grad.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P]
         lib.orc_bh_forward_grad.argtypes = [_P, _I64, _P, _F, _P]
         lib.orc_bh_adjoint_grad.argtypes = [_P, _I64, _P, _F, _P, _P, _P]
+        lib.orc_brute_adjoint_geom.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P, _P,
+                                               _P, _P, _P]
+        lib.orc_bh_adjoint_geom.argtypes = [_P, _I64, _P, _F, _P, _P, _P, _P, _P]
         lib.orc_far_test.restype = _I
         lib.orc_far_test.argtypes = [_P, _P, _F, _F]
         _lib = lib
@@ -164,6 +167,27 @@ def brute_forward_grad(points, normals, areas, eps, mu, queries):
     _load().orc_brute_forward_grad(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, _ptr(mu), nq,
                                    _ptr(q), _ptr(out))
     return out
+
+
+def brute_adjoint_geom(points, normals, areas, eps, mu, queries, g=None, gg=None):
+    """Plain O(NQ) gradients of L(D, grad D) with respect to mu, the normals and
+    eps (readings R9, R10): (dmu [N, C], dn [N, 3], deps [N]) float64."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    mu = _f32(mu)
+    if mu.ndim == 1:
+        mu = mu[:, None]
+    q = _f32(queries)
+    n, C, nq = p.shape[0], mu.shape[1], q.shape[0]
+    g64 = None if g is None else _f64(np.asarray(g).reshape(nq, C))
+    gg64 = None if gg is None else _f64(np.asarray(gg).reshape(nq, C, 3))
+    dmu = np.zeros((n, C), np.float64)
+    dn = np.zeros((n, 3), np.float64)
+    deps = np.zeros(n, np.float64)
+    _load().orc_brute_adjoint_geom(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, _ptr(mu), nq,
+                                   _ptr(q), _ptr(g64), _ptr(gg64), _ptr(dmu), _ptr(dn),
+                                   _ptr(deps))
+    return dmu, dn, deps
 
 
 def far_test(x, c, r, beta) -> bool:
@@ -257,6 +281,22 @@ class Tree:
         _load().orc_bh_adjoint_grad(self._h, nq, _ptr(q), float(beta), _ptr(g64), _ptr(gg64),
                                     _ptr(out))
         return out
+
+    def adjoint_geom(self, queries, beta, g=None, gg=None):
+        """Barnes-Hut gradients of L(D, grad D) with respect to mu, the normals and
+        eps (R10): (dmu [N, C], dn [N, 3], deps [N]) float64, input order."""
+        if self.C is None:
+            raise RuntimeError("call update() first")
+        q = _f32(queries)
+        nq = q.shape[0]
+        g64 = None if g is None else _f64(np.asarray(g).reshape(nq, self.C))
+        gg64 = None if gg is None else _f64(np.asarray(gg).reshape(nq, self.C, 3))
+        dmu = np.zeros((self.n, self.C), np.float64)
+        dn = np.zeros((self.n, 3), np.float64)
+        deps = np.zeros(self.n, np.float64)
+        _load().orc_bh_adjoint_geom(self._h, nq, _ptr(q), float(beta), _ptr(g64), _ptr(gg64),
+                                    _ptr(dmu), _ptr(dn), _ptr(deps))
+        return dmu, dn, deps
 
     def adjoint(self, queries, beta, g):
         """Two-stage adjoint (Sec. 6.2, App. C): dL/dmu [N, C] float64, input order."""

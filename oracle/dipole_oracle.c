@@ -45,6 +45,19 @@
  *       b = rho'(t)/(eps r^4) - 3 rho/r^5, rho'(t) = (4/sqrt(pi)) t^2 exp(-t^2);
  *       a far node uses the same with n -> n~^c, p -> p~, eps -> eps~, A -> A~.
  *       A zero-distance term contributes nothing to D or to grad D.
+ *   R10 Gradients with respect to the normals and the regularization radii
+ *       (the paper trains normals and eps but states the adjoint only for
+ *       the attributes, App. C).  A point term is linear in n_m: d/dn_m of
+ *       A mu a (n.u)/(4 pi) is A mu a u/(4 pi), and of its x-gradient
+ *       -A mu (a I + b u u^T)/(4 pi).  A far node's n~_t^c depends on n_m
+ *       through A_m mu_m^c/A~_t (eq. farfield_dipole_features), so n_m
+ *       receives (A_m mu_m^c/A~_t) dn~_t^c from every node t holding it (the
+ *       stage-1 sums of eq. farfield_features_gradient).  With t = r/eps,
+ *       da/deps = -(4/sqrt(pi)) t^3 exp(-t^2)/(eps r^3) and
+ *       db/deps = (8/sqrt(pi)) t^5 exp(-t^2)/(eps r^5); a far node depends on
+ *       eps_m through eps~_t (R5), d eps~_t/d eps_m = A_m/A~_t, with one
+ *       scalar stage-1 sum d eps~_t per node.  eps = 0 has zero eps-gradient.
+ *       The paper's single global eps receives the sum over m.
  *
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
  * the radius are specified operation by operation.
@@ -109,6 +122,18 @@ static void grad_factors(double r, double eps, double* a, double* b) {
     double drho = 4.0 / sqrt(ORC_PI) * t * t * exp(-t * t);
     *a = rho / r3;
     *b = drho / (eps * r3 * r) - 3.0 * rho / (r3 * r * r);
+}
+
+/* da/deps and db/deps of reading R10 (r > 0); both 0 for eps = 0. */
+static void eps_factors(double r, double eps, double* da, double* db) {
+    if (eps == 0.0) {
+        *da = 0.0;
+        *db = 0.0;
+        return;
+    }
+    double t = r / eps, e = exp(-t * t), r3 = r * r * r, c = 4.0 / sqrt(ORC_PI);
+    *da = -c * t * t * t * e / (eps * r3);
+    *db = 2.0 * c * t * t * t * t * t * e / (eps * r3 * r * r);
 }
 
 /* Gradient in x of A P_eps(x, p): -A/(4 pi) [a n + b (n.u) u], u = p - x (R9).
@@ -187,6 +212,66 @@ void orc_brute_adjoint(int64_t n, const float* pts, const float* nrm, const floa
                                     eps ? (double)eps[m] : 0.0);
             for (int c = 0; c < C; ++c) gm[c] += w * g[j * C + c];
         }
+    }
+}
+
+/* One point's contributions to the gradients of L with respect to mu_m, n_m
+ * and eps_m (R9, R10), for the upstream gradients gv[c] = dL/dD^c and
+ * gg[3c + k] = dL/d(dD^c/dx_k) at x (either may be NULL), u = p - x:
+ *   dmu^c += A/(4 pi) [g^c a (n.u) - a (n.G^c) - b (n.u)(u.G^c)]
+ *   dn    += A/(4 pi) sum_c mu^c [g^c a u - a G^c - b (u.G^c) u]
+ *   deps  += A/(4 pi) sum_c mu^c [g^c a_e (n.u) - a_e (n.G^c) - b_e (n.u)(u.G^c)]
+ * with a_e = da/deps, b_e = db/deps.  Nothing for x == p. */
+static void point_geom_terms(const double x[3], const float* p, const float* nrm, double A,
+                             double eps, int C, const double* mu, const double* gv,
+                             const double* gg, double* dmu, double* dn, double* deps) {
+    double ux = p[0] - x[0], uy = p[1] - x[1], uz = p[2] - x[2];
+    double r2 = ux * ux + uy * uy + uz * uz;
+    if (r2 == 0.0) return;
+    double r = sqrt(r2), a, b, ae, be;
+    grad_factors(r, eps, &a, &b);
+    eps_factors(r, eps, &ae, &be);
+    double nx = nrm[0], ny = nrm[1], nz = nrm[2];
+    double nu = nx * ux + ny * uy + nz * uz;
+    double f = A / (4.0 * ORC_PI);
+    for (int c = 0; c < C; ++c) {
+        double g = gv ? gv[c] : 0.0;
+        double G0 = gg ? gg[3 * c] : 0.0, G1 = gg ? gg[3 * c + 1] : 0.0, G2 = gg ? gg[3 * c + 2] : 0.0;
+        double nG = nx * G0 + ny * G1 + nz * G2, uG = ux * G0 + uy * G1 + uz * G2;
+        dmu[c] += f * (g * a * nu - a * nG - b * nu * uG);
+        double mc = mu[c];
+        dn[0] += f * mc * (g * a * ux - a * G0 - b * uG * ux);
+        dn[1] += f * mc * (g * a * uy - a * G1 - b * uG * uy);
+        dn[2] += f * mc * (g * a * uz - a * G2 - b * uG * uz);
+        *deps += f * mc * (g * ae * nu - ae * nG - be * nu * uG);
+    }
+}
+
+/* Plain definition of dL/dmu [n,C], dL/dn [n,3] and dL/deps [n] (R9, R10) for
+ * dL/dD = g [q,C] and dL/d(grad D) = gg [q,C,3] (either may be NULL); sums of
+ * point_geom_terms over all queries.  Outputs may be NULL. */
+void orc_brute_adjoint_geom(int64_t n, const float* pts, const float* nrm, const float* area,
+                            const float* eps, int C, const float* mu, int64_t q,
+                            const float* qry, const double* g, const double* gg, double* dmu,
+                            double* dn, double* deps) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < n; ++m) {
+        double* mu_m = (double*)malloc(sizeof(double) * C);
+        double* dm = (double*)calloc((size_t)C, sizeof(double));
+        double dv[3] = {0.0, 0.0, 0.0}, de = 0.0;
+        for (int c = 0; c < C; ++c) mu_m[c] = mu[m * C + c];
+        for (int64_t j = 0; j < q; ++j) {
+            double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+            point_geom_terms(x, pts + 3 * m, nrm + 3 * m, area[m], eps ? (double)eps[m] : 0.0, C,
+                             mu_m, g ? g + j * C : NULL, gg ? gg + j * 3 * C : NULL, dm, dv, &de);
+        }
+        if (dmu)
+            for (int c = 0; c < C; ++c) dmu[m * C + c] = dm[c];
+        if (dn)
+            for (int k = 0; k < 3; ++k) dn[3 * m + k] = dv[k];
+        if (deps) deps[m] = de;
+        free(mu_m);
+        free(dm);
     }
 }
 
@@ -764,4 +849,126 @@ void orc_bh_adjoint_grad(const orc_tree* T, int64_t q, const float* qry, float b
     }
     free(dnt);
     free(dmu);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients with respect to mu, the normals and eps (R10)                    */
+/* ------------------------------------------------------------------------ */
+
+/* AdjointQuery for all point parameters.  A far node (v = p~ - x) adds
+ *   dn~_t^c += A~/(4 pi) [g^c a v - a G^c - b (v.G^c) v]
+ *   deps~_t += A~/(4 pi) sum_c [g^c a_e (n~^c.v) - a_e (n~^c.G^c) - b_e (n~^c.v)(v.G^c)]
+ * (a, b, a_e, b_e at d = |v| and eps~_t); an opened leaf adds its points'
+ * point_geom_terms. */
+static void adjoint_query_geom(const orc_tree* T, const float xf[3], const double x[3],
+                               const double* gv, const double* gg, int32_t t, float beta,
+                               double* dnt, double* det, double* dmu, double* dnp, double* dep) {
+    int C = T->C;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
+        double vx = T->cen[3 * t] - x[0], vy = T->cen[3 * t + 1] - x[1], vz = T->cen[3 * t + 2] - x[2];
+        double d = sqrt(vx * vx + vy * vy + vz * vz);
+        double a, b, ae, be;
+        grad_factors(d, T->epsn[t], &a, &b);
+        eps_factors(d, T->epsn[t], &ae, &be);
+        double f = T->area[t] / (4.0 * ORC_PI);
+        const double* nt = T->nt + (int64_t)t * 3 * C;
+        double* o = dnt + (int64_t)t * 3 * C;
+        double e_acc = 0.0;
+        for (int c = 0; c < C; ++c) {
+            double g = gv ? gv[c] : 0.0;
+            double G0 = gg ? gg[3 * c] : 0.0, G1 = gg ? gg[3 * c + 1] : 0.0, G2 = gg ? gg[3 * c + 2] : 0.0;
+            double vG = vx * G0 + vy * G1 + vz * G2;
+            double nv = nt[3 * c] * vx + nt[3 * c + 1] * vy + nt[3 * c + 2] * vz;
+            double nG = nt[3 * c] * G0 + nt[3 * c + 1] * G1 + nt[3 * c + 2] * G2;
+            double inc[3] = {f * (g * a * vx - a * G0 - b * vG * vx),
+                             f * (g * a * vy - a * G1 - b * vG * vy),
+                             f * (g * a * vz - a * G2 - b * vG * vz)};
+            for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+                o[3 * c + k] += inc[k];
+            }
+            e_acc += f * (g * ae * nv - ae * nG - be * nv * vG);
+        }
+#pragma omp atomic
+        det[t] += e_acc;
+        return;
+    }
+    if (T->is_leaf[t]) {
+        double* dm = (double*)calloc((size_t)C, sizeof(double));
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
+            double dv[3] = {0.0, 0.0, 0.0}, de = 0.0;
+            for (int c = 0; c < C; ++c) dm[c] = 0.0;
+            point_geom_terms(x, T->p + 3 * m, T->nrm + 3 * m, T->A[m], T->eps[m], C,
+                             T->mu + m * C, gv, gg, dm, dv, &de);
+            for (int c = 0; c < C; ++c) {
+#pragma omp atomic
+                dmu[m * C + c] += dm[c];
+            }
+            for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+                dnp[3 * m + k] += dv[k];
+            }
+#pragma omp atomic
+            dep[m] += de;
+        }
+        free(dm);
+        return;
+    }
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c])
+        adjoint_query_geom(T, xf, x, gv, gg, c, beta, dnt, det, dmu, dnp, dep);
+}
+
+/* dL/dmu [n,C], dL/dn [n,3] and dL/deps [n] (input order; any output may be
+ * NULL) for dL/dD = g [q,C] and dL/d(grad D) = gg [q,C,3] (either may be
+ * NULL).  Stage 2 per point m, over the nodes t holding it (R8):
+ *   dmu_m^c = near + sum_t (A_m/A~_t) n_m . dn~_t^c   (eq. farfield_features_gradient)
+ *   dn_m    = near + sum_t sum_c (A_m mu_m^c/A~_t) dn~_t^c
+ *   deps_m  = near + sum_t (A_m/A~_t) deps~_t */
+void orc_bh_adjoint_geom(const orc_tree* T, int64_t q, const float* qry, float beta,
+                         const double* g, const double* gg, double* gmu, double* gn,
+                         double* geps) {
+    int C = T->C;
+    int64_t n = T->n, nn = T->nn;
+    double* dnt = (double*)calloc((size_t)(nn * 3 * C), sizeof(double));
+    double* det = (double*)calloc((size_t)nn, sizeof(double));
+    double* dmu = (double*)calloc((size_t)(n * C), sizeof(double));
+    double* dnp = (double*)calloc((size_t)(n * 3), sizeof(double));
+    double* dep = (double*)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        adjoint_query_geom(T, xf, x, g ? g + j * C : NULL, gg ? gg + j * 3 * C : NULL, 0, beta,
+                           dnt, det, dmu, dnp, dep);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < n; ++m) {
+        int64_t o = T->perm[m];
+        const float* nm = T->nrm + 3 * m;
+        for (int c = 0; c < C; ++c) {
+            double s = dmu[m * C + c];
+            for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
+                const double* d = dnt + (int64_t)t * 3 * C + 3 * c;
+                s += (double)T->A[m] / T->area[t] * (nm[0] * d[0] + nm[1] * d[1] + nm[2] * d[2]);
+            }
+            if (gmu) gmu[o * C + c] = s;
+        }
+        double v[3] = {dnp[3 * m], dnp[3 * m + 1], dnp[3 * m + 2]}, e = dep[m];
+        for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
+            double f = (double)T->A[m] / T->area[t];
+            for (int c = 0; c < C; ++c) {
+                const double* d = dnt + (int64_t)t * 3 * C + 3 * c;
+                for (int k = 0; k < 3; ++k) v[k] += f * T->mu[m * C + c] * d[k];
+            }
+            e += f * det[t];
+        }
+        if (gn)
+            for (int k = 0; k < 3; ++k) gn[3 * o + k] = v[k];
+        if (geps) geps[o] = e;
+    }
+    free(dnt);
+    free(det);
+    free(dmu);
+    free(dnp);
+    free(dep);
 }
