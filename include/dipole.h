@@ -252,6 +252,38 @@ int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, floa
                         void* stream);
 
 /*
+ * Adjoint with respect to the attributes, the normals and the radii.  The
+ * paper trains the normals and the regularization eps besides the attributes
+ * (Sec. 7, inverse rendering) but states the adjoint only for the attributes
+ * (App. C).  Every term is linear in n_m, and a node's moment S_t^c =
+ * sum A_m mu_m^c n_m, so
+ *   dL/dn_m   = A_m sum_c mu_m^c sum_{t holding m} dS_t^c + opened-leaf terms
+ *               A_m sum_c mu_m^c [g^c a u - a G^c - b (u.G^c) u]/(4 pi);
+ * eps enters through rho(r/eps) and, at a far node, through eps~_t =
+ * sum A_m eps_m / A~_t, with da/deps = -(4/sqrt(pi)) t^3 e^{-t^2}/(eps r^3)
+ * and db/deps = (8/sqrt(pi)) t^5 e^{-t^2}/(eps r^5):
+ *   dL/deps_m = A_m sum_{t holding m} dE_t / A~_t + opened-leaf terms,
+ *   dE_t = sum_c [g^c a_e (S^c.v) - a_e (S^c.G^c) - b_e (S^c.v)(v.G^c)]/(4 pi).
+ * Both are evaluated in float for t < 10 (0 beyond, where exp(-t^2)
+ * underflows) and are 0 for eps = 0.  A single global eps receives
+ * sum_m dL/deps_m.
+ *
+ *   grad_out [q, channels], grad_grad [q, channels, 3]: upstream gradients of
+ *                D and grad D (either may be NULL, not both)
+ *   grad_attrs [n, channels], grad_normals [n, 3], grad_radii [n] float,
+ *                caller's point order; any may be NULL, not all
+ *   accumulate 0 or 1, for every output given
+ *   plan_perm, plan_cost: NULL, or the plan of a forward on the same queries
+ *
+ * Uses the tree's adjoint scratch plus n*16 + n_nodes*4 bytes allocated on
+ * the first call: adjoint calls on one tree must not overlap.
+ */
+int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        const float* grad_out, const float* grad_grad, float* grad_attrs,
+                        float* grad_normals, float* grad_radii, int32_t accumulate,
+                        const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream);
+
+/*
  * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,
  * leaf points summed} (int32 [q,3], device).  Same traversal and decisions as
  * dipole_forward; used for the roofline's algorithmic bytes and to check the

@@ -35,7 +35,8 @@ void free_tree_memory(dipole_tree* t) {
     void* bufs[] = {t->pts,    t->code,    t->perm,   t->leaf_of, t->nodes,  t->first,
                     t->count,  t->level,   t->parent, t->skip,    t->is_leaf, t->nchild,
                     t->big_idx, t->agg64,  t->eps_node, t->bbox,  t->status, t->mu,
-                    t->S,      t->S64,     t->dS,     t->dmu,     t->lvl_list, t->lvl_off};
+                    t->S,      t->S64,     t->dS,     t->dmu,     t->lvl_list, t->lvl_off,
+                    t->dE,     t->dgeo};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -307,6 +308,40 @@ int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, floa
     c.plan_cost = const_cast<uint32_t*>(plan_cost);
     c.plan_in = plan_perm != nullptr;
     return dip::query(tree, c, as_stream(stream));
+}
+
+int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, float beta,
+                        const float* grad_out, const float* grad_grad, float* grad_attrs,
+                        float* grad_normals, float* grad_radii, int32_t accumulate,
+                        const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_geom: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: q must be in [0, 2^31)");
+    if (!grad_attrs && !grad_normals && !grad_radii)
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_adjoint_geom: one of grad_attrs, grad_normals, grad_radii is required");
+    if (q > 0 && (!queries || (!grad_out && !grad_grad)))
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_adjoint_geom: queries and one of grad_out, grad_grad are required");
+    if ((plan_perm == nullptr) != (plan_cost == nullptr))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: plan_perm and plan_cost go together");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: accumulate must be 0 or 1");
+    cudaStream_t s = as_stream(stream);
+    int rc = dip::ensure_geom_scratch(tree, s);
+    if (rc) return rc;
+    dip::QueryCall c;
+    c.mode = dip::kAdjointGeom;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.gg = grad_grad;
+    c.grad = grad_attrs; c.grad_n = grad_normals; c.grad_eps = grad_radii;
+    c.accumulate = accumulate;
+    c.plan_perm = const_cast<uint32_t*>(plan_perm);
+    c.plan_cost = const_cast<uint32_t*>(plan_cost);
+    c.plan_in = plan_perm != nullptr;
+    return dip::query(tree, c, s);
 }
 
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,

@@ -29,6 +29,8 @@ struct QueryArgs {
     const float* gg;    // dL/d(grad D) [q, C, 3]
     float* dS;
     float* dmu;
+    float* dE;          // [nn] d eps~_t sums (kAdjointGeom)
+    float* dgeo;        // [n, 4] opened-leaf normal (xyz) and radius (w) terms (kAdjointGeom)
     int32_t* counts;
     unsigned long long* work;
     const uint32_t* porder;  // packet order (longest first), or NULL for Morton order

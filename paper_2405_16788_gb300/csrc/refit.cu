@@ -181,6 +181,84 @@ __global__ void __launch_bounds__(128) k_stage2(
     }
 }
 
+// Stage 2 for the normals and radii (reading of the paper's training of n and
+// eps, Sec. 7 with App. C).  Per leaf, over the nodes u holding it:
+//   dL/dn_m   = A_m sum_c mu_m^c sum_u dS_u^c + opened-leaf terms,
+//   dL/deps_m = A_m sum_u dE_u / A~_u       + opened-leaf terms,
+// since S_u^c = sum A_m mu_m^c n_m and eps~_u = sum A_m eps_m / A~_u.
+template <int CP, typename AT>
+__global__ void __launch_bounds__(128) k_stage2_geom(
+    int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
+    const int32_t* __restrict__ first, const int32_t* __restrict__ count,
+    const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ parent,
+    const double* __restrict__ agg64, const float* __restrict__ dS, const float* __restrict__ dE,
+    const AT* __restrict__ mu, const float* __restrict__ dgeo, int accumulate,
+    float* __restrict__ grad_n, float* __restrict__ grad_eps) {
+    constexpr int SR = srow(CP);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (!is_leaf[t]) continue;
+        const int64_t f = first[t], k = count[t];
+        if (grad_eps) {
+            float E = 0.0f;
+            for (int64_t u = t; u >= 0; u = parent[u])
+                E = fmaf(dE[u], __frcp_rn((float)agg64[5 * u]), E);
+            for (int64_t m = f; m < f + k; ++m) {
+                const float v = fmaf(pts[m].w.w, E, dgeo[4 * m + 3]);
+                float* dst = grad_eps + perm[m];
+                *dst = accumulate ? *dst + v : v;
+            }
+        }
+        if (!grad_n) continue;
+#pragma unroll 1
+        for (int c0 = 0; c0 < CP; c0 += 4) {
+            float D[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) D[j] = 0.0f;
+            for (int64_t u = t; u >= 0; u = parent[u]) {
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    if (3 * c0 + j >= 3 * CP) break;
+                    D[j] += dS[u * SR + 3 * c0 + j];
+                }
+            }
+            for (int64_t m = f; m < f + k; ++m) {
+                float v[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c0 + c >= CP) break;
+                    const float mc = to_f<AT>(mu[m * CP + c0 + c]);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) v[j] = fmaf(mc, D[3 * c + j], v[j]);
+                }
+                const float A = pts[m].w.w;
+                float* dst = grad_n + 3 * (int64_t)perm[m];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float x = A * v[j];
+                    if (c0 == 0) {
+                        x += dgeo[4 * m + j];
+                        dst[j] = accumulate ? dst[j] + x : x;
+                    } else {
+                        dst[j] += x;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int CP, typename AT>
+void launch_stage2_geom(const dipole_tree* t, float* grad_n, float* grad_eps, int accumulate,
+                        cudaStream_t s) {
+    int64_t blocks = (t->nn + 127) / 128;
+    int64_t cap = (int64_t)num_sms() * 16;
+    note_launch();
+    k_stage2_geom<CP, AT><<<(unsigned)(blocks < cap ? blocks : cap), 128, 0, s>>>(
+        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, t->agg64, t->dS, t->dE,
+        (const AT*)t->mu, t->dgeo, accumulate, grad_n, grad_eps);
+}
+
 template <int CP, typename AT>
 void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     int64_t blocks = (t->nn + 127) / 128;
@@ -272,6 +350,36 @@ int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s) {
         case 64: launch_stage2<64>(t, grad, accumulate, s); break;
         default: return dip_fail(-1, "dipole_adjoint: unsupported channel count");
     }
+    DIP_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int ensure_geom_scratch(dipole_tree* t, cudaStream_t s) {
+    if (!t->dE) DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dE, sizeof(float) * (size_t)t->nn, s));
+    if (!t->dgeo) DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dgeo, sizeof(float) * 4 * (size_t)t->n, s));
+    return 0;
+}
+
+int stage2_geom(const dipole_tree* t, float* grad_n, float* grad_eps, int accumulate,
+                cudaStream_t s) {
+    if (!grad_n && !grad_eps) return 0;
+#define DIP_S2G_CASE(K)                                                                   \
+    case K:                                                                               \
+        if (t->dtype == 1) launch_stage2_geom<K, __nv_bfloat16>(t, grad_n, grad_eps, accumulate, s); \
+        else launch_stage2_geom<K, float>(t, grad_n, grad_eps, accumulate, s);            \
+        break;
+    switch (t->Cp) {
+        DIP_S2G_CASE(1)
+        DIP_S2G_CASE(2)
+        DIP_S2G_CASE(4)
+        DIP_S2G_CASE(8)
+        DIP_S2G_CASE(16)
+        DIP_S2G_CASE(32)
+        DIP_S2G_CASE(64)
+        default:
+            return dip_fail(-1, "stage2_geom: unsupported channel count");
+    }
+#undef DIP_S2G_CASE
     DIP_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -337,6 +337,8 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.gg = nullptr;
     a.dS = nullptr;
     a.dmu = nullptr;
+    a.dE = nullptr;
+    a.dgeo = nullptr;
     a.counts = nullptr;
     a.work = work;
     a.porder = nullptr;  // Morton packet order
@@ -353,7 +355,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     uint32_t* plan_perm = call.plan_perm;
     uint32_t* plan_cost = call.plan_cost;
     const bool plan_in = call.plan_in;
-    const bool adjoint = mode == kAdjoint || mode == kAdjointGrad;
+    const bool adjoint = mode == kAdjoint || mode == kAdjointGrad || mode == kAdjointGeom;
     const int SR = srow(t->Cp > 0 ? t->Cp : 1);
     const int64_t np = (q + 31) / 32;
     uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
@@ -397,6 +399,10 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         DIP_CUDA_TRY(cudaMemsetAsync(t->dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
     }
+    if (mode == kAdjointGeom) {
+        DIP_CUDA_TRY(cudaMemsetAsync(t->dE, 0, sizeof(float) * (size_t)t->nn, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(t->dgeo, 0, sizeof(float) * 4 * (size_t)t->n, s));
+    }
     int rc = 0;
     if (q > 0) {
         QueryArgs a;
@@ -418,6 +424,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.gg = call.gg;
         a.dS = t->dS;
         a.dmu = t->dmu;
+        a.dE = t->dE;
+        a.dgeo = t->dgeo;
         a.counts = call.counts;
         a.work = work;
         a.porder = porder;
@@ -427,7 +435,9 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         else if (mode == kCount) rc = dispatch<kCount>(t, a, s);
         else rc = dispatch_grad(t, mode, a, s);
     }
-    if (rc == 0 && adjoint) rc = stage2(t, call.grad, call.accumulate, s);
+    if (rc == 0 && adjoint && call.grad) rc = stage2(t, call.grad, call.accumulate, s);
+    if (rc == 0 && mode == kAdjointGeom)
+        rc = stage2_geom(t, call.grad_n, call.grad_eps, call.accumulate, s);
     cudaFreeAsync(work, s);
     if (codes) {
         cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);

@@ -19,6 +19,11 @@
 // and for a point of an opened leaf, with w = A n,
 //   dmu^c += [a (w.u) g^c - a (w.G^c) - b (w.u)(u.G^c)]/(4 pi);
 // stage 2 (eq. farfield_features_gradient) is unchanged.
+//
+// kAdjointGeom extends that adjoint to the normals and radii: a far node also
+// sums dE_t = d L/d eps~_t over the warp (one atomic), and an opened leaf's
+// point also gets its normal and radius terms (four values, one warp
+// reduce-scatter); k_stage2_geom (refit.cu) sends both to the points.
 #include "query.cuh"
 
 namespace dip {
@@ -76,10 +81,32 @@ __device__ __forceinline__ void grad_factors(float d2, float inv_eps, float& a, 
     b = (trho1 - 3.0f * rho) * (inv_d3 * inv_d2);
 }
 
+// a_e = da/deps = -(4/sqrt(pi)) t^3 exp(-t^2)/(eps d^3) and
+// b_e = db/deps = (8/sqrt(pi)) t^5 exp(-t^2)/(eps d^5), t = d/eps.  No cut at
+// kTCut: far from every point these tiny values are the whole eps-gradient.
+// Both are 0 for eps = 0 (t = inf) and where exp(-t^2) underflows.
+__device__ __forceinline__ void eps_factors(float d2, float inv_eps, float& ae, float& be) {
+    const float inv_d = rsqrtf(d2);
+    const float t = d2 * inv_d * inv_eps;
+    if (!(t < 10.0f)) {  // exp(-100) is below the float range; also t = inf
+        ae = 0.0f;
+        be = 0.0f;
+        return;
+    }
+    const float u = t * t;
+    const float e = 2.0f * kTwoOverSqrtPi * __expf(-u) * t * u * inv_eps;  // (4/sqrt(pi)) t^3 e^-t^2 / eps
+    const float inv_d3 = inv_d * inv_d * inv_d;
+    ae = -e * inv_d3;
+    be = 2.0f * e * u * (inv_d3 * inv_d * inv_d);
+}
+
+// Three resident blocks for the forward (80 registers, a few spilled bytes:
+// -10% time against two blocks at 100 registers); two for the adjoints.
 template <int CG, typename AT, int MODE>
-__global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) {
+__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_query_grad(const QueryArgs a) {
     static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
     constexpr bool FWD = MODE == kForwardGrad;
+    constexpr bool GEOM = MODE == kAdjointGeom;  // also the normal and radius gradients
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned kFoldSteps = 16;
     constexpr int NV = FWD ? 4 * CG : 1;  // D and grad D per channel: [4c] D, [4c+1+k] d/dx_k
@@ -114,6 +141,7 @@ __global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) 
             // adjoint: upstream values and gradients of this group, scaled by
             // 1/(4 pi), in lane_channel_order
             float gl[FWD ? 1 : CG], Gl[FWD ? 1 : 3 * CG];
+            float gN[GEOM ? CG : 1], GN[GEOM ? 3 * CG : 1];  // natural channel order
             if (!FWD) {
                 float gc[CG], Gc[3 * CG];
 #pragma unroll
@@ -140,6 +168,14 @@ __global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) 
                     Gl[FWD ? 0 : 3 * i + 1] = v1;
                     Gl[FWD ? 0 : 3 * i + 2] = v2;
                 }
+                if (GEOM) {
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) {
+                        gN[GEOM ? c : 0] = gc[c];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) GN[GEOM ? 3 * c + k : 0] = Gc[3 * c + k];
+                    }
+                }
             }
 
             unsigned next = valid ? 0u : nn;
@@ -154,8 +190,8 @@ __global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) 
                 const float4 geo = __ldg(&nodes[n].geo);
                 const int4 meta = __ldg(&nodes[n].meta);
                 const bool act = next == n;
-                float4 s_first[FWD ? (3 * CG + 3) / 4 : 1];
-                if (FWD) {
+                float4 s_first[(FWD || GEOM) ? (3 * CG + 3) / 4 : 1];
+                if (FWD || GEOM) {
                     const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR + 3 * c0);
 #pragma unroll
                     for (int j = 0; j < (3 * CG + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
@@ -206,6 +242,30 @@ __global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) 
                             val[3 * i + 2] = fmaf(coef, vz, -fa * G2);
                         }
                         adjoint_vec_reduce<CG>(val, a.dS + (size_t)n * SR + 3 * c0, ord[0], lane);
+                        if (GEOM) {
+                            // d eps~_t += sum_c [g^c a_e (S^c.v) - a_e (S^c.G^c) - b_e (S^c.v)(v.G^c)]
+                            float ae = 0.f, be = 0.f;
+                            if (far) eps_factors(d2, __int_as_float(meta.w), ae, be);
+                            float s[4 * ((3 * CG + 3) / 4)];
+#pragma unroll
+                            for (int j = 0; j < (3 * CG + 3) / 4; ++j) {
+                                s[4 * j] = s_first[j].x; s[4 * j + 1] = s_first[j].y;
+                                s[4 * j + 2] = s_first[j].z; s[4 * j + 3] = s_first[j].w;
+                            }
+                            float e = 0.f;
+#pragma unroll
+                            for (int c = 0; c < CG; ++c) {
+                                const float G0 = GN[3 * c], G1 = GN[3 * c + 1], G2 = GN[3 * c + 2];
+                                const float sx = s[3 * c], sy = s[3 * c + 1], sz = s[3 * c + 2];
+                                const float sv = fmaf(sx, vx, fmaf(sy, vy, sz * vz));
+                                const float sG = fmaf(sx, G0, fmaf(sy, G1, sz * G2));
+                                const float vG = fmaf(vx, G0, fmaf(vy, G1, vz * G2));
+                                e += fmaf(ae, fmaf(gN[c], sv, -sG), -be * sv * vG);
+                            }
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(FULL, e, off);
+                            if (lane == 0 && e != 0.f) atomicAdd(a.dE + n, e);
+                        }
                     }
                 }
 
@@ -251,6 +311,31 @@ __global__ void __launch_bounds__(kQThreads, 2) k_query_grad(const QueryArgs a) 
                                 val[i] = fmaf(fa, fmaf(wu, gl[i], -wG), -bwu * uG);
                             }
                             adjoint_scalar_reduce<CG>(val, a.dmu + (size_t)(f + j) * Cp + c0, ord[0], lane);
+                            if (GEOM) {
+                                // normal (A sum_c mu^c [g^c a u - a G^c - b (u.G^c) u]) and
+                                // radius (sum_c mu^c [g^c a_e (w.u) - a_e (w.G^c) - b_e (w.u)(u.G^c)])
+                                float ae = 0.f, be = 0.f;
+                                if (open_leaf && fa != 0.f) {
+                                    const float r2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+                                    eps_factors(r2, pr.geo.w, ae, be);
+                                }
+                                float m[CG];
+                                load_row<AT>(reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * Cp + c0, m, CG);
+                                float gv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                                for (int c = 0; c < CG; ++c) {
+                                    const float G0 = GN[3 * c], G1 = GN[3 * c + 1], G2 = GN[3 * c + 2];
+                                    const float uG = fmaf(ux, G0, fmaf(uy, G1, uz * G2));
+                                    const float wG = fmaf(pr.w.x, G0, fmaf(pr.w.y, G1, pr.w.z * G2));
+                                    const float ga = fa * gN[c], bu = fb * uG;
+                                    gv[0] = fmaf(m[c], fmaf(ga, ux, -fmaf(fa, G0, bu * ux)), gv[0]);
+                                    gv[1] = fmaf(m[c], fmaf(ga, uy, -fmaf(fa, G1, bu * uy)), gv[1]);
+                                    gv[2] = fmaf(m[c], fmaf(ga, uz, -fmaf(fa, G2, bu * uz)), gv[2]);
+                                    gv[3] = fmaf(m[c], fmaf(ae, fmaf(gN[c], wu, -wG), -be * wu * uG), gv[3]);
+                                }
+                                gv[0] *= pr.w.w; gv[1] *= pr.w.w; gv[2] *= pr.w.w;
+                                warp_reduce_add<4>(gv, a.dgeo + 4 * (size_t)(f + j), lane);
+                            }
                         }
                     }
                 }
@@ -290,18 +375,21 @@ void launch_grad(const QueryArgs& a, cudaStream_t s) {
     note_launch(); k_query_grad<CG, AT, MODE><<<grid, kQThreads, 0, s>>>(a);
 }
 
+template <int CG, int MODE>
+void launch_grad_dtype(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
+    if constexpr (MODE == kAdjointGrad) {
+        launch_grad<CG, float, MODE>(a, s);  // reads no attributes
+    } else {
+        if (t->dtype == 0) launch_grad<CG, float, MODE>(a, s);
+        else launch_grad<CG, __nv_bfloat16, MODE>(a, s);
+    }
+}
+
 template <int MODE>
 void launch_grad_cg(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
-    if (t->Cp == 1) {
-        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<1, float, MODE>(a, s);
-        else launch_grad<1, __nv_bfloat16, MODE>(a, s);
-    } else if (t->Cp == 2) {
-        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<2, float, MODE>(a, s);
-        else launch_grad<2, __nv_bfloat16, MODE>(a, s);
-    } else {
-        if (MODE == kAdjointGrad || t->dtype == 0) launch_grad<4, float, MODE>(a, s);
-        else launch_grad<4, __nv_bfloat16, MODE>(a, s);
-    }
+    if (t->Cp == 1) launch_grad_dtype<1, MODE>(t, a, s);
+    else if (t->Cp == 2) launch_grad_dtype<2, MODE>(t, a, s);
+    else launch_grad_dtype<4, MODE>(t, a, s);
 }
 
 }  // namespace
@@ -310,6 +398,7 @@ int dispatch_grad(const dipole_tree* t, int mode, const QueryArgs& a, cudaStream
     if (t->Cp != 1 && t->Cp != 2 && t->Cp % 4 != 0) return dip_fail(-1, "unsupported channel count");
     if (mode == kForwardGrad) launch_grad_cg<kForwardGrad>(t, a, s);
     else if (mode == kAdjointGrad) launch_grad_cg<kAdjointGrad>(t, a, s);
+    else if (mode == kAdjointGeom) launch_grad_cg<kAdjointGeom>(t, a, s);
     else return dip_fail(-1, "dispatch_grad: not a gradient mode");
     return 0;
 }

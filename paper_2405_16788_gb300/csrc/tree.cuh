@@ -48,6 +48,8 @@ struct dipole_tree {
     double* S64 = nullptr;       // [nbig, 3 Cp]
     float* dS = nullptr;         // [nn, 3 Cp] adjoint node accumulators
     float* dmu = nullptr;        // [n, Cp] adjoint opened-leaf accumulators
+    float* dE = nullptr;         // [nn] adjoint d eps~_t sums (normal/radius gradients)
+    float* dgeo = nullptr;       // [n, 4] adjoint opened-leaf normal and radius terms
     int attr_Cp_alloc = 0;
     int attr_dtype_alloc = -1;
 
@@ -85,9 +87,9 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
 int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
 
 // Query modes: the dipole sum (eq. dipole_sum with Alg. 1), its adjoint, the
-// traversal counters, the sum with its spatial gradient, and the adjoint of
-// both.
-enum { kForward = 0, kAdjoint = 1, kCount = 2, kForwardGrad = 3, kAdjointGrad = 4 };
+// traversal counters, the sum with its spatial gradient, the adjoint of both,
+// and that adjoint extended to the normals and radii.
+enum { kForward = 0, kAdjoint = 1, kCount = 2, kForwardGrad = 3, kAdjointGrad = 4, kAdjointGeom = 5 };
 
 // One query call.  Query plan (caller-owned, optional): plan_in = false writes
 // the Morton permutation into plan_perm [q] and each packet's warp steps into
@@ -102,7 +104,9 @@ struct QueryCall {
     float* gout = nullptr;           // grad D [q, C, 3] (kForwardGrad)
     const float* g = nullptr;        // dL/dD [q, C] (kAdjoint; optional in kAdjointGrad)
     const float* gg = nullptr;       // dL/d(grad D) [q, C, 3] (optional in kAdjointGrad)
-    float* grad = nullptr;           // dL/dmu [n, C] (adjoint modes)
+    float* grad = nullptr;           // dL/dmu [n, C] (adjoint modes; optional in kAdjointGeom)
+    float* grad_n = nullptr;         // dL/dn [n, 3] (optional in kAdjointGeom)
+    float* grad_eps = nullptr;       // dL/deps [n] (optional in kAdjointGeom)
     int accumulate = 0;
     int32_t* counts = nullptr;       // [q, 3] (kCount)
     uint32_t* plan_perm = nullptr;
@@ -120,5 +124,13 @@ int64_t noalloc_max_queries();
 
 // Stage 2 of the adjoint (eq. farfield_features_gradient) into grad [n, C].
 int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s);
+
+// Scratch of the normal/radius adjoint (dE, dgeo), allocated on first use.
+int ensure_geom_scratch(dipole_tree* t, cudaStream_t s);
+
+// Stage 2 for the normals and radii: grad_n [n, 3] and grad_eps [n] (either
+// may be NULL), caller order.
+int stage2_geom(const dipole_tree* t, float* grad_n, float* grad_eps, int accumulate,
+                cudaStream_t s);
 
 }  // namespace dip

@@ -35,7 +35,7 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
             "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
             "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned",
-            "dipole_forward_grad", "dipole_adjoint_grad"]
+            "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom"]
 
 
 class DipoleError(RuntimeError):
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_query_counts": [P, P, I64, F, P, P],
             "dipole_forward_grad": [P, P, I64, F, P, P, P, P, P],
             "dipole_adjoint_grad": [P, P, I64, F, P, P, P, I32, P, P, P],
+            "dipole_adjoint_geom": [P, P, I64, F, P, P, P, P, P, I32, P, P, P],
             "dipole_sync_status": [P, P],
             "dipole_tree_info_get": [P, P],
             "dipole_tree_export": [P] * 15,
@@ -257,6 +258,20 @@ def dipole_adjoint_grad(tree: int, queries: torch.Tensor, beta: float, grad_out,
     _check(load_library().dipole_adjoint_grad(
         ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
         _opt(grad_out, "grad_out"), _opt(grad_grad, "grad_grad"), _dev(grad_attrs, "grad_attrs"),
+        int(bool(accumulate)), pp, pc, _stream(stream)))
+
+
+def dipole_adjoint_geom(tree: int, queries: torch.Tensor, beta: float, grad_out, grad_grad,
+                        grad_attrs, grad_normals, grad_radii, accumulate: bool = False,
+                        plan: QueryPlan | None = None, stream=None):
+    """dL/dmu [n, C], dL/dn [n, 3], dL/deps [n] (each may be None) for upstream
+    gradients of D and grad D (either may be None)."""
+    q = int(queries.shape[0])
+    pp, pc = _plan_ptrs(plan, q)
+    _check(load_library().dipole_adjoint_geom(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _opt(grad_out, "grad_out"), _opt(grad_grad, "grad_grad"), _opt(grad_attrs, "grad_attrs"),
+        _opt(grad_normals, "grad_normals"), _opt(grad_radii, "grad_radii"),
         int(bool(accumulate)), pp, pc, _stream(stream)))
 
 
@@ -449,6 +464,22 @@ class DipoleTree:
                             accumulate, plan, stream)
         return grad_attrs
 
+    def adjoint_geom(self, queries: torch.Tensor, beta: float, grad_out=None, grad_grad=None,
+                     attrs: bool = True, normals: bool = True, radii: bool = True,
+                     plan: QueryPlan | None = None, stream=None):
+        """(dL/dmu [n, C], dL/dn [n, 3], dL/deps [n]) for upstream gradients of D
+        and of grad_x D; an output not asked for is None."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        dev = queries.device
+        gm = torch.empty((self.n, self.C), device=dev, dtype=torch.float32) if attrs else None
+        gn = torch.empty((self.n, 3), device=dev, dtype=torch.float32) if normals else None
+        ge = torch.empty((self.n,), device=dev, dtype=torch.float32) if radii else None
+        c = lambda t: None if t is None else t.to(torch.float32).contiguous()
+        dipole_adjoint_geom(self.handle, queries, beta, c(grad_out), c(grad_grad), gm, gn, ge,
+                            False, plan, stream)
+        return gm, gn, ge
+
     def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
         counts = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.int32)
         dipole_query_counts(self.handle, queries, beta, counts, stream)
@@ -506,8 +537,11 @@ class DipoleSumGrad(torch.autograd.Function):
     is the two-stage adjoint of both outputs; queries get no gradient."""
 
     @staticmethod
-    def forward(ctx, attrs, tree: DipoleTree, queries, beta: float):
-        tree.refit(attrs)
+    def forward(ctx, attrs, tree: DipoleTree, queries, beta: float, refit: bool = True):
+        if refit:
+            tree.refit(attrs)
+        elif tree.C != attrs.reshape(attrs.shape[0], -1).shape[1]:
+            raise DipoleError(DIPOLE_ESTATE, "refit=False needs the tree refit with these attrs")
         plan = QueryPlan(queries.shape[0], queries.device)
         out, gx = tree.forward_grad(queries, beta, value=True, plan=plan)
         ctx.plan = plan
@@ -527,15 +561,72 @@ class DipoleSumGrad(torch.autograd.Function):
             raise DipoleError(DIPOLE_ESTATE, "the tree was refit with another channel count "
                                              "between forward and backward")
         if grad_out is None and grad_gx is None:
-            return None, None, None, None
+            return None, None, None, None, None
         g = tree.adjoint_grad(queries, ctx.beta, grad_out, grad_gx, plan=ctx.plan)
-        return g.to(ctx.attr_dtype).reshape(ctx.attr_shape), None, None, None
+        return g.to(ctx.attr_dtype).reshape(ctx.attr_shape), None, None, None, None
 
 
 def dipole_sum_and_grad(attrs: torch.Tensor, tree: DipoleTree, queries: torch.Tensor,
-                        beta: float = 2.0):
-    """(D [q, C], grad_x D [q, C, 3]), differentiable in attrs."""
-    return DipoleSumGrad.apply(attrs, tree, queries, beta)
+                        beta: float = 2.0, refit: bool = True):
+    """(D [q, C], grad_x D [q, C, 3]), differentiable in attrs.  refit=False
+    skips the tree update when the tree already holds these attrs (a second
+    query batch in the same step); the caller guarantees that."""
+    return DipoleSumGrad.apply(attrs, tree, queries, beta, refit)
+
+
+class DipoleField(torch.autograd.Function):
+    """The dipole sum (and optionally its spatial gradient) differentiable in
+    the point normals, radii and attributes, as trained by the paper's inverse
+    rendering (positions and areas are fixed).  Forward builds the tree from
+    the current normals and radii, refits the attributes and queries; backward
+    is the adjoint of every output with respect to all three (and the queries
+    get sum_c dL/dD^c grad D^c when they require a gradient)."""
+
+    @staticmethod
+    def forward(ctx, points, normals, areas, radii, attrs, queries, beta: float, with_grad: bool,
+                leaf_size: int):
+        tree = DipoleTree(points.detach(), normals.detach().contiguous(), areas.detach(),
+                          None if radii is None else radii.detach().contiguous(),
+                          leaf_size=leaf_size)
+        tree.refit(attrs.detach())
+        plan = QueryPlan(queries.shape[0], queries.device)
+        q = queries.detach().contiguous()
+        if with_grad:
+            d, gx = tree.forward_grad(q, beta, value=True, plan=plan)
+        else:
+            d, gx = tree.forward(q, beta, plan=plan), None
+        ctx.tree, ctx.plan, ctx.beta, ctx.with_grad = tree, plan, float(beta), with_grad
+        ctx.attr_dtype, ctx.attr_shape = attrs.dtype, attrs.shape
+        ctx.has_radii = radii is not None
+        ctx.save_for_backward(q)
+        return (d, gx) if with_grad else d
+
+    @staticmethod
+    def backward(ctx, grad_out, grad_gx=None):
+        (q,) = ctx.saved_tensors
+        tree = ctx.tree
+        need = ctx.needs_input_grad
+        gn = ge = gm = gq = None
+        if need[1] or need[3] or need[4]:
+            gm, gn, ge = tree.adjoint_geom(q, ctx.beta, grad_out, grad_gx if ctx.with_grad else None,
+                                           attrs=need[4], normals=need[1],
+                                           radii=need[3] and ctx.has_radii, plan=ctx.plan)
+            if gm is not None:
+                gm = gm.to(ctx.attr_dtype).reshape(ctx.attr_shape)
+        if need[5]:
+            if ctx.with_grad and grad_gx is not None and bool(torch.any(grad_gx != 0)):
+                raise NotImplementedError("second derivatives in the query position")
+            _, gx = tree.forward_grad(q, ctx.beta, value=False)
+            gq = torch.einsum("qc,qck->qk", grad_out.to(torch.float32), gx)
+        return None, gn, None, ge, gm, gq, None, None, None
+
+
+def dipole_field(points, normals, areas, radii, attrs, queries, beta: float = 2.0,
+                 with_grad: bool = False, leaf_size: int = 8):
+    """D [q, C] (or (D, grad_x D [q, C, 3]) with with_grad), differentiable in
+    normals, radii, attrs (and, for D, the queries)."""
+    return DipoleField.apply(points, normals, areas, radii, attrs, queries, beta, with_grad,
+                             leaf_size)
 
 
 def dipole_sum(attrs: torch.Tensor, tree: DipoleTree, queries: torch.Tensor, beta: float = 2.0):
