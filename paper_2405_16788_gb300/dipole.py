@@ -35,7 +35,8 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_tree_export", "dipole_tree_destroy", "dipole_last_error",
             "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
             "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned",
-            "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom"]
+            "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom",
+            "dipole_forward_grid"]
 
 
 class DipoleError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_forward_grad": [P, P, I64, F, P, P, P, P, P],
             "dipole_adjoint_grad": [P, P, I64, F, P, P, P, I32, P, P, P],
             "dipole_adjoint_geom": [P, P, I64, F, P, P, P, P, P, I32, P, P, P],
+            "dipole_forward_grid": [P, P, F, P, F, P, P],
             "dipole_sync_status": [P, P],
             "dipole_tree_info_get": [P, P],
             "dipole_tree_export": [P] * 15,
@@ -273,6 +275,16 @@ def dipole_adjoint_geom(tree: int, queries: torch.Tensor, beta: float, grad_out,
         _opt(grad_out, "grad_out"), _opt(grad_grad, "grad_grad"), _opt(grad_attrs, "grad_attrs"),
         _opt(grad_normals, "grad_normals"), _opt(grad_radii, "grad_radii"),
         int(bool(accumulate)), pp, pc, _stream(stream)))
+
+
+def dipole_forward_grid(tree: int, lo, spacing: float, dims, beta: float, out: torch.Tensor,
+                        stream=None):
+    """D on the grid lo + spacing * (i, j, k): out [dims[2], dims[1], dims[0], C]."""
+    lo_h = np.ascontiguousarray(np.asarray(lo, np.float32).reshape(3))
+    dims_h = np.ascontiguousarray(np.asarray(dims, np.int64).reshape(3))
+    _check(load_library().dipole_forward_grid(
+        ctypes.c_void_p(tree), lo_h.ctypes.data_as(ctypes.c_void_p), float(spacing),
+        dims_h.ctypes.data_as(ctypes.c_void_p), float(beta), _dev(out, "out"), _stream(stream)))
 
 
 def dipole_query_counts(tree: int, queries: torch.Tensor, beta: float, counts: torch.Tensor,
@@ -479,6 +491,15 @@ class DipoleTree:
         dipole_adjoint_geom(self.handle, queries, beta, c(grad_out), c(grad_grad), gm, gn, ge,
                             False, plan, stream)
         return gm, gn, ge
+
+    def forward_grid(self, lo, spacing: float, dims, beta: float, stream=None) -> torch.Tensor:
+        """D on a dense grid: [dims[2], dims[1], dims[0], C] (x fastest)."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        nx, ny, nz = (int(d) for d in dims)
+        out = torch.empty((nz, ny, nx, self.C), device=self.device, dtype=torch.float32)
+        dipole_forward_grid(self.handle, lo, spacing, (nx, ny, nz), beta, out, stream)
+        return out
 
     def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
         counts = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.int32)

@@ -239,7 +239,7 @@ WORKLOADS = {
                 "Q=4,096 rays x 128 stratified samples = 524,288; beta=2, leaf 8",
     "scene-3m-bf16": "N=3,000,000, 3% outliers, C=16 (1+3+12) stored bf16; Q=16,384 rays x 128",
     "scene-5m-loop": "N=5,000,000 anisotropic density, 5% outliers, C=4; per step 8,192 camera "
-                     "rays x 192 + 8,192 shadow rays x 64",
+                     "rays x 192 + 8,192 shadow rays x 64 to a point light at (1.8, 1.2, 2.2)",
 }
 
 
@@ -276,5 +276,10 @@ def workload(name: str, scale: float = 1.0) -> Workload:
         mu = attributes(cl.n, 4, seed=2005)
         o, d, tn, tf = camera_rays(sz(8192), seed=3005)
         qs, t = stratified_samples(o, d, tn, tf, 192, seed=4005)
-        return Workload(name, cl, mu, qs, meta=dict(rays=(o, d, t)))
+        # one point light outside the scene and the jitter of 64 stratified
+        # samples on each shadow ray
+        jit = _rng(5005).uniform(0, 1, size=(o.shape[0], 64))
+        return Workload(name, cl, mu, qs, meta=dict(rays=(o, d, t), t_near=tn, t_far=tf,
+                                                    light=np.array([1.8, 1.2, 2.2]),
+                                                    shadow_jitter=jit))
     raise KeyError(name)
