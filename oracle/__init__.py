@@ -78,6 +78,7 @@ def _load():
         lib.orc_brute_adjoint_geom.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P, _P,
                                                _P, _P, _P]
         lib.orc_bh_adjoint_geom.argtypes = [_P, _I64, _P, _F, _P, _P, _P, _P, _P]
+        lib.orc_set_kernel.argtypes = [_I]
         lib.orc_far_test.restype = _I
         lib.orc_far_test.argtypes = [_P, _P, _F, _F]
         _lib = lib
@@ -188,6 +189,24 @@ def brute_adjoint_geom(points, normals, areas, eps, mu, queries, g=None, gg=None
                                    _ptr(q), _ptr(g64), _ptr(gg64), _ptr(dmu), _ptr(dn),
                                    _ptr(deps))
     return dmu, dn, deps
+
+
+class kernel:
+    """Context manager selecting the oracle's kernel (reading R11):
+    "regularized" (the paper's, the default) or "desingularized"."""
+
+    _codes = {"regularized": 0, "desingularized": 1}
+
+    def __init__(self, name: str):
+        self.code = self._codes[name]
+
+    def __enter__(self):
+        _load().orc_set_kernel(self.code)
+        return self
+
+    def __exit__(self, *exc):
+        _load().orc_set_kernel(0)
+        return False
 
 
 def far_test(x, c, r, beta) -> bool:

@@ -58,6 +58,13 @@
  *       eps_m through eps~_t (R5), d eps~_t/d eps_m = A_m/A~_t, with one
  *       scalar stage-1 sum d eps~_t per node.  eps = 0 has zero eps-gradient.
  *       The paper's single global eps receives the sum over m.
+ *   R11 Desingularized kernel (the ablation baseline: "a small cutoff in the
+ *       denominator" of the Poisson kernel, Sec. 4.1 footnote and Sec. 7):
+ *       1/r^3 -> 1/max(r, eps)^3 with the point's radius as the cutoff, eps~
+ *       at a far node; written as rho_d(r, eps) = min(1, (r/eps)^3) in place
+ *       of rho so that every formula above applies: a = 1/max(r, eps)^3,
+ *       b = -3/r^5 outside the cutoff and 0 inside, da/deps = -3/eps^4 inside
+ *       and 0 outside, db/deps = 0.  Selected by orc_set_kernel(1).
  *
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
  * the radius are specified operation by operation.
@@ -92,9 +99,20 @@ double orc_rho(double t) {
     return erf(t) - 2.0 * t / sqrt(ORC_PI) * exp(-t * t);
 }
 
-/* rho(r / eps), with eps = 0 meaning the singular kernel (R2). */
+/* Kernel of the queries: 0 the regularized kernel of the paper, 1 the
+ * desingularized kernel of R11. */
+static int g_kernel = 0;
+
+void orc_set_kernel(int kernel) { g_kernel = kernel; }
+
+/* rho(r / eps), with eps = 0 meaning the singular kernel (R2); for the
+ * desingularized kernel min(1, (r/eps)^3) (R11). */
 static double rho_r(double r, double eps) {
     if (eps == 0.0) return 1.0;
+    if (g_kernel == 1) {
+        double q = r / eps;
+        return q >= 1.0 ? 1.0 : q * q * q;
+    }
     return orc_rho(r / eps);
 }
 
@@ -118,6 +136,16 @@ static void grad_factors(double r, double eps, double* a, double* b) {
         return;
     }
     double t = r / eps;
+    if (g_kernel == 1) { /* R11: 1/max(r, eps)^3 */
+        if (t >= 1.0) {
+            *a = 1.0 / r3;
+            *b = -3.0 / (r3 * r * r);
+        } else {
+            *a = 1.0 / (eps * eps * eps);
+            *b = 0.0;
+        }
+        return;
+    }
     double rho = orc_rho(t);
     double drho = 4.0 / sqrt(ORC_PI) * t * t * exp(-t * t);
     *a = rho / r3;
@@ -128,6 +156,11 @@ static void grad_factors(double r, double eps, double* a, double* b) {
 static void eps_factors(double r, double eps, double* da, double* db) {
     if (eps == 0.0) {
         *da = 0.0;
+        *db = 0.0;
+        return;
+    }
+    if (g_kernel == 1) { /* R11 */
+        *da = r < eps ? -3.0 / (eps * eps * eps * eps) : 0.0;
         *db = 0.0;
         return;
     }
