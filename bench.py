@@ -50,6 +50,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true")
+    p.add_argument("--no-next", action="store_true",
+                   help="skip the timings of the gradient, grid and training-loop rows")
+    p.add_argument("--loop-steps", type=int, default=10)
     return p.parse_args()
 
 
@@ -397,6 +400,12 @@ def run_ours(args):
                 "step_ms": float(phb.sum()),
                 "speedup_vs_f32_step": float(ph.sum() / phb.sum())}
 
+    # ---- rows beyond the hot path: spatial gradient, normal/radius adjoint,
+    # dense grid, training loop (timed with CUDA events, untimed for `value`) ----
+    nxt = None
+    if rank == 0 and not args.no_next:
+        nxt = next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args)
+
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -447,11 +456,103 @@ def run_ours(args):
                 "config": config_of(w, "flushed between timed steps (512 MB write)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "breakdown": breakdown,
-                "bf16_attrs": bf16, "impl": "ours"}
+                "bf16_attrs": bf16, "next_rows": nxt, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         td.destroy_process_group()
     return 0
+
+
+def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args):
+    """Timings of the rows built beyond the forward/adjoint step, each the
+    median of 5 launches after one warm-up, L2 flushed before each."""
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    h = dp.dipole_build_tree(P, Nr, A, E, LEAF, 10)
+    dp.dipole_refit(h, MU)
+    plan = dp.QueryPlan(Q, dev)
+    OUT = torch.empty((Q, C), device=dev)
+    GX = torch.empty((Q, C, 3), device=dev)
+    GG = torch.from_numpy(np.random.default_rng(1).normal(size=(Q, C, 3)).astype(np.float32)).to(dev)
+    GM = torch.empty((N, C), device=dev)
+    GN = torch.empty((N, 3), device=dev)
+    GE = torch.empty((N,), device=dev)
+    f_ms = timed(lambda: dp.dipole_forward_grad(h, X, BETA, OUT, GX, plan))
+    a_ms = timed(lambda: dp.dipole_adjoint_grad(h, X, BETA, G, GG, GM, False, plan))
+    geo_ms = timed(lambda: dp.dipole_adjoint_geom(h, X, BETA, G, GG, GM, GN, GE, False, plan))
+    res = {"spatial_gradient": {
+        "forward_grad_ms": f_ms, "adjoint_grad_ms": a_ms,
+        "queries_per_s_fwd_adj": Q / ((f_ms + a_ms) * 1e-3),
+        "adjoint_geom_ms": geo_ms,
+        "workload": "the bench workload's tree and queries, C=4, plan from forward_grad"}}
+    dims = (512, 512, 512)
+    grid_out = torch.empty((dims[2], dims[1], dims[0], C), device=dev)
+    g_ms = timed(lambda: dp.dipole_forward_grid(h, (-1.5, -1.5, -1.5), 3.0 / 511, dims, BETA,
+                                                grid_out), reps=3)
+    res["dense_grid"] = {"dims": list(dims), "forward_ms": g_ms,
+                         "queries_per_s": dims[0] * dims[1] * dims[2] / (g_ms * 1e-3)}
+    dp.dipole_sync_status(h)
+    dp.dipole_tree_destroy(h)
+    del grid_out
+    if args.loop_steps > 0:
+        res["training_loop"] = loop_row(torch, dev, args.loop_steps)
+    return res
+
+
+def loop_row(torch, dev, steps):
+    """Adam on the attributes of the 5M-point loop scene through the renderer
+    (camera + shadow rays, tree built once and refit per step)."""
+    from paper_2405_16788_gb300 import render
+    w = syn.workload("scene-5m-loop")
+    o, d, t = w.meta["rays"]
+    c = w.cloud
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+    rd = render.Renderer(T(c.points), T(c.normals), T(c.areas), T(c.eps), T(o), T(d), T(t),
+                         T(w.meta["t_near"]), T(w.meta["light"]), n_shadow=64,
+                         shadow_jitter=T(w.meta["shadow_jitter"]), queries=T(w.queries))
+    with torch.no_grad():
+        target, _, _ = rd.render(T(w.mu))
+    mu0 = w.mu.copy()
+    mu0[:, 0] = 1.0
+    master = T(mu0).requires_grad_(True)
+    opt = torch.optim.Adam([master], lr=1e-2)
+
+    def one():
+        opt.zero_grad(set_to_none=True)
+        L, _ = rd.loss(master, target)
+        L.backward()
+        opt.step()
+        return L
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        L = one()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nq = rd.R * rd.S + rd.R * rd.K
+    rd.tree.sync_status()
+    return {"workload": "scene-5m-loop", "points": c.n, "queries_per_step": nq,
+            "step_ms": ms, "queries_per_s": nq / (ms * 1e-3), "steps": steps,
+            "loss_last": float(L.detach()),
+            "step": "refit + forward/gradient on camera and shadow rays + their adjoints + "
+                    "PyTorch rendering and Adam"}
 
 
 def dp_cp(C: int) -> int:

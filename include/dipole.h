@@ -53,12 +53,21 @@ typedef enum {
 
 typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
 
+/* Radial factor of the kernel.  REGULARIZED is the paper's method:
+ * rho(r/eps)/r^3 with rho of eq. regularized_poisson (Sec. 4.1).
+ * DESINGULARIZED is the ablation baseline the paper compares against
+ * (Sec. 4.1 footnote; Sec. 7 ablation: "a small cutoff in the denominator"),
+ * read as 1/max(r, eps)^3 with the point's radius eps as the cutoff (eps~ at
+ * a far node); eps = 0 gives the singular kernel in both. */
+typedef enum { DIPOLE_KERNEL_REGULARIZED = 0, DIPOLE_KERNEL_DESINGULARIZED = 1 } dipole_kernel;
+
 /* Octree parameters.  leaf_size in [1, 64] (the paper's leaves are single
  * points, Sec. 6.1; 8 is the default here); max_depth in [0, 10] octal digits
- * of the 30-bit Morton code. */
+ * of the 30-bit Morton code; kernel a dipole_kernel (default REGULARIZED). */
 typedef struct {
     int32_t leaf_size;
     int32_t max_depth;
+    int32_t kernel;
 } dipole_build_params;
 
 typedef struct {
@@ -70,6 +79,7 @@ typedef struct {
     int32_t max_depth;
     float bbox_lo[3];    /* bounding cube of the Morton quantisation */
     float bbox_ext;
+    int32_t kernel;      /* dipole_kernel of the build */
 } dipole_tree_info;
 
 /*
@@ -282,6 +292,23 @@ int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, floa
                         const float* grad_out, const float* grad_grad, float* grad_attrs,
                         float* grad_normals, float* grad_radii, int32_t accumulate,
                         const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream);
+
+/*
+ * Primal queries on a dense grid, e.g. the 512^3 or 1024^3 evaluation grid of
+ * the geometry field that the paper meshes with marching cubes (Sec. 7):
+ * point (i, j, k) is lo + spacing * (i, j, k), computed in float as
+ * lo[0] + ((float)i * spacing) with one rounding per operation (likewise j,
+ * k), 0 <= i < dims[0], 0 <= j < dims[1], 0 <= k < dims[2].  The points are
+ * generated inside the traversal kernel, 32 at a time as 4x4x2 bricks (no
+ * query array and no sort), with the same far test and sums as dipole_forward.
+ *
+ *   lo [3], dims [3]  host arrays; 1 <= dims[d] <= 2^24, product <= 2^40
+ *   spacing           > 0
+ *   out               [dims[2], dims[1], dims[0], channels] float (x fastest)
+ * Errors: as dipole_forward.
+ */
+int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
+                        const int64_t* dims, float beta, float* out, void* stream);
 
 /*
  * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,

@@ -1,6 +1,7 @@
 // C ABI entry points (include/dipole.h): argument checks, error reporting and
 // the tree object's lifetime.  All compute runs in the kernels of
 // tree_build.cu, refit.cu, traverse.cu and sort.cu.
+#include <cmath>
 #include <atomic>
 #include <cstdio>
 #include <string>
@@ -79,15 +80,18 @@ int dipole_build_tree(const float* points, const float* normals, const float* ar
     if (n < 1) return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: n must be >= 1");
     if (n > (int64_t)INT32_MAX / 2)
         return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: n must be < 2^30");
-    int leaf_size = 8, max_depth = 10;
+    int leaf_size = 8, max_depth = 10, kernel = DIPOLE_KERNEL_REGULARIZED;
     if (params) {
         leaf_size = params->leaf_size;
         max_depth = params->max_depth;
+        kernel = params->kernel;
     }
     if (leaf_size < 1 || leaf_size > 64)
         return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: leaf_size must be in [1, 64]");
     if (max_depth < 0 || max_depth > 10)
         return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: max_depth must be in [0, 10]");
+    if (kernel != DIPOLE_KERNEL_REGULARIZED && kernel != DIPOLE_KERNEL_DESINGULARIZED)
+        return dip_fail(DIPOLE_EINVAL, "dipole_build_tree: kernel must be a dipole_kernel");
     configure_pool_once();
     dipole_tree* t = new (std::nothrow) dipole_tree();
     if (!t) return dip_fail(DIPOLE_ENOMEM, "dipole_build_tree: out of host memory");
@@ -95,6 +99,7 @@ int dipole_build_tree(const float* points, const float* normals, const float* ar
     t->n = n;
     t->leaf_size = leaf_size;
     t->max_depth = max_depth;
+    t->kernel = kernel;
     int rc = dip::build_tree(t, points, normals, areas, radii, as_stream(stream));
     if (rc != 0) {
         cudaStreamSynchronize(as_stream(stream));
@@ -120,8 +125,11 @@ int dipole_tree_import(const float* points, const float* normals, const float* a
     if (n_nodes < 1 || n_nodes > 2 * n + 1)
         return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: n_nodes must be in [1, 2n+1]");
     int leaf_size = params ? params->leaf_size : 8, max_depth = params ? params->max_depth : 10;
+    int kernel = params ? params->kernel : DIPOLE_KERNEL_REGULARIZED;
     if (leaf_size < 1 || leaf_size > 64 || max_depth < 0 || max_depth > 10)
         return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: bad leaf_size or max_depth");
+    if (kernel != DIPOLE_KERNEL_REGULARIZED && kernel != DIPOLE_KERNEL_DESINGULARIZED)
+        return dip_fail(DIPOLE_EINVAL, "dipole_tree_import: kernel must be a dipole_kernel");
     // Every index a kernel will follow must stay in range; the structure itself
     // (nesting, order) is not checked: a traversal of a corrupt structure ends
     // at its step bound with DIPOLE_ETRAVERSAL.
@@ -149,6 +157,7 @@ int dipole_tree_import(const float* points, const float* normals, const float* a
     t->nn = n_nodes;
     t->leaf_size = leaf_size;
     t->max_depth = max_depth;
+    t->kernel = kernel;
     int rc = dip::import_tree(t, points, normals, areas, radii, codes, perm, first, count, level,
                               skip, is_leaf, as_stream(stream));
     if (rc != 0) {
@@ -344,6 +353,35 @@ int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, floa
     return dip::query(tree, c, s);
 }
 
+int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
+                        const int64_t* dims, float beta, float* out, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: tree is NULL");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_grid: call dipole_refit first");
+    if (!lo || !dims || !out)
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: lo, dims and out are required");
+    if (!(spacing > 0.0f) || !std::isfinite(spacing))
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: spacing must be finite and > 0");
+    int64_t total = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (!std::isfinite(lo[d])) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: lo must be finite");
+        if (dims[d] < 1 || dims[d] > (int64_t(1) << 24))
+            return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: dims must be in [1, 2^24]");
+        total *= dims[d];
+        if (total > (int64_t(1) << 40))
+            return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: more than 2^40 grid points");
+    }
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: beta must be > 0");
+    dip::QueryCall c;
+    c.mode = dip::kForward;
+    c.q = total; c.beta = beta; c.out = out;
+    for (int d = 0; d < 3; ++d) {
+        c.grid_lo[d] = lo[d];
+        c.grid_dim[d] = dims[d];
+    }
+    c.grid_h = spacing;
+    return dip::query(tree, c, as_stream(stream));
+}
+
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                         int32_t* counts, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: tree is NULL");
@@ -384,6 +422,7 @@ int dipole_tree_info_get(const dipole_tree* tree, dipole_tree_info* info) {
     info->max_depth = tree->max_depth;
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = tree->bbox_host[a];
     info->bbox_ext = tree->bbox_host[3];
+    info->kernel = tree->kernel;
     return DIPOLE_OK;
 }
 

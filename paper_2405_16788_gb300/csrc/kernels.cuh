@@ -47,6 +47,21 @@ __device__ __forceinline__ float rho_over_d3(float d2, float inv_eps) {
     return rho * inv_d3;
 }
 
+// Desingularized radial factor 1 / max(d, delta)^3 with delta = 1/inv_eps (the
+// ablation kernel with a cutoff in the denominator); inv_eps = +inf gives
+// 1/d^3.
+__device__ __forceinline__ float desing_over_d3(float d2, float inv_eps) {
+    const float inv_d = rsqrtf(d2);
+    const float t = d2 * inv_d * inv_eps;  // d / delta
+    if (t >= 1.0f) return inv_d * inv_d * inv_d;
+    return inv_eps * inv_eps * inv_eps;
+}
+
+// The radial factor of the tree's kernel (kernel is uniform across a launch).
+__device__ __forceinline__ float radial_over_d3(float d2, float inv_eps, int kernel) {
+    return kernel == 0 ? rho_over_d3(d2, inv_eps) : desing_over_d3(d2, inv_eps);
+}
+
 // Kahan-compensated add: s + (c) tracks the sum, c holds the lost low part
 // with the sign convention sum = s - c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {

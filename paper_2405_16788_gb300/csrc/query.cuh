@@ -10,6 +10,15 @@ namespace dip {
 
 constexpr int kQThreads = 256;
 
+// A dense grid of query points lo + h (i, j, k), 0 <= i < dim[0] etc., walked
+// as 4x4x2 bricks (one 32-query packet each); nb[0] = 0 means no grid.
+struct GridSpec {
+    float lo[3] = {0.f, 0.f, 0.f};
+    float h = 0.f;
+    int64_t dim[3] = {0, 0, 0};
+    int64_t nb[3] = {0, 0, 0};
+};
+
 struct QueryArgs {
     const NodeRec* nodes;
     const PointRec* pts;
@@ -19,6 +28,7 @@ struct QueryArgs {
     int64_t nq;
     const uint32_t* qperm;
     float beta;
+    int kernel;         // dipole_kernel of the tree
     int C;
     int Cp;
     const void* mu;
@@ -35,6 +45,7 @@ struct QueryArgs {
     unsigned long long* work;
     const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
     uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
+    GridSpec grid;           // dense-grid queries instead of q / qperm
 };
 
 // n attribute values (n = 1, 2 or 4; p aligned to n elements) as floats.

@@ -22,7 +22,7 @@
 namespace dip {
 namespace {
 
-template <int CP, typename AT, int MODE>
+template <int CP, typename AT, int MODE, int KERN>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
 k_query(const QueryArgs a) {
     constexpr int SR = srow(CP);
@@ -39,12 +39,28 @@ k_query(const QueryArgs a) {
         pk = __shfl_sync(FULL, pk, 0);
         if ((int64_t)pk * 32 >= a.nq) break;
         const int64_t pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
-        const int64_t base = pm * 32;
-        const int64_t qi = base + lane;
-        const bool valid = qi < a.nq;
-        const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+        bool valid;
+        int64_t qo;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
+        if (a.grid.nb[0] > 0) {
+            // dense grid: packet pm is the 4x4x2 brick pm (bricks x-fastest);
+            // the lane's point is lo + h * (i, j, k), one rounding per operation
+            const int64_t bx = pm % a.grid.nb[0], r = pm / a.grid.nb[0];
+            const int64_t by = r % a.grid.nb[1], bz = r / a.grid.nb[1];
+            const int64_t i = 4 * bx + (lane & 3), j = 4 * by + ((lane >> 2) & 3), k = 2 * bz + (lane >> 4);
+            valid = i < a.grid.dim[0] && j < a.grid.dim[1] && k < a.grid.dim[2];
+            qo = valid ? i + a.grid.dim[0] * (j + a.grid.dim[1] * k) : 0;
+            if (valid) {
+                x0 = __fadd_rn(a.grid.lo[0], __fmul_rn((float)i, a.grid.h));
+                x1 = __fadd_rn(a.grid.lo[1], __fmul_rn((float)j, a.grid.h));
+                x2 = __fadd_rn(a.grid.lo[2], __fmul_rn((float)k, a.grid.h));
+            }
+        } else {
+            const int64_t qi = pm * 32 + lane;
+            valid = qi < a.nq;
+            qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+            if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
+        }
 
         // Forward sums: plain float partial sums (part), folded every kFoldSteps
         // warp steps into a Kahan-compensated sum (acc, cmp) for small channel
@@ -132,7 +148,7 @@ k_query(const QueryArgs a) {
                 if (__any_sync(FULL, far)) {
                     // far field, eq. farfield: rho(d/eps~) S.(p~ - x) / d^3 (1/4pi applied at the end)
                     float k = 0.f;
-                    if (far) k = rho_over_d3(d2, __int_as_float(meta.w));
+                    if (far) k = radial_over_d3(d2, __int_as_float(meta.w), KERN);
                     const float vx = -k * dx, vy = -k * dy, vz = -k * dz;
                     if (MODE == kForward) {
                         const float* Sr = a.S + (size_t)n * SR;
@@ -169,7 +185,7 @@ k_query(const QueryArgs a) {
                             const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
                             const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                             if (r2 > 0.f)
-                                k = rho_over_d3(r2, pr.geo.w) *
+                                k = radial_over_d3(r2, pr.geo.w, KERN) *
                                     fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
                         }
                         if (MODE == kForward) {
@@ -228,11 +244,19 @@ __global__ void k_iota(uint32_t* v, int64_t n) {
 // Packets below this count are too few for the queue's tail to matter.
 constexpr int64_t kOrderMinPackets = 2048;
 
+template <int CP, typename AT, int MODE, int KERN>
+void launch_query_k(const QueryArgs& a, cudaStream_t s) {
+    static int per_sm = 0;
+    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN>, a.nq, per_sm);
+    note_launch(); k_query<CP, AT, MODE, KERN><<<grid, kQThreads, 0, s>>>(a);
+}
+
+// The kernel choice is a template parameter: a runtime branch between the two
+// radial factors costs the forward registers.
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
-    static int per_sm = 0;
-    const unsigned grid = query_grid(k_query<CP, AT, MODE>, a.nq, per_sm);
-    note_launch(); k_query<CP, AT, MODE><<<grid, kQThreads, 0, s>>>(a);
+    if (MODE == kCount || a.kernel == 0) launch_query_k<CP, AT, MODE, 0>(a, s);
+    else launch_query_k<CP, AT, MODE, 1>(a, s);
 }
 
 template <int MODE>
@@ -327,6 +351,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.nq = q;
     a.qperm = idx;
     a.beta = beta;
+    a.kernel = t->kernel;
     a.C = t->C;
     a.Cp = t->Cp;
     a.mu = t->mu;
@@ -343,6 +368,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.work = work;
     a.porder = nullptr;  // Morton packet order
     a.pcost = nullptr;
+    a.grid = GridSpec{};
     rc = dispatch<kForward>(t, a, s);
     if (rc) return rc;
     DIP_CUDA_TRY(cudaGetLastError());
@@ -361,7 +387,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
     unsigned long long* work = nullptr;
     DIP_CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(unsigned long long), s));
-    if (q > 0) {
+    const bool grid = call.grid_dim[0] > 0;
+    if (q > 0 && !grid) {
         DIP_CUDA_TRY(cudaMallocAsync((void**)&codes, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&ktmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
@@ -382,7 +409,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     // order of the packets, never a result.
     const uint32_t* porder = nullptr;
     uint32_t* pcost = nullptr;
-    if (q > 0 && np >= kOrderMinPackets && mode != kCount) {
+    if (q > 0 && !grid && np >= kOrderMinPackets && mode != kCount) {
         if (plan_in && plan_cost) {
             DIP_CUDA_TRY(cudaMemcpyAsync(codes, plan_cost, sizeof(uint32_t) * np,
                                          cudaMemcpyDeviceToDevice, s));
@@ -414,6 +441,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.nq = q;
         a.qperm = idx;
         a.beta = call.beta;
+        a.kernel = t->kernel;
         a.C = t->C;
         a.Cp = t->Cp;
         a.mu = t->mu;
@@ -430,6 +458,18 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.work = work;
         a.porder = porder;
         a.pcost = pcost;
+        a.grid = GridSpec{};
+        if (grid) {
+            for (int d = 0; d < 3; ++d) {
+                a.grid.lo[d] = call.grid_lo[d];
+                a.grid.dim[d] = call.grid_dim[d];
+            }
+            a.grid.h = call.grid_h;
+            a.grid.nb[0] = (call.grid_dim[0] + 3) / 4;
+            a.grid.nb[1] = (call.grid_dim[1] + 3) / 4;
+            a.grid.nb[2] = (call.grid_dim[2] + 1) / 2;
+            a.nq = 32 * a.grid.nb[0] * a.grid.nb[1] * a.grid.nb[2];  // one packet per brick
+        }
         if (mode == kForward) rc = dispatch<kForward>(t, a, s);
         else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
         else if (mode == kCount) rc = dispatch<kCount>(t, a, s);

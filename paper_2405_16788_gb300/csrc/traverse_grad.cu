@@ -81,23 +81,76 @@ __device__ __forceinline__ void grad_factors(float d2, float inv_eps, float& a, 
     b = (trho1 - 3.0f * rho) * (inv_d3 * inv_d2);
 }
 
-// a_e = da/deps = -(4/sqrt(pi)) t^3 exp(-t^2)/(eps d^3) and
-// b_e = db/deps = (8/sqrt(pi)) t^5 exp(-t^2)/(eps d^5), t = d/eps.  No cut at
-// kTCut: far from every point these tiny values are the whole eps-gradient.
-// Both are 0 for eps = 0 (t = inf) and where exp(-t^2) underflows.
-__device__ __forceinline__ void eps_factors(float d2, float inv_eps, float& ae, float& be) {
+// grad_factors plus the eps-derivatives a_e = da/deps =
+// -(4/sqrt(pi)) t^3 exp(-t^2)/(eps d^3) and b_e = db/deps =
+// (8/sqrt(pi)) t^5 exp(-t^2)/(eps d^5), sharing the reciprocal square root and
+// the exponential.  a_e, b_e have no cut at kTCut: far from every point these
+// tiny values are the whole eps-gradient; they are 0 for eps = 0 (t = inf) and
+// from t = 10, where exp(-t^2) leaves the float range.
+__device__ __forceinline__ void geom_factors(float d2, float inv_eps, float& a, float& b, float& ae,
+                                             float& be) {
     const float inv_d = rsqrtf(d2);
+    const float inv_d2 = inv_d * inv_d;
+    const float inv_d3 = inv_d2 * inv_d;
     const float t = d2 * inv_d * inv_eps;
-    if (!(t < 10.0f)) {  // exp(-100) is below the float range; also t = inf
+    const float u = t * t;
+    const float e = t < 10.0f ? __expf(-u) : 0.0f;
+    if (t >= kTCut) {
+        a = inv_d3;
+        b = -3.0f * inv_d3 * inv_d2;
+    } else if (t < kTSeries) {
+        float p = kSer6;
+        p = fmaf(p, u, kSer5);
+        p = fmaf(p, u, kSer4);
+        p = fmaf(p, u, kSer3);
+        p = fmaf(p, u, kSer2);
+        p = fmaf(p, u, kSer1);
+        p = fmaf(p, u, kSer0);
+        float r = kGSer6;
+        r = fmaf(r, u, kGSer5);
+        r = fmaf(r, u, kGSer4);
+        r = fmaf(r, u, kGSer3);
+        r = fmaf(r, u, kGSer2);
+        r = fmaf(r, u, kGSer1);
+        r = fmaf(r, u, kGSer0);
+        const float ie2 = inv_eps * inv_eps, ie3 = ie2 * inv_eps;
+        a = p * ie3;
+        b = r * (ie3 * ie2);
+    } else {
+        const float rho = erff(t) - kTwoOverSqrtPi * t * e;
+        const float trho1 = 2.0f * kTwoOverSqrtPi * u * t * e;
+        a = rho * inv_d3;
+        b = (trho1 - 3.0f * rho) * (inv_d3 * inv_d2);
+    }
+    if (t < 10.0f) {
+        const float g = 2.0f * kTwoOverSqrtPi * e * t * u * inv_eps;
+        ae = -g * inv_d3;
+        be = 2.0f * g * u * (inv_d3 * inv_d2);
+    } else {
         ae = 0.0f;
         be = 0.0f;
-        return;
     }
-    const float u = t * t;
-    const float e = 2.0f * kTwoOverSqrtPi * __expf(-u) * t * u * inv_eps;  // (4/sqrt(pi)) t^3 e^-t^2 / eps
-    const float inv_d3 = inv_d * inv_d * inv_d;
-    ae = -e * inv_d3;
-    be = 2.0f * e * u * (inv_d3 * inv_d * inv_d);
+}
+
+// The desingularized kernel's factors (1/max(d, delta)^3, delta = 1/inv_eps):
+// outside the cutoff a = 1/d^3, b = -3/d^5 and no delta-dependence; inside,
+// a = 1/delta^3, b = 0, a_e = da/ddelta = -3/delta^4, b_e = 0.
+__device__ __forceinline__ void desing_factors(float d2, float inv_eps, float& a, float& b, float& ae,
+                                               float& be) {
+    const float inv_d = rsqrtf(d2);
+    const float t = d2 * inv_d * inv_eps;
+    be = 0.0f;
+    if (t >= 1.0f) {
+        const float inv_d3 = inv_d * inv_d * inv_d;
+        a = inv_d3;
+        b = -3.0f * inv_d3 * inv_d * inv_d;
+        ae = 0.0f;
+    } else {
+        const float ie3 = inv_eps * inv_eps * inv_eps;
+        a = ie3;
+        b = 0.0f;
+        ae = -3.0f * ie3 * inv_eps;
+    }
 }
 
 // Three resident blocks for the forward (80 registers, a few spilled bytes:
@@ -208,8 +261,12 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_q
                 if (act) next = (far || leaf) ? (unsigned)meta.x : n + 1u;
 
                 if (__any_sync(FULL, far)) {
-                    float fa = 0.f, fb = 0.f;
-                    if (far) grad_factors(d2, __int_as_float(meta.w), fa, fb);
+                    float fa = 0.f, fb = 0.f, fae = 0.f, fbe = 0.f;
+                    if (far) {
+                        if (a.kernel) desing_factors(d2, __int_as_float(meta.w), fa, fb, fae, fbe);
+                        else if (GEOM) geom_factors(d2, __int_as_float(meta.w), fa, fb, fae, fbe);
+                        else grad_factors(d2, __int_as_float(meta.w), fa, fb);
+                    }
                     const float vx = -dx, vy = -dy, vz = -dz;  // v = p~ - x
                     if (FWD) {
                         float s[4 * ((3 * CG + 3) / 4)];
@@ -244,8 +301,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_q
                         adjoint_vec_reduce<CG>(val, a.dS + (size_t)n * SR + 3 * c0, ord[0], lane);
                         if (GEOM) {
                             // d eps~_t += sum_c [g^c a_e (S^c.v) - a_e (S^c.G^c) - b_e (S^c.v)(v.G^c)]
-                            float ae = 0.f, be = 0.f;
-                            if (far) eps_factors(d2, __int_as_float(meta.w), ae, be);
+                            const float ae = fae, be = fbe;
                             float s[4 * ((3 * CG + 3) / 4)];
 #pragma unroll
                             for (int j = 0; j < (3 * CG + 3) / 4; ++j) {
@@ -274,12 +330,14 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_q
                     const int f = meta.y, cnt = meta.z;
                     for (int j = 0; j < cnt; ++j) {
                         const PointRec pr = pts[f + j];
-                        float fa = 0.f, fb = 0.f, wu = 0.f;
+                        float fa = 0.f, fb = 0.f, wu = 0.f, pae = 0.f, pbe = 0.f;
                         const float ux = pr.geo.x - x0, uy = pr.geo.y - x1, uz = pr.geo.z - x2;
                         if (open_leaf) {
                             const float r2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
                             if (r2 > 0.f) {
-                                grad_factors(r2, pr.geo.w, fa, fb);
+                                if (a.kernel) desing_factors(r2, pr.geo.w, fa, fb, pae, pbe);
+                                else if (GEOM) geom_factors(r2, pr.geo.w, fa, fb, pae, pbe);
+                                else grad_factors(r2, pr.geo.w, fa, fb);
                                 wu = fmaf(pr.w.x, ux, fmaf(pr.w.y, uy, pr.w.z * uz));
                             }
                         }
@@ -314,11 +372,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_q
                             if (GEOM) {
                                 // normal (A sum_c mu^c [g^c a u - a G^c - b (u.G^c) u]) and
                                 // radius (sum_c mu^c [g^c a_e (w.u) - a_e (w.G^c) - b_e (w.u)(u.G^c)])
-                                float ae = 0.f, be = 0.f;
-                                if (open_leaf && fa != 0.f) {
-                                    const float r2 = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
-                                    eps_factors(r2, pr.geo.w, ae, be);
-                                }
+                                const float ae = pae, be = pbe;
                                 float m[CG];
                                 load_row<AT>(reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * Cp + c0, m, CG);
                                 float gv[4] = {0.f, 0.f, 0.f, 0.f};

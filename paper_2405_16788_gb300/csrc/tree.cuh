@@ -13,6 +13,7 @@ struct dipole_tree {
     int64_t nn = 0;
     int leaf_size = 8;
     int max_depth = 10;
+    int kernel = 0;              // dipole_kernel: 0 regularized, 1 desingularized
 
     // points, Morton order
     dip::PointRec* pts = nullptr;
@@ -112,6 +113,11 @@ struct QueryCall {
     uint32_t* plan_perm = nullptr;
     uint32_t* plan_cost = nullptr;
     bool plan_in = false;
+    // dense grid (kForward / kCount): queries = lo + h (i, j, k), out in
+    // x-fastest grid order; grid_dim[0] = 0 means no grid
+    float grid_lo[3] = {0.f, 0.f, 0.f};
+    float grid_h = 0.f;
+    int64_t grid_dim[3] = {0, 0, 0};
 };
 
 int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s);

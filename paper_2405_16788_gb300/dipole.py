@@ -45,15 +45,26 @@ class DipoleError(RuntimeError):
         self.code = code
 
 
+DIPOLE_KERNEL_REGULARIZED = 0
+DIPOLE_KERNEL_DESINGULARIZED = 1
+_KERNELS = {"regularized": DIPOLE_KERNEL_REGULARIZED, "desingularized": DIPOLE_KERNEL_DESINGULARIZED}
+
+
+def _kernel_code(kernel) -> int:
+    return _KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+
+
 class _BuildParams(ctypes.Structure):
-    _fields_ = [("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32)]
+    _fields_ = [("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("kernel", ctypes.c_int32)]
 
 
 class _TreeInfo(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("channels", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32),
-                ("bbox_lo", ctypes.c_float * 3), ("bbox_ext", ctypes.c_float)]
+                ("bbox_lo", ctypes.c_float * 3), ("bbox_ext", ctypes.c_float),
+                ("kernel", ctypes.c_int32)]
 
 
 _lib = None
@@ -140,15 +151,16 @@ def _dev(t: torch.Tensor, name: str, dtype=torch.float32, shape=None) -> ctypes.
 # ---------------------------------------------------------------- C names
 
 def dipole_build_tree(points, normals, areas, radii=None, leaf_size=8, max_depth=10,
-                      stream=None) -> int:
-    """Build the octree and node geometry; returns the opaque tree handle."""
+                      stream=None, kernel="regularized") -> int:
+    """Build the octree and node geometry; returns the opaque tree handle.
+    kernel: "regularized" (the paper's) or "desingularized" (its ablation)."""
     lib = load_library()
     n = int(points.shape[0])
     pp = _dev(points, "points", shape=(n, 3))
     pn = _dev(normals, "normals", shape=(n, 3))
     pa = _dev(areas, "areas", shape=(n,))
     pr = None if radii is None else _dev(radii, "radii", shape=(n,))
-    params = _BuildParams(int(leaf_size), int(max_depth))
+    params = _BuildParams(int(leaf_size), int(max_depth), _kernel_code(kernel))
     h = ctypes.c_void_p()
     _check(lib.dipole_build_tree(pp, pn, pa, pr, n, ctypes.byref(params), _stream(stream),
                                  ctypes.byref(h)))
@@ -307,7 +319,7 @@ def dipole_tree_info_get(tree: int) -> dict:
     _check(load_library().dipole_tree_info_get(ctypes.c_void_p(tree), ctypes.byref(info)))
     return dict(n_points=info.n_points, n_nodes=info.n_nodes, channels=info.channels,
                 dtype=info.dtype, leaf_size=info.leaf_size, max_depth=info.max_depth,
-                bbox_lo=list(info.bbox_lo), bbox_ext=info.bbox_ext)
+                bbox_lo=list(info.bbox_lo), bbox_ext=info.bbox_ext, kernel=info.kernel)
 
 
 def dipole_tree_export(tree: int, moments: bool = False, stream=None) -> dict:
@@ -336,7 +348,7 @@ def dipole_probe_l2(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=N
 
 
 def dipole_tree_import(points, normals, areas, radii, exported: dict, leaf_size=8, max_depth=10,
-                       stream=None) -> int:
+                       stream=None, kernel="regularized") -> int:
     """Rebuild a tree from dipole_tree_export's arrays (host numpy) and the
     point inputs (CUDA tensors); returns the tree handle."""
     lib = load_library()
@@ -348,7 +360,7 @@ def dipole_tree_import(points, normals, areas, radii, exported: dict, leaf_size=
     code = None if code is None else np.ascontiguousarray(code, dtype=np.uint32)
     nn = int(host["first"].shape[0])
     hp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
-    params = _BuildParams(int(leaf_size), int(max_depth))
+    params = _BuildParams(int(leaf_size), int(max_depth), _kernel_code(kernel))
     h = ctypes.c_void_p()
     _check(lib.dipole_tree_import(_dev(points, "points", shape=(n, 3)),
                                   _dev(normals, "normals", shape=(n, 3)),
@@ -372,24 +384,24 @@ class DipoleTree:
     caller's point order; outputs come back in that order."""
 
     def __init__(self, points, normals, areas, radii=None, leaf_size=8, max_depth=10,
-                 stream=None):
+                 stream=None, kernel="regularized"):
         self.n = int(points.shape[0])
         # kernels still read the inputs after the build call returns (stream order)
         self._inputs = (points, normals, areas, radii)
         self.handle = dipole_build_tree(points, normals, areas, radii, leaf_size, max_depth,
-                                        stream)
+                                        stream, kernel)
         self.C = 0
         self.device = points.device
 
     @classmethod
     def from_export(cls, points, normals, areas, radii, exported: dict, leaf_size=8, max_depth=10,
-                    stream=None) -> "DipoleTree":
+                    stream=None, kernel="regularized") -> "DipoleTree":
         """A tree rebuilt from dipole_tree_export's arrays (checkpoint / resume)."""
         self = cls.__new__(cls)
         self.n = int(points.shape[0])
         self._inputs = (points, normals, areas, radii)
         self.handle = dipole_tree_import(points, normals, areas, radii, exported, leaf_size,
-                                         max_depth, stream)
+                                         max_depth, stream, kernel)
         self.C = 0
         self.device = points.device
         return self
