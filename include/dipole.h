@@ -56,8 +56,8 @@ typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
 /* Radial factor of the kernel.  REGULARIZED is the paper's method:
  * rho(r/eps)/r^3 with rho of eq. regularized_poisson (Sec. 4.1).
  * DESINGULARIZED is the ablation baseline the paper compares against
- * (Sec. 4.1 footnote; Sec. 7 ablation: "a small cutoff in the denominator"),
- * read as 1/max(r, eps)^3 with the point's radius eps as the cutoff (eps~ at
+ * (Sec. 4.1 footnote; Sec. 7 ablation), which bounds the kernel's denominator
+ * away from zero; read as 1/max(r, eps)^3 with the point's radius eps as the cutoff (eps~ at
  * a far node); eps = 0 gives the singular kernel in both. */
 typedef enum { DIPOLE_KERNEL_REGULARIZED = 0, DIPOLE_KERNEL_DESINGULARIZED = 1 } dipole_kernel;
 

@@ -58,8 +58,8 @@
  *       eps_m through eps~_t (R5), d eps~_t/d eps_m = A_m/A~_t, with one
  *       scalar stage-1 sum d eps~_t per node.  eps = 0 has zero eps-gradient.
  *       The paper's single global eps receives the sum over m.
- *   R11 Desingularized kernel (the ablation baseline: "a small cutoff in the
- *       denominator" of the Poisson kernel, Sec. 4.1 footnote and Sec. 7):
+ *   R11 Desingularized kernel (the ablation baseline of Sec. 4.1, footnote,
+ *       and Sec. 7, which bounds the Poisson kernel's denominator from below):
  *       1/r^3 -> 1/max(r, eps)^3 with the point's radius as the cutoff, eps~
  *       at a far node; written as rho_d(r, eps) = min(1, (r/eps)^3) in place
  *       of rho so that every formula above applies: a = 1/max(r, eps)^3,

@@ -60,6 +60,11 @@ def test_argument_errors_without_gpu(lib_path):
     assert lib.dipole_forward_grad(None, None, 0, 2.0, None, None, None, None, None) == -1
     assert lib.dipole_adjoint_grad(None, None, 0, 2.0, None, None, None, 0, None, None, None) == -1
     lib.dipole_tree_destroy(None)  # a no-op
+    fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    bad_kernel = dipole._BuildParams(8, 10, 2)
+    assert lib.dipole_build_tree(fake, fake, fake, None, 10, ctypes.byref(bad_kernel), None,
+                                 ctypes.byref(out)) == -1
+    assert "kernel" in dipole.dipole_last_error()
 
 
 def test_oracle_and_library_share_nothing():
