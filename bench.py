@@ -96,7 +96,7 @@ def config_of(w, flush: str):
 
 # ------------------------------------------------------------------ oracle
 
-def oracle_sample(w, seconds: float):
+def oracle_sample(w, seconds: float, keep: bool = False):
     """Time the oracle (as it stands) on a bounded sample of the workload and
     scale to one full step: tree build and update once, forward and adjoint
     per query, adjoint's per-call fixed cost (stage 2) measured separately."""
@@ -120,14 +120,19 @@ def oracle_sample(w, seconds: float):
     q = w.queries[idx]
     g = syn.upstream_grad(n_s, w.mu.shape[1], seed=77).astype(np.float64)
     t0 = time.perf_counter()
-    T.forward(q, BETA)
+    fwd_ref = T.forward(q, BETA)
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
     T.adjoint(q[:1], BETA, g[:1])
     t_adj_fixed = time.perf_counter() - t0
     t0 = time.perf_counter()
-    T.adjoint(q, BETA, g)
+    adj_ref = T.adjoint(q, BETA, g)
     t_adj = time.perf_counter() - t0
+    # the plain O(NQ) sum on a few queries, as interactions per second
+    nb = 128
+    t0 = time.perf_counter()
+    oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, q[:nb])
+    brute_ips = nb * c.n / (time.perf_counter() - t0)
     per_q = t_fwd / n_s + max(t_adj - t_adj_fixed, 0.0) / n_s
     est = t_build + t_update + t_adj_fixed + Q * per_q
     return dict(value=Q / est, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
@@ -137,7 +142,9 @@ def oracle_sample(w, seconds: float):
                 seconds_per_step_est=est, build_s=t_build, update_s=t_update,
                 fwd_us_per_query=1e6 * t_fwd / n_s,
                 adj_us_per_query=1e6 * max(t_adj - t_adj_fixed, 0.0) / n_s,
-                adj_fixed_s=t_adj_fixed)
+                adj_fixed_s=t_adj_fixed, brute_force_interactions_per_s=brute_ips,
+                brute_force_sample=f"{nb} queries x {c.n} points"), \
+        (dict(idx=idx, g=g, fwd=fwd_ref, adj=adj_ref) if keep else None)
 
 
 def run_reference(args):
@@ -148,7 +155,7 @@ def run_reference(args):
     per = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(w, per)
-    vals = [oracle_sample(w, per) for _ in range(args.steps)]
+    vals = [oracle_sample(w, per)[0] for _ in range(args.steps)]
     secs = [v["seconds_per_step_est"] for v in vals]
     value = len(w.queries) / statistics.mean(secs)
     cb = dict(vals[-1])
@@ -221,7 +228,7 @@ class ClockSampler:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ["traverse.cu", "kernels.cuh"]:
+    for f in ["traverse.cu", "query.cuh", "kernels.cuh", "common.cuh"]:
         with open(os.path.join(ROOT, "paper_2405_16788_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -384,6 +391,9 @@ def run_ours(args):
                 "l2_probe_gbs": l2, "frac_of_l2_probe": (achieved / l2) if l2 else None,
                 "working_set_mb": (N * (32 + 4 * C) + info["n_nodes"] * (32 + 4 * srow(C))) / 2 ** 20}
     breakdown = {"build_ms": ph[0], "refit_ms": ph[1], "forward_ms": ph[2], "adjoint_ms": ph[3],
+                 "forward_queries_per_s": Q / (ph[2] * 1e-3),
+                 "adjoint_queries_per_s": Q / (ph[3] * 1e-3),
+                 "refit_forward_adjoint_queries_per_s": Q / ((ph[1] + ph[2] + ph[3]) * 1e-3),
                  "interactions_per_s": world * (An + Ln) * 2 / (ms_per_step * 1e-3),
                  "nodes": info["n_nodes"]}
 
@@ -445,8 +455,10 @@ def run_ours(args):
                "steps": k_e2e, "timing": "host wall clock, pinned host buffers, sync per step"}
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(w, args.cpu_seconds)
+        cpu, ref = oracle_sample(w, args.cpu_seconds, keep=True)
+        accuracy = sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -456,11 +468,38 @@ def run_ours(args):
                 "config": config_of(w, "flushed between timed steps (512 MB write)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "breakdown": breakdown,
-                "bf16_attrs": bf16, "next_rows": nxt, "impl": "ours"}
+                "bf16_attrs": bf16, "next_rows": nxt, "accuracy": accuracy, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         td.destroy_process_group()
     return 0
+
+
+def sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref):
+    """Errors of the GPU path against the oracle's FP64 Barnes-Hut on the CPU
+    baseline's query sample: forward on those queries, adjoint with the
+    upstream gradient nonzero on them only (so the oracle's adjoint over the
+    sample is the whole answer).  Per channel max|y - r| / max|r|."""
+    def normwise(y, r):
+        y, r = np.asarray(y, np.float64), np.asarray(r, np.float64)
+        den = np.max(np.abs(r), axis=0)
+        return (np.max(np.abs(y - r), axis=0) / np.where(den > 0, den, 1.0)).tolist()
+    h = dp.dipole_build_tree(P, Nr, A, E, LEAF, 10)
+    dp.dipole_refit(h, MU)
+    out = torch.empty((Q, C), device=dev)
+    dp.dipole_forward(h, X, BETA, out)
+    gfull = torch.zeros((Q, C), device=dev)
+    idx = torch.from_numpy(ref["idx"]).to(dev)
+    gfull[idx] = torch.from_numpy(ref["g"].astype(np.float32)).to(dev)
+    grad = torch.empty((N, C), device=dev)
+    dp.dipole_adjoint(h, X, BETA, gfull, grad, False)
+    dp.dipole_sync_status(h)
+    fwd = out[idx].cpu().numpy()
+    adj = grad.cpu().numpy()
+    dp.dipole_tree_destroy(h)
+    return {"forward_normwise": normwise(fwd, ref["fwd"]), "adjoint_normwise": normwise(adj, ref["adj"]),
+            "queries": int(len(ref["idx"])),
+            "against": "oracle FP64 Barnes-Hut, same tree rules; gates 1e-4 forward, 1e-3 adjoint"}
 
 
 def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args):

@@ -153,10 +153,12 @@ __device__ __forceinline__ void desing_factors(float d2, float inv_eps, float& a
     }
 }
 
-// Three resident blocks for the forward (80 registers, a few spilled bytes:
-// -10% time against two blocks at 100 registers); two for the adjoints.
+// Three resident blocks for the forward and the normal/radius adjoint (80
+// registers, a few spilled bytes: -10% and -9% against two blocks at 100 and
+// 109 registers); two for the gradient adjoint (72 registers fit three anyway).
 template <int CG, typename AT, int MODE>
-__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad) ? 3 : 2) k_query_grad(const QueryArgs a) {
+__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kAdjointGeom) ? 3 : 2)
+    k_query_grad(const QueryArgs a) {
     static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
     constexpr bool FWD = MODE == kForwardGrad;
     constexpr bool GEOM = MODE == kAdjointGeom;  // also the normal and radius gradients

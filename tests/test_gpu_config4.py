@@ -1,0 +1,42 @@
+"""Mixed precision at full size: 3,000,000 points, 16 channels stored in
+bfloat16, 2,097,152 queries.  On a 10,000-query subsample: the bf16 path
+against the oracle on the bf16-rounded attributes (1e-4, the kernel's own
+error), against the oracle on the float32 attributes (relative 2-norm 3e-3 per
+channel: the bf16 quantisation of the inputs), the float32 path on the same
+GPU (1e-4); the adjoint (upstream gradient on the subsample only) 1e-3."""
+import numpy as np
+import pytest
+
+from paper_2405_16788_gb300 import synthetic as syn
+from _helpers import bf16_round, gpu_tree, normwise, oracle_tree, rel_l2, to_dev
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def test_config4_bf16_full_size_subsample():
+    import torch
+    w = syn.workload("scene-3m-bf16")
+    Q, C = len(w.queries), w.mu.shape[1]
+    assert (w.cloud.n, Q, C) == (3_000_000, 2_097_152, 16)
+    idx = np.random.default_rng(4).choice(Q, 10000, replace=False)
+    gt = gpu_tree(w.cloud)
+    X = to_dev(w.queries)
+    gt.refit(to_dev(w.mu).to(torch.bfloat16))
+    yb = gt.forward(X, 2.0)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    g = np.zeros((Q, C), np.float32)
+    g[idx] = syn.upstream_grad(10000, C, seed=21)
+    ga = gt.adjoint(X, 2.0, to_dev(g)).cpu().numpy()
+    gt.refit(to_dev(w.mu))
+    yf = gt.forward(X, 2.0)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    gt.sync_status()
+
+    ot = oracle_tree(w.cloud)
+    ot.update(bf16_round(w.mu))
+    ref_b = ot.forward(w.queries[idx], 2.0)
+    aref = ot.adjoint(w.queries[idx], 2.0, g[idx].astype(np.float64))
+    ot.update(w.mu)
+    ref_f = ot.forward(w.queries[idx], 2.0)
+    assert np.all(normwise(yb, ref_b) <= 1e-4), normwise(yb, ref_b)
+    assert np.all(rel_l2(yb, ref_f) <= 3e-3), rel_l2(yb, ref_f)
+    assert np.all(normwise(yf, ref_f) <= 1e-4), normwise(yf, ref_f)
+    assert np.all(normwise(ga, aref) <= 1e-3), normwise(ga, aref)
