@@ -414,7 +414,8 @@ def run_ours(args):
     # dense grid, training loop (timed with CUDA events, untimed for `value`) ----
     nxt = None
     if rank == 0 and not args.no_next:
-        nxt = next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args)
+        nxt = next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args,
+                        (Tn, An, Ln), hbm_peak)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -502,7 +503,8 @@ def sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref):
             "against": "oracle FP64 Barnes-Hut, same tree rules; gates 1e-4 forward, 1e-3 adjoint"}
 
 
-def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args):
+def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args, counts,
+              hbm_peak):
     """Timings of the rows built beyond the forward/adjoint step, each the
     median of 5 launches after one warm-up, L2 flushed before each."""
     def timed(fn, reps=5):
@@ -531,10 +533,23 @@ def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, arg
     f_ms = timed(lambda: dp.dipole_forward_grad(h, X, BETA, OUT, GX, plan))
     a_ms = timed(lambda: dp.dipole_adjoint_grad(h, X, BETA, G, GG, GM, False, plan))
     geo_ms = timed(lambda: dp.dipole_adjoint_geom(h, X, BETA, G, GG, GM, GN, GE, False, plan))
+    # algorithmic bytes per launch, same walk as the forward (per-query counts):
+    # forward_grad writes D and grad D (16C B per query); the normal/radius
+    # adjoint reads g and G (16C), the moments of every far node (12C + 4) and
+    # the attributes of every leaf point (4C) besides the point records (32)
+    Tn, An, Ln = counts
+    b_fg = 16 * Tn + (4 + 12 * C) * An + (28 + 4 * C) * Ln + (12 + 16 * C) * Q
+    b_geo = 16 * Tn + (4 + 12 * C) * An + (32 + 4 * C) * Ln + (12 + 16 * C) * Q
     res = {"spatial_gradient": {
         "forward_grad_ms": f_ms, "adjoint_grad_ms": a_ms,
         "queries_per_s_fwd_adj": Q / ((f_ms + a_ms) * 1e-3),
         "adjoint_geom_ms": geo_ms,
+        "forward_grad_logical_gbs": b_fg / (f_ms * 1e-3) / 1e9,
+        "forward_grad_frac_of_hbm": b_fg / (f_ms * 1e-3) / 1e9 / hbm_peak,
+        "adjoint_geom_logical_gbs": b_geo / (geo_ms * 1e-3) / 1e9,
+        "adjoint_geom_frac_of_hbm": b_geo / (geo_ms * 1e-3) / 1e9 / hbm_peak,
+        "bytes_formulas": {"forward_grad": "16*tested + (4+12C)*far + (28+4C)*leaf + (12+16C)*queries",
+                           "adjoint_geom": "16*tested + (4+12C)*far + (32+4C)*leaf + (12+16C)*queries"},
         "workload": "the bench workload's tree and queries, C=4, plan from forward_grad"}}
     dims = (512, 512, 512)
     grid_out = torch.empty((dims[2], dims[1], dims[0], C), device=dev)
