@@ -198,18 +198,23 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
 
 /*
  * Forward and adjoint sharing a query plan (caller-owned device buffers):
- *   plan_perm [q]              uint32, written by dipole_forward_planned: the Morton
- *                              order of the queries (a permutation of [0, q))
- *   plan_cost [ceil(q / 32)]   uint32, written by dipole_forward_planned: the traversal
- *                              steps of every 32-query packet
+ *   plan_perm [q]                  uint32, written by dipole_forward_planned: the Morton
+ *                                  order of the queries (a permutation of [0, q))
+ *   plan_cost [8 * ceil(q / 32)]   uint32, written by dipole_forward_planned: a record of
+ *                                  every 32-query packet's walk: first ceil(q/32) sort keys
+ *                                  (0xffff - the packet's traversal steps), then 7 nodes per
+ *                                  packet, the nodes its walk visited at steps 256, 512, ...
  * dipole_forward_planned = dipole_forward that also writes the plan.
  * dipole_adjoint_planned = dipole_adjoint that reads the plan of a forward on the
  *   same queries (the order of every training step: primal queries, then their
- *   adjoint, Sec. 6.2) instead of sorting them again, and schedules the
- *   longest packets first.  Results do not depend on the plan; it must come
- *   from dipole_forward_planned with the same q (plan_perm must be a
- *   permutation of [0, q)), and the forward must be complete on `stream` or
- *   ordered before the adjoint.
+ *   adjoint, Sec. 6.2) instead of sorting them again; it cuts every packet's walk
+ *   at the recorded nodes into preorder ranges of about 256 steps and runs the
+ *   ranges longest first (a lane enters a range in the state its depth-first walk
+ *   has there, which the range start's ancestors decide).  Results do not depend on
+ *   the plan: any increasing sequence of cuts partitions the walk; a plan from
+ *   other queries only changes the balance.  It must come from a forward with the
+ *   same q (plan_perm a permutation of [0, q)), complete on `stream` or ordered
+ *   before the adjoint.
  * Same arguments, results and errors as dipole_forward / dipole_adjoint otherwise.
  */
 int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,

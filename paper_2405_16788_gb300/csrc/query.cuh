@@ -46,7 +46,19 @@ struct QueryArgs {
     const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
     uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
     GridSpec grid;           // dense-grid queries instead of q / qperm
+    uint32_t* pcuts;         // forward with a plan: the node of every kCutSteps-th warp step
+    const uint4* items;      // ranged adjoint: work items {packet, lo, hi, steps} (order: porder)
+    const unsigned* n_items; // number of valid items
+    const int32_t* parent;   // node parents (ranged items)
 };
+
+// Query plan layout (per 32-query packet): the sort key 0xffff - steps, then
+// kPlanCuts cut nodes: cut k is the node the packet's warp visited at step
+// (k + 1) * kCutSteps.  Any increasing cut sequence partitions the preorder,
+// so a stale or foreign plan changes only the balance, never a result.
+constexpr unsigned kCutSteps = 256u;
+constexpr unsigned kPlanCuts = 7u;
+constexpr unsigned kPlanWords = 1u + kPlanCuts;
 
 // n attribute values (n = 1, 2 or 4; p aligned to n elements) as floats.
 template <typename AT>

@@ -22,7 +22,11 @@
 namespace dip {
 namespace {
 
-template <int CP, typename AT, int MODE, int KERN>
+// RANGED (adjoint with a plan): each work item is a preorder range [lo, hi)
+// of one packet's walk; a lane enters it in the state its depth-first walk has
+// at lo (decided by lo's ancestors alone) and stops at hi, so the items of a
+// packet together visit exactly the packet's nodes, each once.
+template <int CP, typename AT, int MODE, int KERN, bool RANGED>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
 k_query(const QueryArgs a) {
     constexpr int SR = srow(CP);
@@ -37,8 +41,18 @@ k_query(const QueryArgs a) {
         unsigned long long pk = 0;
         if (lane == 0) pk = atomicAdd(a.work, 1ull);
         pk = __shfl_sync(FULL, pk, 0);
-        if ((int64_t)pk * 32 >= a.nq) break;
-        const int64_t pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
+        int64_t pm;
+        unsigned lo = 0u, hi = nn;
+        if (RANGED) {
+            if (pk >= *a.n_items) break;
+            const uint4 it = a.items[a.porder[pk]];
+            pm = (int64_t)it.x;
+            lo = it.y;
+            hi = it.z;
+        } else {
+            if ((int64_t)pk * 32 >= a.nq) break;
+            pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
+        }
         bool valid;
         int64_t qo;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
@@ -106,11 +120,28 @@ k_query(const QueryArgs a) {
         };
         int n_tested = 0, n_far = 0, n_pts = 0;
 
-        unsigned next = valid ? 0u : nn;
+        unsigned next = valid ? lo : nn;
+        if (RANGED && lo > 0u) {
+            // the walk reaches lo unless an ancestor of lo is far; it then
+            // resumes at the topmost far ancestor's skip, the largest of them
+            const unsigned start = next;
+            int32_t u = a.parent[lo];
+            for (int up = 0; up <= kMaxLevel + 1 && u >= 0; ++up) {
+                const float4 geo = __ldg(&nodes[u].geo);
+                const int4 meta = __ldg(&nodes[u].meta);
+                const float dx = __fsub_rn(x0, geo.x);
+                const float dy = __fsub_rn(x1, geo.y);
+                const float dz = __fsub_rn(x2, geo.z);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const float R = __fmul_rn(a.beta, geo.w);
+                if (start == lo && d2 > __fmul_rn(R, R)) next = max(next, (unsigned)meta.x);
+                u = a.parent[u];
+            }
+        }
         unsigned steps = 0;
         for (;;) {
             const unsigned n = __reduce_min_sync(FULL, next);
-            if (n >= nn) break;
+            if (n >= hi) break;
             if (++steps > nn) {  // a well-formed tree needs at most nn steps
                 if (lane == 0) atomicOr(a.status, kStatusTraversal);
                 break;
@@ -206,12 +237,18 @@ k_query(const QueryArgs a) {
                         }
                     }
                 }
-                if (MODE == kForward && kBlocked && (steps % kFoldSteps) == 0u) {
+                if (MODE == kForward && (steps % kFoldSteps) == 0u) {
+                    if (kBlocked) {
 #pragma unroll
-                    for (int c = 0; c < CP; ++c) {
-                        kahan_add(acc[c], cmp[c], part[c]);
-                        part[c] = 0.f;
+                        for (int c = 0; c < CP; ++c) {
+                            kahan_add(acc[c], cmp[c], part[c]);
+                            part[c] = 0.f;
+                        }
                     }
+                    // plan record: the node of every kCutSteps-th step (a multiple of kFoldSteps)
+                    if (a.pcuts && lane == 0 && (steps & (kCutSteps - 1u)) == 0u &&
+                        steps <= kCutSteps * kPlanCuts)
+                        a.pcuts[(size_t)pm * kPlanCuts + steps / kCutSteps - 1u] = n;
                 }
             }
         }
@@ -235,6 +272,43 @@ k_query(const QueryArgs a) {
     }
 }
 
+// Work items of the ranged adjoint: packet p's walk (steps from its sort key)
+// is cut at its recorded cuts while they increase inside (0, nn); item k of p
+// goes to slot p * kPlanWords + k with the sort key of its estimated steps;
+// unused slots get the largest key and sort last.
+__global__ void k_plan_items(const uint32_t* keys, const uint32_t* cuts, int64_t np, unsigned nn,
+                             uint4* items, uint32_t* ikeys, uint32_t* iidx, unsigned* n_items) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[p];
+        const unsigned steps = key <= 0xffffu ? 0xffffu - key : 0u;
+        unsigned ncut = 0, prev = 0;
+        const unsigned want = min(kPlanCuts, steps / kCutSteps);
+        while (ncut < want) {
+            const unsigned c = cuts[p * kPlanCuts + ncut];
+            if (c <= prev || c >= nn) break;
+            prev = c;
+            ++ncut;
+        }
+        unsigned lo = 0;
+        for (unsigned k = 0; k < kPlanWords; ++k) {
+            const int64_t slot = p * kPlanWords + k;
+            iidx[slot] = (uint32_t)slot;
+            if (k <= ncut) {
+                const unsigned hi = k < ncut ? cuts[p * kPlanCuts + k] : nn;
+                const unsigned est = k < ncut ? kCutSteps : max(1u, steps - ncut * kCutSteps);
+                items[slot] = make_uint4((unsigned)p, lo, hi, est);
+                ikeys[slot] = 0xfffeu - min(est, 0xfffeu);
+                lo = hi;
+            } else {
+                items[slot] = make_uint4((unsigned)p, nn, nn, 0u);
+                ikeys[slot] = 0xffffu;
+            }
+        }
+        atomicAdd(n_items, ncut + 1u);
+    }
+}
+
 __global__ void k_iota(uint32_t* v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -244,19 +318,26 @@ __global__ void k_iota(uint32_t* v, int64_t n) {
 // Packets below this count are too few for the queue's tail to matter.
 constexpr int64_t kOrderMinPackets = 2048;
 
-template <int CP, typename AT, int MODE, int KERN>
+template <int CP, typename AT, int MODE, int KERN, bool RANGED>
 void launch_query_k(const QueryArgs& a, cudaStream_t s) {
     static int per_sm = 0;
-    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN>, a.nq, per_sm);
-    note_launch(); k_query<CP, AT, MODE, KERN><<<grid, kQThreads, 0, s>>>(a);
+    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN, RANGED>, a.nq, per_sm);
+    note_launch(); k_query<CP, AT, MODE, KERN, RANGED><<<grid, kQThreads, 0, s>>>(a);
 }
 
-// The kernel choice is a template parameter: a runtime branch between the two
-// radial factors costs the forward registers.
+// The kernel choice and ranged items are template parameters: runtime
+// branches cost the plain kernels registers.
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
-    if (MODE == kCount || a.kernel == 0) launch_query_k<CP, AT, MODE, 0>(a, s);
-    else launch_query_k<CP, AT, MODE, 1>(a, s);
+    if constexpr (MODE == kAdjoint) {
+        if (a.items) {
+            if (a.kernel == 0) launch_query_k<CP, AT, MODE, 0, true>(a, s);
+            else launch_query_k<CP, AT, MODE, 1, true>(a, s);
+            return;
+        }
+    }
+    if (MODE == kCount || a.kernel == 0) launch_query_k<CP, AT, MODE, 0, false>(a, s);
+    else launch_query_k<CP, AT, MODE, 1, false>(a, s);
 }
 
 template <int MODE>
@@ -368,6 +449,10 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.work = work;
     a.porder = nullptr;  // Morton packet order
     a.pcost = nullptr;
+    a.pcuts = nullptr;
+    a.items = nullptr;
+    a.n_items = nullptr;
+    a.parent = t->parent;
     a.grid = GridSpec{};
     rc = dispatch<kForward>(t, a, s);
     if (rc) return rc;
@@ -409,7 +494,28 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     // order of the packets, never a result.
     const uint32_t* porder = nullptr;
     uint32_t* pcost = nullptr;
-    if (q > 0 && !grid && np >= kOrderMinPackets && mode != kCount) {
+    uint32_t* pcuts = nullptr;
+    uint4* items = nullptr;
+    unsigned* n_items = nullptr;
+    uint32_t *ikeys = nullptr, *iidx = nullptr, *ikt = nullptr, *ivt = nullptr, *ihist = nullptr;
+    if (q > 0 && !grid && np >= kOrderMinPackets && mode == kAdjoint && plan_in && plan_cost) {
+        // ranged items from the plan's walk cuts, longest first
+        const int64_t ni = np * kPlanWords;
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikeys, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&iidx, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikt, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ivt, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ihist, sizeof(uint32_t) * radix_hist_entries(ni), s));
+        DIP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(unsigned), s));
+        note_launch();
+        k_plan_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, plan_cost + np, np,
+                                                                  (unsigned)t->nn, items, ikeys,
+                                                                  iidx, n_items);
+        radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
+        porder = iidx;
+    } else if (q > 0 && !grid && np >= kOrderMinPackets && mode != kCount) {
         if (plan_in && plan_cost) {
             DIP_CUDA_TRY(cudaMemcpyAsync(codes, plan_cost, sizeof(uint32_t) * np,
                                          cudaMemcpyDeviceToDevice, s));
@@ -419,6 +525,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
             porder = ktmp;
         } else if (!plan_in && plan_cost) {
             pcost = plan_cost;
+            if (mode == kForward) pcuts = plan_cost + np;
         }
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
@@ -458,6 +565,10 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.work = work;
         a.porder = porder;
         a.pcost = pcost;
+        a.pcuts = pcuts;
+        a.items = items;
+        a.n_items = n_items;
+        a.parent = t->parent;
         a.grid = GridSpec{};
         if (grid) {
             for (int d = 0; d < 3; ++d) {
@@ -479,6 +590,10 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     if (rc == 0 && mode == kAdjointGeom)
         rc = stage2_geom(t, call.grad_n, call.grad_eps, call.accumulate, s);
     cudaFreeAsync(work, s);
+    if (items) {
+        cudaFreeAsync(items, s); cudaFreeAsync(n_items, s); cudaFreeAsync(ikeys, s);
+        cudaFreeAsync(iidx, s); cudaFreeAsync(ikt, s); cudaFreeAsync(ivt, s); cudaFreeAsync(ihist, s);
+    }
     if (codes) {
         cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);
         cudaFreeAsync(hist, s);

@@ -205,14 +205,18 @@ def dipole_adjoint(tree: int, queries: torch.Tensor, beta: float, grad_out: torc
 
 
 class QueryPlan:
-    """Caller-owned query plan: the Morton order of a query batch and each
-    32-query packet's traversal steps, written by dipole_forward_planned and
-    read by dipole_adjoint_planned on the same queries."""
+    """Caller-owned query plan: the Morton order of a query batch and a record
+    of each 32-query packet's walk (its steps and the nodes where it passed
+    every 256th step), written by the forward (dipole_forward_planned,
+    dipole_forward_grad) and read by the adjoint on the same queries."""
+
+    WORDS_PER_PACKET = 8
 
     def __init__(self, q: int, device):
         self.q = int(q)
+        npk = max((self.q + 31) // 32, 1)
         self.perm = torch.empty(max(self.q, 1), dtype=torch.int32, device=device)
-        self.cost = torch.empty(max((self.q + 31) // 32, 1), dtype=torch.int32, device=device)
+        self.cost = torch.empty(npk * self.WORDS_PER_PACKET, dtype=torch.int32, device=device)
 
 
 def dipole_forward_planned(tree: int, queries: torch.Tensor, beta: float, out: torch.Tensor,

@@ -224,3 +224,28 @@ def test_planned_forward_and_adjoint_match_unplanned():
     ap2 = gt.adjoint(q, 2.0, g, plan=plan).cpu().numpy()
     assert np.all(normwise(ap2, a) <= 1e-5)
     gt.sync_status()
+
+
+def test_planned_adjoint_with_any_plan_record_is_correct():
+    """The adjoint cuts each packet's walk at the plan's recorded nodes; any
+    record (here random words: non-increasing cuts, out-of-range nodes, keys
+    of any size) only changes how the work is divided, never the result."""
+    import torch
+    from paper_2405_16788_gb300 import dipole
+    w = syn.workload("scene-200k", scale=0.3)
+    nq = 120000
+    q = to_dev(w.queries[:nq])
+    g = to_dev(syn.upstream_grad(nq, 4, seed=13))
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    ref = gt.adjoint(q, 2.0, g).cpu().numpy()
+    plan = dipole.QueryPlan(nq, q.device)
+    gt.forward(q, 2.0, plan=plan)  # a valid permutation
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    nn = gt.info["n_nodes"]
+    for lo, hi in [(0, 2 ** 31 - 1), (0, nn), (0, 4000)]:
+        plan.cost.copy_(torch.randint(lo, hi, plan.cost.shape, generator=gen, device="cuda",
+                                      dtype=torch.int64).to(torch.int32))
+        got = gt.adjoint(q, 2.0, g, plan=plan).cpu().numpy()
+        assert np.all(normwise(got, ref) <= 1e-5), normwise(got, ref)
+    gt.sync_status()
