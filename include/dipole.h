@@ -200,21 +200,24 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
  * Forward and adjoint sharing a query plan (caller-owned device buffers):
  *   plan_perm [q]                  uint32, written by dipole_forward_planned: the Morton
  *                                  order of the queries (a permutation of [0, q))
- *   plan_cost [8 * ceil(q / 32)]   uint32, written by dipole_forward_planned: a record of
- *                                  every 32-query packet's walk: first ceil(q/32) sort keys
- *                                  (0xffff - the packet's traversal steps), then 7 nodes per
- *                                  packet, the nodes its walk visited at steps 256, 512, ...
- * dipole_forward_planned = dipole_forward that also writes the plan.
+ *   plan_cost [8 * ceil(q / 32)]   uint32, written by dipole_forward_planned: 8 words per
+ *                                  32-query packet: its traversal steps, the nodes its walk
+ *                                  visited at steps 256, 512, 768 of its lower part, the node
+ *                                  where the walk was split in two, and the same three for its
+ *                                  upper part (0 = none)
+ * dipole_forward_planned = dipole_forward that also writes the plan.  (Every forward
+ *   of 65,536 queries or more walks each packet as two preorder ranges run by two
+ *   warps, cut at the leaf holding the middle point of the packet's code range: a
+ *   lane enters a range in the state its depth-first walk has there, which the range
+ *   start's ancestors decide.)
  * dipole_adjoint_planned = dipole_adjoint that reads the plan of a forward on the
  *   same queries (the order of every training step: primal queries, then their
- *   adjoint, Sec. 6.2) instead of sorting them again; it cuts every packet's walk
- *   at the recorded nodes into preorder ranges of about 256 steps and runs the
- *   ranges longest first (a lane enters a range in the state its depth-first walk
- *   has there, which the range start's ancestors decide).  Results do not depend on
- *   the plan: any increasing sequence of cuts partitions the walk; a plan from
- *   other queries only changes the balance.  It must come from a forward with the
- *   same q (plan_perm a permutation of [0, q)), complete on `stream` or ordered
- *   before the adjoint.
+ *   adjoint, Sec. 6.2) instead of sorting them again; it cuts every packet's walk at
+ *   the recorded nodes into preorder ranges of about 256 steps and runs the ranges
+ *   longest first.  Results do not depend on the plan: any increasing sequence of
+ *   cuts partitions the walk; a plan from other queries only changes the balance.  It
+ *   must come from a forward with the same q (plan_perm a permutation of [0, q)),
+ *   complete on `stream` or ordered before the adjoint.
  * Same arguments, results and errors as dipole_forward / dipole_adjoint otherwise.
  */
 int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,

@@ -43,22 +43,23 @@ struct QueryArgs {
     float* dgeo;        // [n, 4] opened-leaf normal (xyz) and radius (w) terms (kAdjointGeom)
     int32_t* counts;
     unsigned long long* work;
-    const uint32_t* porder;  // packet order (longest first), or NULL for Morton order
-    uint32_t* pcost;         // if set: per-packet warp steps (Morton packet index), for scheduling
+    const uint32_t* porder;  // packet (or item) order, or NULL for Morton order
     GridSpec grid;           // dense-grid queries instead of q / qperm
-    uint32_t* pcuts;         // forward with a plan: the node of every kCutSteps-th warp step
-    const uint4* items;      // ranged adjoint: work items {packet, lo, hi, steps} (order: porder)
+    uint32_t* plan;          // query plan being written (forward): kPlanWords per packet
+    const uint4* items;      // ranged work items {packet, lo, hi, part}, read in porder if set
     const unsigned* n_items; // number of valid items
     const int32_t* parent;   // node parents (ranged items)
 };
 
-// Query plan layout (per 32-query packet): the sort key 0xffff - steps, then
-// kPlanCuts cut nodes: cut k is the node the packet's warp visited at step
-// (k + 1) * kCutSteps.  Any increasing cut sequence partitions the preorder,
-// so a stale or foreign plan changes only the balance, never a result.
+// Query plan, kPlanWords words per 32-query packet: [0] the packet's warp
+// steps (all its items together); [1..3] the nodes its lower forward item
+// visited at its steps 256, 512, 768; [4] the node where the forward split
+// the walk; [5..7] the same as [1..3] for the upper item (0 = none).  Any
+// increasing subsequence of [1..7] inside (0, nn) partitions the walk, so a
+// stale or foreign plan changes only the balance of an adjoint, never a result.
 constexpr unsigned kCutSteps = 256u;
-constexpr unsigned kPlanCuts = 7u;
-constexpr unsigned kPlanWords = 1u + kPlanCuts;
+constexpr unsigned kPartCuts = 3u;
+constexpr unsigned kPlanWords = 8u;
 
 // n attribute values (n = 1, 2 or 4; p aligned to n elements) as floats.
 template <typename AT>

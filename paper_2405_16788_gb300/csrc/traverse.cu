@@ -22,10 +22,13 @@
 namespace dip {
 namespace {
 
-// RANGED (adjoint with a plan): each work item is a preorder range [lo, hi)
-// of one packet's walk; a lane enters it in the state its depth-first walk has
-// at lo (decided by lo's ancestors alone) and stops at hi, so the items of a
-// packet together visit exactly the packet's nodes, each once.
+// RANGED: each work item is a preorder range [lo, hi) of one packet's walk; a
+// lane enters it in the state its depth-first walk has at lo (decided by lo's
+// ancestors alone) and stops at hi, so the items of a packet together visit
+// exactly the packet's nodes, each once.  The forward splits every packet in
+// two (k_fwd_items) and its two parts add into the zeroed output (a sum of two
+// floats does not depend on their order); the adjoint with a plan cuts every
+// walk at the nodes the forward recorded (k_plan_items).
 template <int CP, typename AT, int MODE, int KERN, bool RANGED>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
 k_query(const QueryArgs a) {
@@ -43,12 +46,14 @@ k_query(const QueryArgs a) {
         pk = __shfl_sync(FULL, pk, 0);
         int64_t pm;
         unsigned lo = 0u, hi = nn;
+        unsigned half = 0u;  // forward item: 0 lower, 1 upper part of the walk
         if (RANGED) {
             if (pk >= *a.n_items) break;
-            const uint4 it = a.items[a.porder[pk]];
+            const uint4 it = a.items[a.porder ? a.porder[pk] : pk];
             pm = (int64_t)it.x;
             lo = it.y;
             hi = it.z;
+            half = it.w;
         } else {
             if ((int64_t)pk * 32 >= a.nq) break;
             pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
@@ -121,7 +126,7 @@ k_query(const QueryArgs a) {
         int n_tested = 0, n_far = 0, n_pts = 0;
 
         unsigned next = valid ? lo : nn;
-        if (RANGED && lo > 0u) {
+        if (RANGED && lo > 0u && lo < nn) {
             // the walk reaches lo unless an ancestor of lo is far; it then
             // resumes at the topmost far ancestor's skip, the largest of them
             const unsigned start = next;
@@ -245,10 +250,10 @@ k_query(const QueryArgs a) {
                             part[c] = 0.f;
                         }
                     }
-                    // plan record: the node of every kCutSteps-th step (a multiple of kFoldSteps)
-                    if (a.pcuts && lane == 0 && (steps & (kCutSteps - 1u)) == 0u &&
-                        steps <= kCutSteps * kPlanCuts)
-                        a.pcuts[(size_t)pm * kPlanCuts + steps / kCutSteps - 1u] = n;
+                    // plan record: the node of every kCutSteps-th step of this part
+                    if (RANGED && a.plan && lane == 0 && (steps & (kCutSteps - 1u)) == 0u &&
+                        steps <= kCutSteps * kPartCuts)
+                        a.plan[(size_t)pm * kPlanWords + 1u + 4u * half + steps / kCutSteps - 1u] = n;
                 }
             }
         }
@@ -257,12 +262,17 @@ k_query(const QueryArgs a) {
             for (int c = 0; c < CP; ++c) kahan_add(acc[c], cmp[c], part[c]);
         }
 
-        if (a.pcost && lane == 0) a.pcost[pm] = 0xffffu - (steps < 0xffffu ? steps : 0xffffu);
+        if (RANGED && MODE == kForward && a.plan && lane == 0)
+            atomicAdd(a.plan + (size_t)pm * kPlanWords, steps);
         if (valid) {
             if (MODE == kForward) {
 #pragma unroll
-                for (int c = 0; c < CP; ++c)
-                    if (c < a.C) a.out[qo * a.C + c] = __fsub_rn(acc[c], cmp[c]) * kInv4Pi;
+                for (int c = 0; c < CP; ++c) {
+                    if (c >= a.C) continue;
+                    const float v = __fsub_rn(acc[c], cmp[c]) * kInv4Pi;
+                    if (RANGED) atomicAdd(a.out + qo * a.C + c, v);  // the two parts of a packet
+                    else a.out[qo * a.C + c] = v;
+                }
             } else if (MODE == kCount) {
                 a.counts[3 * qo] = n_tested;
                 a.counts[3 * qo + 1] = n_far;
@@ -272,32 +282,33 @@ k_query(const QueryArgs a) {
     }
 }
 
-// Work items of the ranged adjoint: packet p's walk (steps from its sort key)
-// is cut at its recorded cuts while they increase inside (0, nn); item k of p
-// goes to slot p * kPlanWords + k with the sort key of its estimated steps;
-// unused slots get the largest key and sort last.
-__global__ void k_plan_items(const uint32_t* keys, const uint32_t* cuts, int64_t np, unsigned nn,
-                             uint4* items, uint32_t* ikeys, uint32_t* iidx, unsigned* n_items) {
+// Work items of the ranged adjoint: packet p's walk is cut at the increasing
+// nodes of plan words [1..7] inside (0, nn); item k of p goes to slot
+// p * kPlanWords + k with the sort key of its estimated steps (the packet's
+// steps shared evenly); unused slots get the largest key and sort last.
+__global__ void k_plan_items(const uint32_t* plan, int64_t np, unsigned nn, uint4* items,
+                             uint32_t* ikeys, uint32_t* iidx, unsigned* n_items) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t key = keys[p];
-        const unsigned steps = key <= 0xffffu ? 0xffffu - key : 0u;
+        const uint32_t* w = plan + p * kPlanWords;
+        unsigned cut[kPlanWords - 1];
         unsigned ncut = 0, prev = 0;
-        const unsigned want = min(kPlanCuts, steps / kCutSteps);
-        while (ncut < want) {
-            const unsigned c = cuts[p * kPlanCuts + ncut];
-            if (c <= prev || c >= nn) break;
-            prev = c;
-            ++ncut;
+        for (unsigned k = 1; k < kPlanWords; ++k) {
+            const unsigned c = w[k];
+            if (c > prev && c < nn) {
+                cut[ncut++] = c;
+                prev = c;
+            }
         }
+        const unsigned steps = min(w[0], 0xfff0u);
+        const unsigned est = max(1u, steps / (ncut + 1u));
         unsigned lo = 0;
         for (unsigned k = 0; k < kPlanWords; ++k) {
             const int64_t slot = p * kPlanWords + k;
             iidx[slot] = (uint32_t)slot;
             if (k <= ncut) {
-                const unsigned hi = k < ncut ? cuts[p * kPlanCuts + k] : nn;
-                const unsigned est = k < ncut ? kCutSteps : max(1u, steps - ncut * kCutSteps);
-                items[slot] = make_uint4((unsigned)p, lo, hi, est);
+                const unsigned hi = k < ncut ? cut[k] : nn;
+                items[slot] = make_uint4((unsigned)p, lo, hi, 0u);
                 ikeys[slot] = 0xfffeu - min(est, 0xfffeu);
                 lo = hi;
             } else {
@@ -309,10 +320,47 @@ __global__ void k_plan_items(const uint32_t* keys, const uint32_t* cuts, int64_t
     }
 }
 
-__global__ void k_iota(uint32_t* v, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = (uint32_t)i;
+// Sort keys (longest first) and indices of packets from the plan's steps.
+__global__ void k_cost_keys(const uint32_t* plan, uint32_t* keys, uint32_t* idx, int64_t np) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        keys[p] = 0xffffu - min(plan[p * kPlanWords], 0xffffu);
+        idx[p] = (uint32_t)p;
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n, uint32_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The forward's two items per packet: the walk is cut at the leaf holding the
+// middle point (Morton order) of those whose codes fall in the packet's code
+// range, which puts about half of a packet's near-field work on each side.
+// The cut is also written to the plan (word 4) when one is recorded.
+__global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int key_shift,
+                            const uint32_t* pcode, int64_t n, const int32_t* leaf_of, unsigned nn,
+                            uint4* items, unsigned* n_items, uint32_t* plan) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t first = p * 32, last = min(q, first + 32) - 1;
+        const uint32_t cmin = qkeys[first] << key_shift;
+        const uint32_t cmax = ((qkeys[last] + 1u) << key_shift) - 1u;
+        const int64_t ilo = lower_bound_u32(pcode, n, cmin);
+        const int64_t ihi = lower_bound_u32(pcode, n, cmax + 1u);
+        const int64_t imid = min((ilo + ihi) / 2, n - 1);
+        unsigned cut = (unsigned)leaf_of[imid];
+        if (cut == 0u || cut >= nn) cut = nn;  // one item holds the whole walk
+        items[2 * p] = make_uint4((unsigned)p, 0u, cut, 0u);
+        items[2 * p + 1] = make_uint4((unsigned)p, cut, nn, 1u);
+        if (plan) plan[p * kPlanWords + 4] = cut < nn ? cut : 0u;
+        if (p == 0) *n_items = (unsigned)(2 * np);
+    }
 }
 
 // Packets below this count are too few for the queue's tail to matter.
@@ -329,7 +377,7 @@ void launch_query_k(const QueryArgs& a, cudaStream_t s) {
 // branches cost the plain kernels registers.
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
-    if constexpr (MODE == kAdjoint) {
+    if constexpr (MODE == kAdjoint || MODE == kForward) {
         if (a.items) {
             if (a.kernel == 0) launch_query_k<CP, AT, MODE, 0, true>(a, s);
             else launch_query_k<CP, AT, MODE, 1, true>(a, s);
@@ -448,8 +496,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.counts = nullptr;
     a.work = work;
     a.porder = nullptr;  // Morton packet order
-    a.pcost = nullptr;
-    a.pcuts = nullptr;
+    a.plan = nullptr;
     a.items = nullptr;
     a.n_items = nullptr;
     a.parent = t->parent;
@@ -493,13 +540,13 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     // packets longest first from those records.  The record only changes the
     // order of the packets, never a result.
     const uint32_t* porder = nullptr;
-    uint32_t* pcost = nullptr;
-    uint32_t* pcuts = nullptr;
+    uint32_t* plan_w = nullptr;  // the plan this forward records
     uint4* items = nullptr;
     unsigned* n_items = nullptr;
     uint32_t *ikeys = nullptr, *iidx = nullptr, *ikt = nullptr, *ivt = nullptr, *ihist = nullptr;
-    if (q > 0 && !grid && np >= kOrderMinPackets && mode == kAdjoint && plan_in && plan_cost) {
-        // ranged items from the plan's walk cuts, longest first
+    const bool big = q > 0 && !grid && np >= kOrderMinPackets;
+    if (big && mode == kAdjoint && plan_in && plan_cost) {
+        // ranged items from the walk cuts recorded by the forward, longest first
         const int64_t ni = np * kPlanWords;
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
@@ -510,23 +557,30 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         DIP_CUDA_TRY(cudaMallocAsync((void**)&ihist, sizeof(uint32_t) * radix_hist_entries(ni), s));
         DIP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(unsigned), s));
         note_launch();
-        k_plan_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, plan_cost + np, np,
-                                                                  (unsigned)t->nn, items, ikeys,
-                                                                  iidx, n_items);
+        k_plan_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, np, (unsigned)t->nn,
+                                                                  items, ikeys, iidx, n_items);
         radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
         porder = iidx;
-    } else if (q > 0 && !grid && np >= kOrderMinPackets && mode != kCount) {
-        if (plan_in && plan_cost) {
-            DIP_CUDA_TRY(cudaMemcpyAsync(codes, plan_cost, sizeof(uint32_t) * np,
-                                         cudaMemcpyDeviceToDevice, s));
-            note_launch();
-            k_iota<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(ktmp, np);
-            radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
-            porder = ktmp;
-        } else if (!plan_in && plan_cost) {
-            pcost = plan_cost;
-            if (mode == kForward) pcuts = plan_cost + np;
-        }
+    } else if (big && plan_in && plan_cost && mode != kCount) {
+        // the gradient adjoints: whole packets, longest first
+        note_launch();
+        k_cost_keys<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, codes, ktmp, np);
+        radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
+        porder = ktmp;
+    }
+    if (big && !plan_in && plan_cost && (mode == kForward || mode == kForwardGrad)) {
+        plan_w = plan_cost;  // items add their steps and record their cuts
+        DIP_CUDA_TRY(cudaMemsetAsync(plan_w, 0, sizeof(uint32_t) * kPlanWords * (size_t)np, s));
+    }
+    if (big && mode == kForward) {
+        // every packet's walk in two ranged items, adding into the zeroed output
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * 2 * np, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
+        DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
+        note_launch();
+        k_fwd_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
+            codes, q, np, 30 - kQueryKeyBits, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
+            n_items, plan_w);
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (adjoint) {
@@ -564,8 +618,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.counts = call.counts;
         a.work = work;
         a.porder = porder;
-        a.pcost = pcost;
-        a.pcuts = pcuts;
+        a.plan = plan_w;
         a.items = items;
         a.n_items = n_items;
         a.parent = t->parent;
@@ -591,8 +644,12 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         rc = stage2_geom(t, call.grad_n, call.grad_eps, call.accumulate, s);
     cudaFreeAsync(work, s);
     if (items) {
-        cudaFreeAsync(items, s); cudaFreeAsync(n_items, s); cudaFreeAsync(ikeys, s);
-        cudaFreeAsync(iidx, s); cudaFreeAsync(ikt, s); cudaFreeAsync(ivt, s); cudaFreeAsync(ihist, s);
+        cudaFreeAsync(items, s);
+        cudaFreeAsync(n_items, s);
+    }
+    if (ikeys) {
+        cudaFreeAsync(ikeys, s); cudaFreeAsync(iidx, s); cudaFreeAsync(ikt, s); cudaFreeAsync(ivt, s);
+        cudaFreeAsync(ihist, s);
     }
     if (codes) {
         cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);

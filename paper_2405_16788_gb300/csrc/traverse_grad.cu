@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                 }
             }
         }
-        if (a.pcost && lane == 0) a.pcost[pm] = 0xffffu - (steps < 0xffffu ? steps : 0xffffu);
+        if (a.plan && lane == 0) atomicAdd(a.plan + (size_t)pm * kPlanWords, steps);
     }
 }
 
