@@ -320,15 +320,6 @@ __global__ void k_plan_items(const uint32_t* plan, int64_t np, unsigned nn, uint
     }
 }
 
-// Sort keys (longest first) and indices of packets from the plan's steps.
-__global__ void k_cost_keys(const uint32_t* plan, uint32_t* keys, uint32_t* idx, int64_t np) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        keys[p] = 0xffffu - min(plan[p * kPlanWords], 0xffffu);
-        idx[p] = (uint32_t)p;
-    }
-}
-
 __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n, uint32_t x) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -545,7 +536,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     unsigned* n_items = nullptr;
     uint32_t *ikeys = nullptr, *iidx = nullptr, *ikt = nullptr, *ivt = nullptr, *ihist = nullptr;
     const bool big = q > 0 && !grid && np >= kOrderMinPackets;
-    if (big && mode == kAdjoint && plan_in && plan_cost) {
+    if (big && (mode == kAdjoint || mode == kAdjointGrad || mode == kAdjointGeom) && plan_in &&
+        plan_cost) {
         // ranged items from the walk cuts recorded by the forward, longest first
         const int64_t ni = np * kPlanWords;
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
@@ -561,22 +553,18 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
                                                                   items, ikeys, iidx, n_items);
         radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
         porder = iidx;
-    } else if (big && plan_in && plan_cost && mode != kCount) {
-        // the gradient adjoints: whole packets, longest first
-        note_launch();
-        k_cost_keys<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, codes, ktmp, np);
-        radix_sort_pairs(codes, ktmp, vtmp, vtmp + np, hist, np, 16, s);
-        porder = ktmp;
     }
     if (big && !plan_in && plan_cost && (mode == kForward || mode == kForwardGrad)) {
         plan_w = plan_cost;  // items add their steps and record their cuts
         DIP_CUDA_TRY(cudaMemsetAsync(plan_w, 0, sizeof(uint32_t) * kPlanWords * (size_t)np, s));
     }
-    if (big && mode == kForward) {
-        // every packet's walk in two ranged items, adding into the zeroed output
+    if (big && (mode == kForward || mode == kForwardGrad)) {
+        // every packet's walk in two ranged items, adding into the zeroed outputs
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * 2 * np, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
-        DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
+        if (call.out) DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
+        if (call.gout)
+            DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
         note_launch();
         k_fwd_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
             codes, q, np, 30 - kQueryKeyBits, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,

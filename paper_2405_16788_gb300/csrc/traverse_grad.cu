@@ -156,7 +156,10 @@ __device__ __forceinline__ void desing_factors(float d2, float inv_eps, float& a
 // Three resident blocks for the forward and the normal/radius adjoint (80
 // registers, a few spilled bytes: -10% and -9% against two blocks at 100 and
 // 109 registers); two for the gradient adjoint (72 registers fit three anyway).
-template <int CG, typename AT, int MODE>
+// RANGED: work items are preorder ranges of a packet's walk, as in the value
+// traversal (two per packet in the forward, the plan's cuts in the adjoints);
+// the same range holds for every channel group, whose walks are identical.
+template <int CG, typename AT, int MODE, bool RANGED>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kAdjointGeom) ? 3 : 2)
     k_query_grad(const QueryArgs a) {
     static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
@@ -176,8 +179,19 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
         unsigned long long pk = 0;
         if (lane == 0) pk = atomicAdd(a.work, 1ull);
         pk = __shfl_sync(FULL, pk, 0);
-        if ((int64_t)pk * 32 >= a.nq) break;
-        const int64_t pm = (int64_t)(a.porder ? a.porder[pk] : pk);
+        int64_t pm;
+        unsigned lo = 0u, hi = nn, half = 0u;
+        if (RANGED) {
+            if (pk >= *a.n_items) break;
+            const uint4 it = a.items[a.porder ? a.porder[pk] : pk];
+            pm = (int64_t)it.x;
+            lo = it.y;
+            hi = it.z;
+            half = it.w;
+        } else {
+            if ((int64_t)pk * 32 >= a.nq) break;
+            pm = (int64_t)(a.porder ? a.porder[pk] : pk);
+        }
         const int64_t qi = pm * 32 + lane;
         const bool valid = qi < a.nq;
         const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
@@ -233,11 +247,28 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                 }
             }
 
-            unsigned next = valid ? 0u : nn;
+            unsigned next = valid ? lo : nn;
+            if (RANGED && lo > 0u && lo < nn) {
+                // the walk reaches lo unless an ancestor of lo is far; it then resumes
+                // at the topmost far ancestor's skip, the largest of them
+                const unsigned start = next;
+                int32_t u = a.parent[lo];
+                for (int up = 0; up <= kMaxLevel + 1 && u >= 0; ++up) {
+                    const float4 geo = __ldg(&nodes[u].geo);
+                    const int4 meta = __ldg(&nodes[u].meta);
+                    const float dx = __fsub_rn(x0, geo.x);
+                    const float dy = __fsub_rn(x1, geo.y);
+                    const float dz = __fsub_rn(x2, geo.z);
+                    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                    const float R = __fmul_rn(a.beta, geo.w);
+                    if (start == lo && d2 > __fmul_rn(R, R)) next = max(next, (unsigned)meta.x);
+                    u = a.parent[u];
+                }
+            }
             unsigned gsteps = 0;
             for (;;) {
                 const unsigned n = __reduce_min_sync(FULL, next);
-                if (n >= nn) break;
+                if (n >= hi) break;
                 if (++gsteps > nn) {  // a well-formed tree needs at most nn steps
                     if (lane == 0) atomicOr(a.status, kStatusTraversal);
                     break;
@@ -401,6 +432,10 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                         kahan_add(acc[i], cmp[i], part[i]);
                         part[i] = 0.f;
                     }
+                    // plan record (first channel group): nodes of this part's steps 256, 512, 768
+                    if (RANGED && a.plan && c0 == 0 && lane == 0 && (gsteps & (kCutSteps - 1u)) == 0u &&
+                        gsteps <= kCutSteps * kPartCuts)
+                        a.plan[(size_t)pm * kPlanWords + 1u + 4u * half + gsteps / kCutSteps - 1u] = n;
                 }
             }
             steps += gsteps;
@@ -412,10 +447,18 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                     for (int c = 0; c < CG; ++c) {
                         if (c0 + c >= a.C) continue;
                         const int64_t o = qo * a.C + c0 + c;
-                        if (a.out) a.out[o] = __fsub_rn(acc[4 * c], cmp[4 * c]) * kInv4Pi;
+                        // ranged: the two parts of a packet add into the zeroed outputs
+                        const float d = __fsub_rn(acc[4 * c], cmp[4 * c]) * kInv4Pi;
+                        if (a.out) {
+                            if (RANGED) atomicAdd(a.out + o, d);
+                            else a.out[o] = d;
+                        }
 #pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            a.gout[3 * o + k] = __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi;
+                        for (int k = 0; k < 3; ++k) {
+                            const float v = __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi;
+                            if (RANGED) atomicAdd(a.gout + 3 * o + k, v);
+                            else a.gout[3 * o + k] = v;
+                        }
                     }
                 }
             }
@@ -424,11 +467,17 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
     }
 }
 
+template <int CG, typename AT, int MODE, bool RANGED>
+void launch_grad_r(const QueryArgs& a, cudaStream_t s) {
+    static int per_sm = 0;
+    const unsigned grid = query_grid(k_query_grad<CG, AT, MODE, RANGED>, a.nq, per_sm);
+    note_launch(); k_query_grad<CG, AT, MODE, RANGED><<<grid, kQThreads, 0, s>>>(a);
+}
+
 template <int CG, typename AT, int MODE>
 void launch_grad(const QueryArgs& a, cudaStream_t s) {
-    static int per_sm = 0;
-    const unsigned grid = query_grid(k_query_grad<CG, AT, MODE>, a.nq, per_sm);
-    note_launch(); k_query_grad<CG, AT, MODE><<<grid, kQThreads, 0, s>>>(a);
+    if (a.items) launch_grad_r<CG, AT, MODE, true>(a, s);
+    else launch_grad_r<CG, AT, MODE, false>(a, s);
 }
 
 template <int CG, int MODE>
