@@ -32,8 +32,9 @@
  *       geometry with the fixed operation order below, so that a CPU and a GPU
  *       implementation take identical decisions.  All values are double.
  *   R7  Node sums (area, area-weighted position, area-weighted eps) are formed
- *       in double, point by point inside a leaf and child by child inside an
- *       internal node, both in Morton order.  The ratios are taken as the sums
+ *       in float inside a leaf, point by point in Morton order with every
+ *       product and sum rounded to float, and in double inside an internal
+ *       node, child by child in Morton order from its children's sums.  The ratios are taken as the sums
  *       times the correctly rounded reciprocal of the area; the node centroid
  *       is that product rounded to float; the node radius is the largest float
  *       distance from that float centroid to a point of the node.
@@ -438,14 +439,17 @@ static void build_node(orc_tree* T, int64_t a, int64_t b, int level, int32_t par
 static void node_sums(orc_tree* T, int32_t t) {
     double sa = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, se = 0.0;
     if (T->is_leaf[t]) {
+        /* R7: float sums inside a leaf (no fused multiply-add: -ffp-contract=off) */
+        float fa = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f, fe = 0.0f;
         for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m) {
-            double A = T->A[m];
-            sa += A;
-            sx += A * (double)T->p[3 * m];
-            sy += A * (double)T->p[3 * m + 1];
-            sz += A * (double)T->p[3 * m + 2];
-            se += A * (double)T->eps[m];
+            float A = T->A[m];
+            fa = fa + A;
+            fx = fx + A * T->p[3 * m];
+            fy = fy + A * T->p[3 * m + 1];
+            fz = fz + A * T->p[3 * m + 2];
+            fe = fe + A * T->eps[m];
         }
+        sa = fa; sx = fx; sy = fy; sz = fz; se = fe;
     } else {
         for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c]) {
             node_sums(T, c);

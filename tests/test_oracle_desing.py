@@ -45,9 +45,9 @@ def test_bh_equals_brute_when_nothing_is_far():
     with oracle.kernel("desingularized"):
         T = oracle.Tree(c.points, c.normals, c.areas, c.eps)
         T.update(w.mu)
-        a = T.forward(w.queries, 1e30)
+        a = T.forward(w.queries, np.inf)
         b = oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
-        ga = T.forward_grad(w.queries, 1e30)
+        ga = T.forward_grad(w.queries, np.inf)
         gb = oracle.brute_forward_grad(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
     assert np.allclose(a, b, rtol=1e-11, atol=1e-13)
     assert np.allclose(ga, gb, rtol=1e-11, atol=1e-13)

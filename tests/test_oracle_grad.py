@@ -100,7 +100,7 @@ def test_bh_gradient_equals_brute_when_nothing_is_far():
     c = w.cloud
     T = oracle.Tree(c.points, c.normals, c.areas, c.eps)
     T.update(w.mu)
-    a = T.forward_grad(w.queries, 1e30)
+    a = T.forward_grad(w.queries, np.inf)
     b = oracle.brute_forward_grad(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
     assert np.allclose(a, b, rtol=1e-11, atol=1e-13)
 

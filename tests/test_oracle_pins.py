@@ -206,7 +206,7 @@ def test_bh_equals_brute_force_when_nothing_is_far():
     c = w.cloud
     T = oracle.Tree(c.points, c.normals, c.areas, c.eps)
     T.update(w.mu)
-    bh = T.forward(w.queries, 1e30)
+    bh = T.forward(w.queries, np.inf)
     bf = oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
     assert np.allclose(bh, bf, rtol=1e-12, atol=1e-14)
 
@@ -214,8 +214,9 @@ def test_bh_equals_brute_force_when_nothing_is_far():
 def test_bh_single_point_leaves_far_field_is_exact_per_point():
     """With single-point leaves (the paper's tree, Sec. 6.1) a leaf has radius 0,
     so it is always far and its far field (eq. farfield) is that point's exact
-    term: a two-point cloud with leaf size 1, queried inside beta times the
-    root radius, reproduces brute force."""
+    term, up to the float rounding of the leaf's sums (reading R7): a two-point
+    cloud with leaf size 1, queried inside beta times the root radius,
+    reproduces brute force."""
     p = np.array([[0.0, 0, 0], [0.3, 0.1, -0.2]], np.float32)
     n = np.array([[0, 0, 1.0], [0.6, 0.8, 0]], np.float32)
     a = np.array([0.2, 0.5], np.float32)
@@ -228,7 +229,7 @@ def test_bh_single_point_leaves_far_field_is_exact_per_point():
     bh, cnt = T.forward(q, 2.0, counters=True)
     bf = oracle.brute_forward(p, n, a, e, mu, q)
     assert np.all(cnt[:, 1] == 2)
-    assert np.allclose(bh, bf, rtol=1e-13, atol=1e-15)
+    assert np.allclose(bh, bf, rtol=1e-6, atol=1e-12)
 
 
 def test_bh_error_shrinks_with_beta():
@@ -309,7 +310,7 @@ def test_bh_adjoint_equals_brute_adjoint_when_nothing_is_far():
     T = oracle.Tree(c.points, c.normals, c.areas, c.eps)
     T.update(w.mu)
     g = syn.upstream_grad(len(w.queries), 1, seed=9)
-    a = T.adjoint(w.queries, 1e30, g)
+    a = T.adjoint(w.queries, np.inf, g)
     b = oracle.brute_adjoint(c.points, c.normals, c.areas, c.eps, w.queries, g)
     assert np.allclose(a, b, rtol=1e-11, atol=1e-14)
 
@@ -343,9 +344,10 @@ def test_node_moments_follow_definition():
     e = T.export()
     A = c.areas.astype(np.float64)
     P = c.points.astype(np.float64)
-    assert abs(e["area"][0] - A.sum()) < 1e-12 * A.sum()
+    # leaves sum in float (reading R7): a few float roundings of the exact sums
+    assert abs(e["area"][0] - A.sum()) < 1e-6 * A.sum()
     cen = (A[:, None] * P).sum(0) / A.sum()
-    assert np.allclose(e["cen"][0], cen, rtol=0, atol=1e-12)
+    assert np.allclose(e["cen"][0], cen, rtol=0, atol=2e-6)
     rmax = np.max(np.linalg.norm(P - e["cen32"][0].astype(np.float64), axis=1))
     assert abs(e["r32"][0] - rmax) <= 2e-7 * rmax
     far = (np.array([[40.0, -25.0, 31.0]]) * np.array([[1.0], [3.0], [9.0]])).astype(np.float32)
