@@ -56,9 +56,10 @@ typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
 /* Radial factor of the kernel.  REGULARIZED is the paper's method:
  * rho(r/eps)/r^3 with rho of eq. regularized_poisson (Sec. 4.1).
  * DESINGULARIZED is the ablation baseline the paper compares against
- * (Sec. 4.1 footnote; Sec. 7 ablation), which bounds the kernel's denominator
- * away from zero; read as 1/max(r, eps)^3 with the point's radius eps as the cutoff (eps~ at
- * a far node); eps = 0 gives the singular kernel in both. */
+ * (Sec. 4.1 footnote; Sec. 7 ablation), which bounds the kernel's
+ * denominator away from zero; read as 1/max(r, eps)^3 with the point's radius
+ * eps as the cutoff (eps~ at a far node); eps = 0 gives the singular kernel in
+ * both. */
 typedef enum { DIPOLE_KERNEL_REGULARIZED = 0, DIPOLE_KERNEL_DESINGULARIZED = 1 } dipole_kernel;
 
 /* Octree parameters.  leaf_size in [1, 64] (the paper's leaves are single
@@ -159,7 +160,8 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
  * buffers and work counter per call; this variant takes them from a
  * file-scope device array instead.
  *
- *   Same arguments, results and errors as dipole_forward, and additionally
+ *   Same arguments, results (up to float rounding: each packet's walk runs in
+ *   one piece here) and errors as dipole_forward, and additionally
  *   q <= 262144 (2^18): larger q returns DIPOLE_EINVAL with a message saying
  *   so (split the queries, or use dipole_forward).
  *

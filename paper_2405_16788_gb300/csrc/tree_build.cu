@@ -306,9 +306,9 @@ __global__ void k_level_fill(int64_t nn, const int32_t* __restrict__ level,
     }
 }
 
-// Node sums in double: point by point inside a leaf, child by child inside an
-// internal node, both in Morton order, so that the float centroid is the
-// same on any machine.  The ratios use one correctly rounded reciprocal of
+// Node sums: in float point by point inside a leaf, in double child by child
+// inside an internal node, both in Morton order, so that the float centroid is
+// the same on any machine and double precision serves only the upper levels.  The ratios use one correctly rounded reciprocal of
 // the area: p~ = (sum A p) * (1 / sum A), eps~ = (sum A eps) * (1 / sum A).
 __device__ __forceinline__ void finalize_geom(int64_t t, const double* s, float4* cen4,
                                               float* eps_node) {
@@ -327,18 +327,22 @@ __global__ void k_geom_leaves(int64_t nn, const PointRec* __restrict__ pts,
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (!is_leaf[t]) continue;
-        double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        // float inside a leaf, one rounding per product and per sum (no fused
+        // multiply-add), point by point in Morton order
+        float fs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         const int64_t f = first[t], k = count[t];
         for (int64_t m = f; m < f + k; ++m) {
             const float4 g = pts[m].geo;
-            const double a = (double)pts[m].w.w;
-            const double e = (double)eps_sorted[m];
-            s[0] = __dadd_rn(s[0], a);
-            s[1] = __dadd_rn(s[1], __dmul_rn(a, (double)g.x));  // products are exact
-            s[2] = __dadd_rn(s[2], __dmul_rn(a, (double)g.y));
-            s[3] = __dadd_rn(s[3], __dmul_rn(a, (double)g.z));
-            s[4] = __dadd_rn(s[4], __dmul_rn(a, e));
+            const float a = pts[m].w.w;
+            fs[0] = __fadd_rn(fs[0], a);
+            fs[1] = __fadd_rn(fs[1], __fmul_rn(a, g.x));
+            fs[2] = __fadd_rn(fs[2], __fmul_rn(a, g.y));
+            fs[3] = __fadd_rn(fs[3], __fmul_rn(a, g.z));
+            fs[4] = __fadd_rn(fs[4], __fmul_rn(a, eps_sorted[m]));
         }
+        double s[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) s[j] = (double)fs[j];
 #pragma unroll
         for (int j = 0; j < 5; ++j) agg[t * 5 + j] = s[j];
         finalize_geom(t, s, cen4, eps_node);
