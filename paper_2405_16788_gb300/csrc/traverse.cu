@@ -336,7 +336,8 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n,
 // The cut is also written to the plan (word 4) when one is recorded.
 __global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int key_shift,
                             const uint32_t* pcode, int64_t n, const int32_t* leaf_of, unsigned nn,
-                            uint4* items, unsigned* n_items, uint32_t* plan) {
+                            uint4* items, unsigned* n_items, uint32_t* plan, uint32_t* ikeys,
+                            uint32_t* iidx) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t first = p * 32, last = min(q, first + 32) - 1;
@@ -349,6 +350,12 @@ __global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int ke
         if (cut == 0u || cut >= nn) cut = nn;  // one item holds the whole walk
         items[2 * p] = make_uint4((unsigned)p, 0u, cut, 0u);
         items[2 * p + 1] = make_uint4((unsigned)p, cut, nn, 1u);
+        // order: packets over many points first (a proxy of their walk's length)
+        const uint32_t key = 0xffffu - (uint32_t)min(ihi - ilo, (int64_t)0xffff);
+        ikeys[2 * p] = key;
+        ikeys[2 * p + 1] = key;
+        iidx[2 * p] = (uint32_t)(2 * p);
+        iidx[2 * p + 1] = (uint32_t)(2 * p + 1);
         if (plan) plan[p * kPlanWords + 4] = cut < nn ? cut : 0u;
         if (p == 0) *n_items = (unsigned)(2 * np);
     }
@@ -560,15 +567,23 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     }
     if (big && (mode == kForward || mode == kForwardGrad)) {
         // every packet's walk in two ranged items, adding into the zeroed outputs
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * 2 * np, s));
+        const int64_t ni = 2 * np;
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikeys, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&iidx, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikt, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ivt, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ihist, sizeof(uint32_t) * radix_hist_entries(ni), s));
         if (call.out) DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
         if (call.gout)
             DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
         note_launch();
         k_fwd_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
             codes, q, np, 30 - kQueryKeyBits, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
-            n_items, plan_w);
+            n_items, plan_w, ikeys, iidx);
+        radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
+        porder = iidx;
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (adjoint) {
