@@ -565,8 +565,9 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         plan_w = plan_cost;  // items add their steps and record their cuts
         DIP_CUDA_TRY(cudaMemsetAsync(plan_w, 0, sizeof(uint32_t) * kPlanWords * (size_t)np, s));
     }
-    if (big && (mode == kForward || mode == kForwardGrad)) {
-        // every packet's walk in two ranged items, adding into the zeroed outputs
+    if (big && mode != kCount && !plan_in) {
+        // every packet's walk in two ranged items (the forward's add into the
+        // zeroed outputs), longest predicted first
         const int64_t ni = 2 * np;
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
