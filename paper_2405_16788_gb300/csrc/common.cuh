@@ -15,6 +15,11 @@ constexpr int kMaxLevel = 10;                       // 30-bit codes: 10 octal di
 constexpr int kMaxChannels = 64;
 constexpr int kBigNode = 1 << 15;  // nodes with at least this many points sum moments in double
 
+// Bottom-up node geometry: levels above kTopLevel one launch each; levels
+// kTopLevel to 0 (few nodes) in one block of kTopThreads threads.
+constexpr int kTopLevel = 4;
+constexpr int kTopThreads = 1024;
+
 // Device status bits (OR-ed by kernels, read by dipole_sync_status).
 constexpr int kStatusTraversal = 1;
 constexpr int kStatusNonFinite = 2;

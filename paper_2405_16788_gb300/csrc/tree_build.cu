@@ -349,26 +349,32 @@ __global__ void k_geom_leaves(int64_t nn, const PointRec* __restrict__ pts,
     }
 }
 
-__global__ void k_geom_level(int l, const int32_t* __restrict__ lvl_off,
+// Levels l_hi down to l_lo; a launch over several levels must be one block
+// (its threads order the levels with __syncthreads).
+__global__ void __launch_bounds__(kTopThreads) k_geom_level(int l_hi, int l_lo,
+                             const int32_t* __restrict__ lvl_off,
                              const int32_t* __restrict__ lvl_list, const int32_t* __restrict__ skip,
                              double* __restrict__ agg, float4* __restrict__ cen4,
                              float* __restrict__ eps_node) {
-    const int32_t b = lvl_off[l], e = lvl_off[l + 1];
-    for (int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = lvl_list[i];
-        double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        int k = 0;
-        for (int32_t ch = p + 1; ch < skip[p] && k < 8; ++k) {
+    for (int l = l_hi; l >= l_lo; --l) {
+        const int32_t b = lvl_off[l], e = lvl_off[l + 1];
+        for (int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int32_t p = lvl_list[i];
+            double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            int k = 0;
+            for (int32_t ch = p + 1; ch < skip[p] && k < 8; ++k) {
 #pragma unroll
-            for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], agg[(int64_t)ch * 5 + j]);
-            const int32_t nx = skip[ch];
-            if (nx <= ch) break;  // only an imported, corrupt tree gets here
-            ch = nx;
+                for (int j = 0; j < 5; ++j) q[j] = __dadd_rn(q[j], agg[(int64_t)ch * 5 + j]);
+                const int32_t nx = skip[ch];
+                if (nx <= ch) break;  // only an imported, corrupt tree gets here
+                ch = nx;
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
+            finalize_geom(p, q, cen4, eps_node);
         }
-#pragma unroll
-        for (int j = 0; j < 5; ++j) agg[(int64_t)p * 5 + j] = q[j];
-        finalize_geom(p, q, cen4, eps_node);
+        if (l > l_lo) __syncthreads();
     }
 }
 
@@ -508,11 +514,14 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
         nn, t->level, t->is_leaf, t->lvl_off, lvl_cnt + kMaxLevel + 1, t->lvl_list);
     note_launch(); k_geom_leaves<<<grid_for(nn, kThreads), kThreads, 0, s>>>(
         nn, t->pts, eps_sorted, t->first, t->count, t->is_leaf, t->agg64, cen4, t->eps_node);
-    for (int l = t->max_depth - 1; l >= 0; --l) {
+    for (int l = t->max_depth - 1; l > kTopLevel; --l) {
         note_launch();
-        k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip,
-                                                                 t->agg64, cen4, t->eps_node);
+        k_geom_level<<<2u * (unsigned)num_sms(), kThreads, 0, s>>>(l, l, t->lvl_off, t->lvl_list,
+                                                                 t->skip, t->agg64, cen4, t->eps_node);
     }
+    note_launch();
+    k_geom_level<<<1, kTopThreads, 0, s>>>(min(kTopLevel, t->max_depth - 1), 0, t->lvl_off,
+                                          t->lvl_list, t->skip, t->agg64, cen4, t->eps_node);
     DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
     note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
                                                         rbits);

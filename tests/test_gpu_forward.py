@@ -182,3 +182,30 @@ def test_full_size_scene_1m_sampled():
     ref, rc = ot.forward(w.queries[idx], 2.0, counters=True)
     assert np.all(normwise(y[idx], ref) <= TOL), normwise(y[idx], ref)
     assert np.array_equal(cnt[idx].astype(np.int64), rc)
+
+
+def test_ranged_walk_edge_cases():
+    """Above 65,536 queries every packet's walk runs as two ranged items: a tree
+    that is a single leaf (no cut inside the walk) and 70,000 identical queries
+    (an empty code range) still give the exact sums, forward and adjoint."""
+    import torch
+    cl = syn.sphere_cloud(5, seed=11, eps=0.05)
+    mu = syn.attributes(cl.n, 4, seed=12)
+    q = syn.uniform_box_queries(70000, seed=13)
+    y, ref, c, rc = _run(cl, mu, q)
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)
+    w = syn.workload("scene-200k", scale=0.05)
+    same = np.repeat(w.queries[100:101], 70000, axis=0)
+    y2, ref2, _, _ = _run(w.cloud, w.mu, same, counts=False)
+    assert np.all(normwise(y2, ref2) <= TOL)
+    assert np.all(y2 == y2[0])  # every copy takes the same two-part sum
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    g = syn.upstream_grad(70000, 4, seed=14)
+    ga = gt.adjoint(to_dev(same), 2.0, to_dev(g)).cpu().numpy()
+    gt.sync_status()
+    ot = oracle_tree(w.cloud)
+    ot.update(w.mu)
+    ref_a = ot.adjoint(w.queries[100:101], 2.0, g.astype(np.float64).sum(0, keepdims=True))
+    assert np.all(normwise(ga, ref_a) <= 1e-3)
