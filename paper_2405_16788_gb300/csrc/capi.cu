@@ -35,9 +35,9 @@ void configure_pool_once() {
 void free_tree_memory(dipole_tree* t) {
     void* bufs[] = {t->pts,    t->code,    t->perm,   t->leaf_of, t->nodes,  t->first,
                     t->count,  t->level,   t->parent, t->skip,    t->is_leaf, t->nchild,
-                    t->big_idx, t->agg64,  t->eps_node, t->bbox,  t->status, t->mu,
-                    t->S,      t->S64,     t->dS,     t->dmu,     t->lvl_list, t->lvl_off,
-                    t->dE,     t->dgeo};
+                    t->agg64,  t->eps_node, t->bbox,  t->status, t->mu,     t->S,
+                    t->dS,     t->dmu,     t->lvl_list, t->lvl_off, t->dE,    t->dgeo,
+                    t->fix_P,  t->fix_tsum, t->fix_cmax, t->fix_kexp, t->fix_done};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }

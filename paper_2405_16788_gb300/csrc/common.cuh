@@ -13,7 +13,6 @@ namespace dip {
 constexpr float kInv4Pi = 0.0795774715459476679f;  // 1 / (4 pi), eq. pcwn
 constexpr int kMaxLevel = 10;                       // 30-bit codes: 10 octal digits
 constexpr int kMaxChannels = 64;
-constexpr int kBigNode = 1 << 15;  // nodes with at least this many points sum moments in double
 
 // Bottom-up node geometry: levels above kTopLevel one launch each; levels
 // kTopLevel to 0 (few nodes) in one block of kTopThreads threads.

@@ -25,18 +25,64 @@ __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// Bottom-up in two kinds of launches: every leaf gathers its points'
-// attributes into Morton order and sums its moments in float; then, level by
-// level from the deepest, every internal node sums its children in order, in
-// double when it holds at least kBigNode points.
+// Bottom-up without a pass per level.  The subtree of node t is the preorder
+// range [t, skip[t]), so with P[u] = the sum of the leaf moments of the nodes
+// before u in preorder, an internal node's moment is S_t = P[skip[t]] - P[t].
+// The leaf moments are float sums over their points; P is taken in 64-bit
+// fixed point with one scale 2^k per moment column, chosen from the column's
+// largest leaf moment so that no partial sum can overflow.  Integer sums are
+// exact and do not depend on the order of the additions, so the result does
+// not depend on how the scan is split across threads; the only roundings are
+// each leaf moment's conversion to a multiple of 2^-k (exact unless it is
+// below 2^-18 of the column's largest) and each node's difference back to
+// float.  Four launches: leaves (and the column maxima), tile sums (the last
+// tile to finish scans them), the prefix P, the internal nodes.
+constexpr int kRefitThreads = 256;
+constexpr int kRefitPer = 4;  // consecutive nodes per thread in the scan passes
+constexpr int kRefitTile = kRefitThreads * kRefitPer;
+constexpr int kFixChunk = 12;  // moment columns per register block
+constexpr int kFixNonFinite = 0x7fffffff;
+
+// f * 2^k for |k| <= 252 in two exact power-of-two steps.
+__device__ __forceinline__ float scale_pow2(float f, int k) {
+    const int a = k / 2, b = k - a;
+    return __fmul_rn(__fmul_rn(f, __int_as_float((a + 127) << 23)), __int_as_float((b + 127) << 23));
+}
+
+// Column scale exponent from the bits of the column's largest |leaf moment|:
+// every leaf moment is below 2^e, so with k = 61 - lg - e (nn < 2^lg) each
+// scaled moment is below 2^(61 - lg) and any sum of nn of them below 2^61.
+__device__ __forceinline__ int fixed_exp(unsigned maxbits, int lg) {
+    if (maxbits == 0u) return 0;
+    if (maxbits >= 0x7f800000u) return kFixNonFinite;
+    const int e = (int)(maxbits >> 23) - 126;
+    return min(max(61 - lg - e, -250), 250);
+}
+
+__device__ __forceinline__ long long to_fixed(float v, int k) {
+    return k == kFixNonFinite ? 0ll : __float2ll_rn(scale_pow2(v, k));
+}
+
+__device__ __forceinline__ float from_fixed(long long d, int k) {
+    return k == kFixNonFinite ? __int_as_float(0x7fffffff) : scale_pow2(__ll2float_rn(d), -k);
+}
+
+__device__ __forceinline__ int bits_of(int64_t nn) {
+    return 64 - __clzll((long long)nn);
+}
+
+// Every leaf gathers its points' attributes into Morton order and sums its
+// moments in float; the largest |moment| of each column goes to cmax.
 template <int CP, typename AT>
 __global__ void __launch_bounds__(128) k_refit_leaves(
     int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-    const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ big_idx,
-    const AT* __restrict__ attrs, int C, AT* __restrict__ mu, float* __restrict__ S,
-    double* __restrict__ S64) {
+    const int32_t* __restrict__ is_leaf, const AT* __restrict__ attrs, int C, AT* __restrict__ mu,
+    float* __restrict__ S, unsigned* __restrict__ cmax) {
     constexpr int SR = srow(CP);
+    __shared__ unsigned smax[3 * CP];
+    for (int j = threadIdx.x; j < 3 * CP; j += blockDim.x) smax[j] = 0u;
+    __syncthreads();
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < nn;
          t0 += (int64_t)gridDim.x * blockDim.x) {
         if (!is_leaf[t0]) continue;
@@ -46,7 +92,6 @@ __global__ void __launch_bounds__(128) k_refit_leaves(
 #pragma unroll
             for (int c = 0; c < CP; ++c) mu[m * CP + c] = c < C ? attrs[o * C + c] : from_f<AT>(0.0f);
         }
-        const int32_t bl = big_idx[t0];
 #pragma unroll
         for (int c0 = 0; c0 < CP; c0 += 4) {
             float sacc[12];
@@ -67,72 +112,197 @@ __global__ void __launch_bounds__(128) k_refit_leaves(
             for (int j = 0; j < 12; ++j) {
                 if (3 * c0 + j >= 3 * CP) break;
                 S[t0 * SR + 3 * c0 + j] = sacc[j];
-                if (bl >= 0) S64[(int64_t)bl * SR + 3 * c0 + j] = (double)sacc[j];
+                const unsigned bits = __float_as_uint(fabsf(sacc[j]));
+                if (bits) atomicMax(&smax[3 * c0 + j], bits);
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < 3 * CP; j += blockDim.x)
+        if (smax[j]) atomicMax(&cmax[j], smax[j]);
+}
+
+// Sum of V int64 values over the block (kRefitThreads threads); the totals
+// land in tot[] of thread 0 only.  red must hold kRefitThreads / 32 * V.
+template <int V>
+__device__ __forceinline__ void block_sum_i64(long long (&v)[V], long long* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) red[warp * V + j] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            long long s = 0;
+            for (int w = 0; w < kRefitThreads / 32; ++w) s += red[w * V + j];
+            v[j] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Exclusive prefix of V int64 values over the block's threads in order.
+template <int V>
+__device__ __forceinline__ void block_exclusive_i64(long long (&v)[V], long long* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        inc[j] = v[j];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, inc[j], o);
+            if (lane >= o) inc[j] += u;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) red[warp * V + j] = inc[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        long long before = 0;
+        for (int w = 0; w < warp; ++w) before += red[w * V + j];
+        v[j] = before + inc[j] - v[j];
+    }
+    __syncthreads();
+}
+
+// Tile b = nodes [b kRefitTile, (b + 1) kRefitTile): the fixed-point sum of its
+// leaf moments per column.  The last tile to finish (an arrival counter; no
+// block waits for another) scans the tile sums into tile offsets, publishes
+// the column exponents and clears cmax and the counter for the next refit.
+template <int CP>
+__global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
+    int64_t nn, const int32_t* __restrict__ is_leaf, const float* __restrict__ S,
+    unsigned* __restrict__ cmax, int* __restrict__ kexp, long long* __restrict__ tsum,
+    unsigned* __restrict__ done) {
+    constexpr int SR = srow(CP), NC = 3 * CP;
+    constexpr int V = NC < kFixChunk ? NC : kFixChunk;
+    __shared__ int sk[NC];
+    __shared__ long long red[kRefitThreads / 32 * V];
+    __shared__ bool last;
+    const int lg = bits_of(nn);
+    for (int j = threadIdx.x; j < NC; j += blockDim.x) sk[j] = fixed_exp(cmax[j], lg);
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRefitTile + (int64_t)threadIdx.x * kRefitPer;
+    const int ntiles = gridDim.x;
+#pragma unroll 1
+    for (int j0 = 0; j0 < NC; j0 += V) {
+        long long v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = 0;
+        for (int r = 0; r < kRefitPer; ++r) {
+            const int64_t t = base + r;
+            if (t >= nn || !is_leaf[t]) continue;
+#pragma unroll
+            for (int j = 0; j < V; ++j) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
+        }
+        block_sum_i64<V>(v, red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) tsum[(int64_t)blockIdx.x * NC + j0 + j] = v[j];
+        }
+    }
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == (unsigned)ntiles - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // exclusive scan of the tile sums, one warp per column, 32 tiles a round
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < NC; j += kRefitThreads / 32) {
+        long long carry = 0;
+        for (int b0 = 0; b0 < ntiles; b0 += 32) {
+            const int b = b0 + lane;
+            const long long x = b < ntiles ? __ldcg(tsum + (int64_t)b * NC + j) : 0ll;
+            long long inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            if (b < ntiles) tsum[(int64_t)b * NC + j] = carry + inc - x;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
+    for (int j = threadIdx.x; j < NC; j += blockDim.x) {
+        kexp[j] = sk[j];
+        cmax[j] = 0u;
+    }
+    if (threadIdx.x == 0) *done = 0u;
+}
+
+// P[t] for the tile's nodes (and P[nn], the total): the tile's offset plus the
+// exclusive prefix of the leaf moments inside the tile.
+template <int CP>
+__global__ void __launch_bounds__(kRefitThreads) k_refit_prefix(
+    int64_t nn, const int32_t* __restrict__ is_leaf, const float* __restrict__ S,
+    const int* __restrict__ kexp, const long long* __restrict__ toff, long long* __restrict__ P) {
+    constexpr int SR = srow(CP), NC = 3 * CP;
+    constexpr int V = NC < kFixChunk ? NC : kFixChunk;
+    __shared__ int sk[NC];
+    __shared__ long long red[kRefitThreads / 32 * V];
+    for (int j = threadIdx.x; j < NC; j += blockDim.x) sk[j] = kexp[j];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRefitTile + (int64_t)threadIdx.x * kRefitPer;
+#pragma unroll 1
+    for (int j0 = 0; j0 < NC; j0 += V) {
+        long long v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = 0;
+        for (int r = 0; r < kRefitPer; ++r) {
+            const int64_t t = base + r;
+            if (t >= nn || !is_leaf[t]) continue;
+#pragma unroll
+            for (int j = 0; j < V; ++j) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
+        }
+        block_exclusive_i64<V>(v, red);
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] += toff[(int64_t)blockIdx.x * NC + j0 + j];
+        for (int r = 0; r < kRefitPer; ++r) {
+            const int64_t t = base + r;
+            if (t >= nn) break;
+            const bool lf = is_leaf[t] != 0;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                P[t * NC + j0 + j] = v[j];
+                if (lf) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
+            }
+            if (t == nn - 1) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) P[nn * NC + j0 + j] = v[j];
             }
         }
     }
 }
 
+// Internal nodes: S_t = P[skip[t]] - P[t], back to float.
 template <int CP>
-__global__ void __launch_bounds__(128) k_refit_level(int l, const int32_t* __restrict__ lvl_off,
-                                                     const int32_t* __restrict__ lvl_list,
-                                                     const int32_t* __restrict__ skip,
-                                                     const int32_t* __restrict__ big_idx,
-                                                     float* __restrict__ S, double* __restrict__ S64) {
-    constexpr int SR = srow(CP);
-    const int32_t b = lvl_off[l], e = lvl_off[l + 1];
-    for (int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = lvl_list[i];
-        const int32_t bp = big_idx[p];
-        const int32_t end = skip[p];
-#pragma unroll 1
-        for (int j0 = 0; j0 < 3 * CP; j0 += 12) {
-            if (bp >= 0) {
-                double q[12];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) q[j] = 0.0;
-                int kc = 0;
-                for (int32_t ch = p + 1; ch < end && kc < 8; ++kc) {
-                    const int32_t bc = big_idx[ch];
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        if (j0 + j >= 3 * CP) break;
-                        q[j] += bc >= 0 ? S64[(int64_t)bc * SR + j0 + j]
-                                        : (double)S[(int64_t)ch * SR + j0 + j];
-                    }
-                    const int32_t nx = skip[ch];
-                    if (nx <= ch) break;  // only an imported, corrupt tree gets here
-                    ch = nx;
-                }
-#pragma unroll
-                for (int j = 0; j < 12; ++j) {
-                    if (j0 + j >= 3 * CP) break;
-                    S64[(int64_t)bp * SR + j0 + j] = q[j];
-                    S[(int64_t)p * SR + j0 + j] = (float)q[j];
-                }
-            } else {
-                float q[12];
-#pragma unroll
-                for (int j = 0; j < 12; ++j) q[j] = 0.0f;
-                int kc = 0;
-                for (int32_t ch = p + 1; ch < end && kc < 8; ++kc) {
-#pragma unroll
-                    for (int j = 0; j < 12; ++j) {
-                        if (j0 + j >= 3 * CP) break;
-                        q[j] += S[(int64_t)ch * SR + j0 + j];
-                    }
-                    const int32_t nx = skip[ch];
-                    if (nx <= ch) break;  // only an imported, corrupt tree gets here
-                    ch = nx;
-                }
-#pragma unroll
-                for (int j = 0; j < 12; ++j) {
-                    if (j0 + j >= 3 * CP) break;
-                    S[(int64_t)p * SR + j0 + j] = q[j];
-                }
-            }
-        }
+__global__ void __launch_bounds__(128) k_refit_internal(
+    int64_t nn, const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ skip,
+    const int* __restrict__ kexp, const long long* __restrict__ P, float* __restrict__ S) {
+    constexpr int SR = srow(CP), NC = 3 * CP;
+    __shared__ int sk[NC];
+    for (int j = threadIdx.x; j < NC; j += blockDim.x) sk[j] = kexp[j];
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (is_leaf[t]) continue;
+        int64_t e = skip[t];
+        if (e < t || e > nn) e = t;  // only an imported, corrupt tree gets here
+        const long long* hi = P + e * NC;
+        const long long* lo = P + t * NC;
+#pragma unroll 4
+        for (int j = 0; j < NC; ++j) S[t * SR + j] = from_fixed(hi[j] - lo[j], sk[j]);
     }
 }
 
@@ -264,15 +434,20 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     int64_t blocks = (t->nn + 127) / 128;
     int64_t cap = (int64_t)num_sms() * 16;
     const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+    const unsigned ntiles = (unsigned)((t->nn + kRefitTile - 1) / kRefitTile);
     note_launch();
     k_refit_leaves<CP, AT><<<grid, 128, 0, s>>>(t->nn, t->pts, t->perm, t->first, t->count,
-                                                t->is_leaf, t->big_idx, (const AT*)attrs, t->C,
-                                                (AT*)t->mu, t->S, t->S64);
-    for (int l = t->max_depth - 1; l >= 0; --l) {
-        note_launch();
-        k_refit_level<CP><<<4u * (unsigned)num_sms(), 128, 0, s>>>(l, t->lvl_off, t->lvl_list, t->skip, t->big_idx,
-                                                t->S, t->S64);
-    }
+                                                t->is_leaf, (const AT*)attrs, t->C, (AT*)t->mu,
+                                                t->S, t->fix_cmax);
+    note_launch();
+    k_refit_tiles<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, t->is_leaf, t->S, t->fix_cmax,
+                                                       t->fix_kexp, t->fix_tsum, t->fix_done);
+    note_launch();
+    k_refit_prefix<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, t->is_leaf, t->S, t->fix_kexp,
+                                                        t->fix_tsum, t->fix_P);
+    note_launch();
+    k_refit_internal<CP><<<grid, 128, 0, s>>>(t->nn, t->is_leaf, t->skip, t->fix_kexp, t->fix_P,
+                                              t->S);
 }
 
 template <int CP>
@@ -301,17 +476,28 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
     const int SR = srow(Cp);
     if (t->attr_Cp_alloc != Cp || t->attr_dtype_alloc != dtype) {
         // (re)allocate the attribute state; previous buffers are freed in stream order
-        void* bufs[] = {t->mu, t->S, t->S64, t->dS, t->dmu};
+        void* bufs[] = {t->mu, t->S, t->dS, t->dmu, t->fix_P, t->fix_tsum, t->fix_cmax,
+                        t->fix_kexp, t->fix_done};
         for (void* b : bufs)
             if (b) cudaFreeAsync(b, s);
-        t->mu = nullptr; t->S = nullptr; t->S64 = nullptr; t->dS = nullptr; t->dmu = nullptr;
+        t->mu = nullptr; t->S = nullptr; t->dS = nullptr; t->dmu = nullptr;
+        t->fix_P = nullptr; t->fix_tsum = nullptr; t->fix_cmax = nullptr; t->fix_kexp = nullptr;
+        t->fix_done = nullptr;
         const size_t esz = dtype == 1 ? 2 : 4;
+        const size_t NC = 3 * (size_t)Cp;
+        const size_t ntiles = (size_t)((t->nn + kRefitTile - 1) / kRefitTile);
         DIP_CUDA_TRY(cudaMallocAsync(&t->mu, esz * (size_t)t->n * Cp, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S, sizeof(float) * (size_t)t->nn * SR, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S64, sizeof(double) * (size_t)(t->nbig + 1) * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dS, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dmu, sizeof(float) * (size_t)t->n * Cp, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_P, sizeof(long long) * ((size_t)t->nn + 1) * NC, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_tsum, sizeof(long long) * ntiles * NC, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_cmax, sizeof(unsigned) * NC, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_kexp, sizeof(int) * NC, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_done, sizeof(unsigned), s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)t->nn * SR, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(t->fix_cmax, 0, sizeof(unsigned) * NC, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(t->fix_done, 0, sizeof(unsigned), s));
         t->attr_Cp_alloc = Cp;
         t->attr_dtype_alloc = dtype;
     }

@@ -30,10 +30,8 @@ struct dipole_tree {
     int32_t* skip = nullptr;
     int32_t* is_leaf = nullptr;
     int32_t* nchild = nullptr;
-    int32_t* big_idx = nullptr;  // index into S64 for nodes with >= kBigNode points, else -1
     int32_t* lvl_list = nullptr; // internal nodes grouped by level
     int32_t* lvl_off = nullptr;  // [kMaxLevel + 2] start of each level in lvl_list
-    int64_t nbig = 0;
     double* agg64 = nullptr;     // [nn, 5] sum A, sum A p (3), sum A eps
     float* eps_node = nullptr;   // [nn]
     float* bbox = nullptr;       // device: lo.xyz, ext, 1024/ext
@@ -46,7 +44,12 @@ struct dipole_tree {
     int dtype = 0;
     void* mu = nullptr;          // [n, Cp] float or bf16, Morton order
     float* S = nullptr;          // [nn, 3 Cp]
-    double* S64 = nullptr;       // [nbig, 3 Cp]
+    // refit scratch: fixed-point prefix of the leaf moments over preorder
+    long long* fix_P = nullptr;     // [nn + 1, 3 Cp]
+    long long* fix_tsum = nullptr;  // [tiles, 3 Cp] tile sums, then tile offsets
+    unsigned* fix_cmax = nullptr;   // [3 Cp] largest |leaf moment| (float bits), 0 between refits
+    int* fix_kexp = nullptr;        // [3 Cp] column scale exponents
+    unsigned* fix_done = nullptr;   // tile arrival counter, 0 between refits
     float* dS = nullptr;         // [nn, 3 Cp] adjoint node accumulators
     float* dmu = nullptr;        // [n, Cp] adjoint opened-leaf accumulators
     float* dE = nullptr;         // [nn] adjoint d eps~_t sums (normal/radius gradients)

@@ -413,9 +413,7 @@ __global__ void k_finalize_nodes(int64_t nn, const float4* __restrict__ cen4,
                                  const int32_t* __restrict__ skip, const int32_t* __restrict__ first,
                                  const int32_t* __restrict__ count,
                                  const int32_t* __restrict__ is_leaf,
-                                 const float* __restrict__ eps_node, NodeRec* __restrict__ nodes,
-                                 int32_t* __restrict__ big_idx, unsigned int* nbig,
-                                 unsigned int nbig_cap) {
+                                 const float* __restrict__ eps_node, NodeRec* __restrict__ nodes) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
          t += (int64_t)gridDim.x * blockDim.x) {
         const float4 c = cen4[t];
@@ -424,12 +422,6 @@ __global__ void k_finalize_nodes(int64_t nn, const float4* __restrict__ cen4,
         r.meta = make_int4(skip[t], first[t], is_leaf[t] ? count[t] : 0,
                            __float_as_int(__frcp_rn(eps_node[t])));
         nodes[t] = r;
-        int32_t b = -1;
-        if (count[t] >= kBigNode) {
-            const unsigned int slot = atomicAdd(nbig, 1u);
-            if (slot < nbig_cap) b = (int32_t)slot;  // an imported tree may overlap nodes
-        }
-        big_idx[t] = b;
     }
 }
 
@@ -488,20 +480,15 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
     DIP_CUDA_TRY(dalloc(&t->nodes, nn, s));
     DIP_CUDA_TRY(dalloc(&t->parent, nn, s));
     DIP_CUDA_TRY(dalloc(&t->nchild, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->big_idx, nn, s));
     DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
     DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
     DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
     DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
     float4* cen4 = nullptr;
-    unsigned int *rbits = nullptr, *nbig = nullptr, *lvl_cnt = nullptr;
+    unsigned int *rbits = nullptr, *lvl_cnt = nullptr;
     DIP_CUDA_TRY(dalloc(&cen4, nn, s));
     DIP_CUDA_TRY(dalloc(&rbits, nn, s));
-    DIP_CUDA_TRY(dalloc(&nbig, 1, s));
     DIP_CUDA_TRY(dalloc(&lvl_cnt, 2 * (kMaxLevel + 1), s));
-    // Nodes of one level are disjoint, so each level has at most n / kBigNode
-    // big nodes: an upper bound that needs no second synchronization.
-    t->nbig = (int64_t)(t->max_depth + 1) * (n / kBigNode + 1);
 
     DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
     note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
@@ -525,16 +512,12 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
     DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
     note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
                                                         rbits);
-    DIP_CUDA_TRY(cudaMemsetAsync(nbig, 0, sizeof(unsigned int), s));
     note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
                                                                  t->first, t->count, t->is_leaf,
-                                                                 t->eps_node, t->nodes,
-                                                                 t->big_idx, nbig,
-                                                                 (unsigned int)t->nbig);
+                                                                 t->eps_node, t->nodes);
     cudaFreeAsync(cen4, s);
     cudaFreeAsync(rbits, s);
     cudaFreeAsync(lvl_cnt, s);
-    cudaFreeAsync(nbig, s);
     DIP_CUDA_TRY(cudaGetLastError());
     return 0;
 }
