@@ -282,12 +282,89 @@ k_query(const QueryArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ item order
+// Work items run in decreasing order of an estimated cost, so that the long
+// ones start first and the queue's tail is short.  The order only needs to be
+// coarse: an item goes to one of 256 buckets of its cost on a log scale (16 per
+// octave; bucket 0 holds the most costly).  The kernel that makes the items
+// counts them per bucket; the last of its blocks to finish (an arrival
+// counter: no block waits for another) turns the counts into bucket starts,
+// and k_order_place puts every item into its bucket.  The order inside a
+// bucket is that of arrival, which changes no result: the forward's two parts
+// of a query add into its zeroed output (a sum of two floats, either order),
+// and the adjoint's node sums are atomic adds in any case.
+// ostate: [0, 256) counts, [256, 512) bucket cursors, [512] arrivals; zeroed
+// before the item kernel.
+constexpr int kOrderBuckets = 256;
+constexpr int kOrderStateWords = 2 * kOrderBuckets + 1;
+constexpr uint32_t kNoBucket = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t cost_bucket(uint32_t c) {
+    const uint32_t x = min(c, 0x7fffffffu) + 1u;
+    const int e = 31 - __clz(x);
+    const uint32_t frac = e >= 4 ? (x >> (e - 4)) & 15u : (x << (4 - e)) & 15u;
+    const uint32_t f = min(16u * (uint32_t)e + frac, (uint32_t)kOrderBuckets - 1u);
+    return (uint32_t)kOrderBuckets - 1u - f;
+}
+
+// End of an item kernel: add the block's bucket counts (sh, shared) to ostate;
+// the last block writes the exclusive bucket starts.  Called by every thread.
+__device__ __forceinline__ void order_counts_flush(const uint32_t* sh, uint32_t* ostate) {
+    __shared__ bool last;
+    __syncthreads();
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+        if (sh[b]) atomicAdd(ostate + b, sh[b]);
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(ostate + 2 * kOrderBuckets, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    const int lane = threadIdx.x;
+    constexpr int K = kOrderBuckets / 32;
+    uint32_t c[K], sum = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        c[k] = __ldcg(ostate + K * lane + k);
+        sum += c[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ostate[kOrderBuckets + K * lane + k] = run;
+        run += c[k];
+    }
+}
+
+__global__ void k_order_place(const uint32_t* __restrict__ ibucket, int64_t ni,
+                              uint32_t* __restrict__ ostate, uint32_t* __restrict__ porder) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < ni; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const uint32_t b = i < ni ? ibucket[i] : kNoBucket;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (b != kNoBucket && lane == leader) base = atomicAdd(ostate + kOrderBuckets + b, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b != kNoBucket) porder[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
 // Work items of the ranged adjoint: packet p's walk is cut at the increasing
 // nodes of plan words [1..7] inside (0, nn); item k of p goes to slot
-// p * kPlanWords + k with the sort key of its estimated steps (the packet's
-// steps shared evenly); unused slots get the largest key and sort last.
+// p * kPlanWords + k, in the bucket of its estimated steps (the packet's steps
+// shared evenly); unused slots get no bucket.
 __global__ void k_plan_items(const uint32_t* plan, int64_t np, unsigned nn, uint4* items,
-                             uint32_t* ikeys, uint32_t* iidx, unsigned* n_items) {
+                             uint32_t* ibucket, unsigned* n_items, uint32_t* ostate) {
+    __shared__ uint32_t sh[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t* w = plan + p * kPlanWords;
@@ -300,24 +377,25 @@ __global__ void k_plan_items(const uint32_t* plan, int64_t np, unsigned nn, uint
                 prev = c;
             }
         }
-        const unsigned steps = min(w[0], 0xfff0u);
-        const unsigned est = max(1u, steps / (ncut + 1u));
+        const unsigned est = max(1u, w[0] / (ncut + 1u));
+        const uint32_t bk = cost_bucket(est);
         unsigned lo = 0;
         for (unsigned k = 0; k < kPlanWords; ++k) {
             const int64_t slot = p * kPlanWords + k;
-            iidx[slot] = (uint32_t)slot;
             if (k <= ncut) {
                 const unsigned hi = k < ncut ? cut[k] : nn;
                 items[slot] = make_uint4((unsigned)p, lo, hi, 0u);
-                ikeys[slot] = 0xfffeu - min(est, 0xfffeu);
+                ibucket[slot] = bk;
                 lo = hi;
             } else {
                 items[slot] = make_uint4((unsigned)p, nn, nn, 0u);
-                ikeys[slot] = 0xffffu;
+                ibucket[slot] = kNoBucket;
             }
         }
+        atomicAdd(&sh[bk], ncut + 1u);
         atomicAdd(n_items, ncut + 1u);
     }
+    order_counts_flush(sh, ostate);
 }
 
 __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n, uint32_t x) {
@@ -333,11 +411,15 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n,
 // The forward's two items per packet: the walk is cut at the leaf holding the
 // middle point (Morton order) of those whose codes fall in the packet's code
 // range, which puts about half of a packet's near-field work on each side.
+// Both go to the bucket of that point count (a proxy of the walk's length).
 // The cut is also written to the plan (word 4) when one is recorded.
 __global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int key_shift,
                             const uint32_t* pcode, int64_t n, const int32_t* leaf_of, unsigned nn,
-                            uint4* items, unsigned* n_items, uint32_t* plan, uint32_t* ikeys,
-                            uint32_t* iidx) {
+                            uint4* items, unsigned* n_items, uint32_t* plan, uint32_t* ibucket,
+                            uint32_t* ostate) {
+    __shared__ uint32_t sh[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t first = p * 32, last = min(q, first + 32) - 1;
@@ -350,15 +432,21 @@ __global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int ke
         if (cut == 0u || cut >= nn) cut = nn;  // one item holds the whole walk
         items[2 * p] = make_uint4((unsigned)p, 0u, cut, 0u);
         items[2 * p + 1] = make_uint4((unsigned)p, cut, nn, 1u);
-        // order: packets over many points first (a proxy of their walk's length)
-        const uint32_t key = 0xffffu - (uint32_t)min(ihi - ilo, (int64_t)0xffff);
-        ikeys[2 * p] = key;
-        ikeys[2 * p + 1] = key;
-        iidx[2 * p] = (uint32_t)(2 * p);
-        iidx[2 * p + 1] = (uint32_t)(2 * p + 1);
+        const uint32_t bk = cost_bucket((uint32_t)min(ihi - ilo, (int64_t)0x7fffffff));
+        ibucket[2 * p] = bk;
+        ibucket[2 * p + 1] = bk;
+        atomicAdd(&sh[bk], 2u);
         if (plan) plan[p * kPlanWords + 4] = cut < nn ? cut : 0u;
         if (p == 0) *n_items = (unsigned)(2 * np);
     }
+    order_counts_flush(sh, ostate);
+}
+
+void order_place(const uint32_t* ibucket, int64_t ni, uint32_t* ostate, uint32_t* porder,
+                 cudaStream_t s) {
+    const int64_t blocks = (ni + 255) / 256, cap = (int64_t)num_sms() * 8;
+    note_launch();
+    k_order_place<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(ibucket, ni, ostate, porder);
 }
 
 // Packets below this count are too few for the queue's tail to matter.
@@ -541,25 +629,23 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     uint32_t* plan_w = nullptr;  // the plan this forward records
     uint4* items = nullptr;
     unsigned* n_items = nullptr;
-    uint32_t *ikeys = nullptr, *iidx = nullptr, *ikt = nullptr, *ivt = nullptr, *ihist = nullptr;
+    uint32_t *ibucket = nullptr, *iorder = nullptr, *ostate = nullptr;
     const bool big = q > 0 && !grid && np >= kOrderMinPackets;
     if (big && (mode == kAdjoint || mode == kAdjointGrad || mode == kAdjointGeom) && plan_in &&
         plan_cost) {
         // ranged items from the walk cuts recorded by the forward, longest first
         const int64_t ni = np * kPlanWords;
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikeys, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&iidx, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikt, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ivt, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ihist, sizeof(uint32_t) * radix_hist_entries(ni), s));
-        DIP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(unsigned), s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ibucket, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&iorder, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ostate, sizeof(uint32_t) * (kOrderStateWords + 1), s));
+        n_items = ostate + kOrderStateWords;
+        DIP_CUDA_TRY(cudaMemsetAsync(ostate, 0, sizeof(uint32_t) * (kOrderStateWords + 1), s));
         note_launch();
         k_plan_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, np, (unsigned)t->nn,
-                                                                  items, ikeys, iidx, n_items);
-        radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
-        porder = iidx;
+                                                                  items, ibucket, n_items, ostate);
+        order_place(ibucket, ni, ostate, iorder, s);
+        porder = iorder;
     }
     if (big && !plan_in && plan_cost && (mode == kForward || mode == kForwardGrad)) {
         plan_w = plan_cost;  // items add their steps and record their cuts
@@ -570,21 +656,20 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         // zeroed outputs), longest predicted first
         const int64_t ni = 2 * np;
         DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&n_items, sizeof(unsigned), s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikeys, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&iidx, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ikt, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ivt, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ihist, sizeof(uint32_t) * radix_hist_entries(ni), s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ibucket, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&iorder, sizeof(uint32_t) * ni, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&ostate, sizeof(uint32_t) * (kOrderStateWords + 1), s));
+        n_items = ostate + kOrderStateWords;
+        DIP_CUDA_TRY(cudaMemsetAsync(ostate, 0, sizeof(uint32_t) * (kOrderStateWords + 1), s));
         if (call.out) DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
         if (call.gout)
             DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
         note_launch();
         k_fwd_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
             codes, q, np, 30 - kQueryKeyBits, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
-            n_items, plan_w, ikeys, iidx);
-        radix_sort_pairs(ikeys, iidx, ikt, ivt, ihist, ni, 16, s);
-        porder = iidx;
+            n_items, plan_w, ibucket, ostate);
+        order_place(ibucket, ni, ostate, iorder, s);
+        porder = iorder;
     }
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (adjoint) {
@@ -649,11 +734,9 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     cudaFreeAsync(work, s);
     if (items) {
         cudaFreeAsync(items, s);
-        cudaFreeAsync(n_items, s);
-    }
-    if (ikeys) {
-        cudaFreeAsync(ikeys, s); cudaFreeAsync(iidx, s); cudaFreeAsync(ikt, s); cudaFreeAsync(ivt, s);
-        cudaFreeAsync(ihist, s);
+        cudaFreeAsync(ibucket, s);
+        cudaFreeAsync(iorder, s);
+        cudaFreeAsync(ostate, s);
     }
     if (codes) {
         cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);
