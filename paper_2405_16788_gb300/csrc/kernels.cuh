@@ -162,18 +162,19 @@ __device__ __forceinline__ void adjoint_far_reduce(float vx, float vy, float vz,
         a1 += __shfl_xor_sync(FULL, vy * gp[1], 16);
         a2 += __shfl_xor_sync(FULL, vz * gp[1], 16);
     }
+    // The remaining lane bits (B and below) finish the three axis sums as a
+    // reduce-scatter over four slots (x, y, z, 0): bit B splits them {x, y} /
+    // {z, 0}, bit B/2 one slot each, a butterfly does the rest; one lane per
+    // slot then adds it.
+    constexpr int B = CH == 4 ? 4 : CH == 2 ? 8 : 16;
+    const bool hb = (lane & B) != 0, lb = (lane & (B / 2)) != 0;
+    const float k0 = (hb ? a2 : a0) + __shfl_xor_sync(FULL, hb ? a0 : a2, B);
+    const float k1 = (hb ? 0.0f : a1) + __shfl_xor_sync(FULL, hb ? a1 : 0.0f, B);
+    float r = (lb ? k1 : k0) + __shfl_xor_sync(FULL, lb ? k0 : k1, B / 2);
 #pragma unroll
-    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1) {
-        a0 += __shfl_xor_sync(FULL, a0, off);
-        a1 += __shfl_xor_sync(FULL, a1, off);
-        a2 += __shfl_xor_sync(FULL, a2, off);
-    }
-    if (lane_owns<CH>(lane)) {
-        float* d = dst + 3 * kept;
-        if (a0 != 0.0f) atomicAdd(d, a0);
-        if (a1 != 0.0f) atomicAdd(d + 1, a1);
-        if (a2 != 0.0f) atomicAdd(d + 2, a2);
-    }
+    for (int off = B / 4; off > 0; off >>= 1) r += __shfl_xor_sync(FULL, r, off);
+    const int axis = (hb ? 2 : 0) + (lb ? 1 : 0);
+    if ((lane & (B / 2 - 1)) == 0 && axis < 3 && r != 0.0f) atomicAdd(dst + 3 * kept + axis, r);
 }
 
 // Opened-leaf point: adds sum over lanes of k g^c into dst[c] for the chunk.
@@ -218,18 +219,19 @@ __device__ __forceinline__ void adjoint_vec_reduce(const float (&v)[3 * CH], flo
         a1 += __shfl_xor_sync(FULL, v[4], 16);
         a2 += __shfl_xor_sync(FULL, v[5], 16);
     }
+    // The remaining lane bits (B and below) finish the three axis sums as a
+    // reduce-scatter over four slots (x, y, z, 0): bit B splits them {x, y} /
+    // {z, 0}, bit B/2 one slot each, a butterfly does the rest; one lane per
+    // slot then adds it.
+    constexpr int B = CH == 4 ? 4 : CH == 2 ? 8 : 16;
+    const bool hb = (lane & B) != 0, lb = (lane & (B / 2)) != 0;
+    const float k0 = (hb ? a2 : a0) + __shfl_xor_sync(FULL, hb ? a0 : a2, B);
+    const float k1 = (hb ? 0.0f : a1) + __shfl_xor_sync(FULL, hb ? a1 : 0.0f, B);
+    float r = (lb ? k1 : k0) + __shfl_xor_sync(FULL, lb ? k0 : k1, B / 2);
 #pragma unroll
-    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1) {
-        a0 += __shfl_xor_sync(FULL, a0, off);
-        a1 += __shfl_xor_sync(FULL, a1, off);
-        a2 += __shfl_xor_sync(FULL, a2, off);
-    }
-    if (lane_owns<CH>(lane)) {
-        float* d = dst + 3 * kept;
-        if (a0 != 0.0f) atomicAdd(d, a0);
-        if (a1 != 0.0f) atomicAdd(d + 1, a1);
-        if (a2 != 0.0f) atomicAdd(d + 2, a2);
-    }
+    for (int off = B / 4; off > 0; off >>= 1) r += __shfl_xor_sync(FULL, r, off);
+    const int axis = (hb ? 2 : 0) + (lb ? 1 : 0);
+    if ((lane & (B / 2 - 1)) == 0 && axis < 3 && r != 0.0f) atomicAdd(dst + 3 * kept + axis, r);
 }
 
 template <int CH>

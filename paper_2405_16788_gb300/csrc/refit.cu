@@ -43,6 +43,9 @@ constexpr int kRefitTile = kRefitThreads * kRefitPer;
 constexpr int kFixChunk = 12;  // moment columns per register block
 constexpr int kFixNonFinite = 0x7fffffff;
 
+// Leading dimension of the column-major prefix P: nn + 1 rows rounded up to 4.
+inline int64_t fix_ld(int64_t nn) { return (nn + 1 + 3) & ~int64_t(3); }
+
 // f * 2^k for |k| <= 252 in two exact power-of-two steps.
 __device__ __forceinline__ float scale_pow2(float f, int k) {
     const int a = k / 2, b = k - a;
@@ -52,68 +55,150 @@ __device__ __forceinline__ float scale_pow2(float f, int k) {
 // Column scale exponent from the bits of the column's largest |leaf moment|:
 // every leaf moment is below 2^e, so with k = 61 - lg - e (nn < 2^lg) each
 // scaled moment is below 2^(61 - lg) and any sum of nn of them below 2^61.
+// Finite floats and nn < 2^31 keep k within [-99, 186].
 __device__ __forceinline__ int fixed_exp(unsigned maxbits, int lg) {
     if (maxbits == 0u) return 0;
     if (maxbits >= 0x7f800000u) return kFixNonFinite;
     const int e = (int)(maxbits >> 23) - 126;
-    return min(max(61 - lg - e, -250), 250);
+    return min(max(61 - lg - e, -200), 200);
 }
 
+// v 2^k rounded to the nearest integer (ties to even), in integer arithmetic
+// (the 64-bit conversion instructions run at the FP64 rate).  The scale keeps
+// the result below 2^61, so the left shift is at most 37.
 __device__ __forceinline__ long long to_fixed(float v, int k) {
-    return k == kFixNonFinite ? 0ll : __float2ll_rn(scale_pow2(v, k));
+    if (k == kFixNonFinite) return 0ll;
+    const uint32_t u = __float_as_uint(v);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    const uint32_t mant = ex ? ((u & 0x7fffffu) | 0x800000u) : (u & 0x7fffffu);
+    const int sh = (ex ? (int)ex : 1) - 150 + k;  // v = mant 2^(max(ex, 1) - 150)
+    uint64_t r;
+    if (sh >= 0) {
+        r = (uint64_t)mant << sh;
+    } else if (sh < -24) {
+        r = 0;  // below 1/4
+    } else {
+        const int rs = -sh;
+        const uint32_t q = mant >> rs, rem = mant & ((1u << rs) - 1u), half = 1u << (rs - 1);
+        r = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+    }
+    return (u >> 31) ? -(long long)r : (long long)r;
 }
 
+// d 2^-k rounded to float (ties to even), in integer arithmetic.
 __device__ __forceinline__ float from_fixed(long long d, int k) {
-    return k == kFixNonFinite ? __int_as_float(0x7fffffff) : scale_pow2(__ll2float_rn(d), -k);
+    if (k == kFixNonFinite) return __int_as_float(0x7fffffff);
+    if (d == 0) return 0.0f;
+    const uint64_t a = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
+    const int msb = 63 - __clzll((long long)a);
+    uint32_t q = (uint32_t)a;
+    int e = 0;
+    if (msb > 23) {
+        const int rs = msb - 23;
+        q = (uint32_t)(a >> rs);
+        const uint64_t rem = a & ((1ull << rs) - 1ull), half = 1ull << (rs - 1);
+        q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+        e = rs;
+    }
+    const float f = __uint2float_rn(q);  // exact: q <= 2^24
+    return scale_pow2(d < 0 ? -f : f, e - k);
+}
+
+// Columns j0 .. j0 + V of row t of S (rows of SR floats, 16-byte aligned;
+// j0 is a multiple of 12 or 0, and the float4s read stay inside the row).
+template <int SR, int V>
+__device__ __forceinline__ void load_cols(const float* __restrict__ S, int64_t t, int j0,
+                                          float (&x)[V]) {
+    const float4* p = reinterpret_cast<const float4*>(S + t * SR + j0);
+#pragma unroll
+    for (int i = 0; i < (V + 3) / 4; ++i) {
+        const float4 q = p[i];
+        if (4 * i < V) x[4 * i] = q.x;
+        if (4 * i + 1 < V) x[4 * i + 1] = q.y;
+        if (4 * i + 2 < V) x[4 * i + 2] = q.z;
+        if (4 * i + 3 < V) x[4 * i + 3] = q.w;
+    }
 }
 
 __device__ __forceinline__ int bits_of(int64_t nn) {
     return 64 - __clzll((long long)nn);
 }
 
-// Every leaf gathers its points' attributes into Morton order and sums its
-// moments in float; the largest |moment| of each column goes to cmax.
+// Leaves, one thread per point (Morton order): the thread gathers its point's
+// attributes into mu and stages them with A_m n_m in shared memory; the
+// thread at each leaf's first point sums the leaf's moments in float, point by
+// point (a leaf running past the block's points reads the rest from global
+// memory).  The largest |moment| of each column goes to cmax.
+constexpr int kLeafThreads = 256;
+
 template <int CP, typename AT>
-__global__ void __launch_bounds__(128) k_refit_leaves(
-    int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
-    const int32_t* __restrict__ first, const int32_t* __restrict__ count,
-    const int32_t* __restrict__ is_leaf, const AT* __restrict__ attrs, int C, AT* __restrict__ mu,
-    float* __restrict__ S, unsigned* __restrict__ cmax) {
+__global__ void __launch_bounds__(kLeafThreads) k_refit_leaves(
+    int64_t n, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
+    const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ count,
+    const AT* __restrict__ attrs, int C, AT* __restrict__ mu, float* __restrict__ S,
+    unsigned* __restrict__ cmax) {
     constexpr int SR = srow(CP);
+    constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
+    constexpr int RW = CH + 3;           // staged row: CH attributes, then A n
+    __shared__ float row[kLeafThreads * RW];
     __shared__ unsigned smax[3 * CP];
     for (int j = threadIdx.x; j < 3 * CP; j += blockDim.x) smax[j] = 0u;
-    __syncthreads();
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < nn;
-         t0 += (int64_t)gridDim.x * blockDim.x) {
-        if (!is_leaf[t0]) continue;
-        const int64_t f = first[t0], k = count[t0];
-        for (int64_t m = f; m < f + k; ++m) {
-            const int64_t o = perm[m];
+    const int tid = threadIdx.x;
+    for (int64_t m0 = (int64_t)blockIdx.x * kLeafThreads; m0 < n;
+         m0 += (int64_t)gridDim.x * kLeafThreads) {
+        const int64_t m = m0 + tid;
+        const bool valid = m < n;
+        const int64_t o = valid ? (int64_t)perm[m] : 0;
+        const float4 w = valid ? pts[m].w : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int32_t leaf = valid ? leaf_of[m] : -1;
+        const bool head = valid && (m == 0 || leaf_of[m - 1] != leaf);
+        const int k = head ? count[leaf] : 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < CP; c0 += CH) {
+            __syncthreads();  // the previous chunk's sums have read the rows
 #pragma unroll
-            for (int c = 0; c < CP; ++c) mu[m * CP + c] = c < C ? attrs[o * C + c] : from_f<AT>(0.0f);
-        }
-#pragma unroll
-        for (int c0 = 0; c0 < CP; c0 += 4) {
-            float sacc[12];
-#pragma unroll
-            for (int j = 0; j < 12; ++j) sacc[j] = 0.0f;
-            for (int64_t m = f; m < f + k; ++m) {
-                const float4 w = pts[m].w;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c0 + c >= CP) break;
-                    const float v = to_f<AT>(mu[m * CP + c0 + c]);
-                    sacc[3 * c] = fmaf(w.x, v, sacc[3 * c]);
-                    sacc[3 * c + 1] = fmaf(w.y, v, sacc[3 * c + 1]);
-                    sacc[3 * c + 2] = fmaf(w.z, v, sacc[3 * c + 2]);
-                }
+            for (int c = 0; c < CH; ++c) {
+                const AT a = (valid && c0 + c < C) ? attrs[o * C + c0 + c] : from_f<AT>(0.0f);
+                if (valid) mu[m * CP + c0 + c] = a;
+                row[tid * RW + c] = to_f<AT>(a);
             }
+            row[tid * RW + CH] = w.x;
+            row[tid * RW + CH + 1] = w.y;
+            row[tid * RW + CH + 2] = w.z;
+            __syncthreads();
+            if (head) {
+                float sacc[3 * CH];
 #pragma unroll
-            for (int j = 0; j < 12; ++j) {
-                if (3 * c0 + j >= 3 * CP) break;
-                S[t0 * SR + 3 * c0 + j] = sacc[j];
-                const unsigned bits = __float_as_uint(fabsf(sacc[j]));
-                if (bits) atomicMax(&smax[3 * c0 + j], bits);
+                for (int j = 0; j < 3 * CH; ++j) sacc[j] = 0.0f;
+                for (int i = 0; i < k; ++i) {
+                    float v[CH], wx, wy, wz;
+                    if (tid + i < kLeafThreads) {
+                        const float* r = row + (tid + i) * RW;
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) v[c] = r[c];
+                        wx = r[CH]; wy = r[CH + 1]; wz = r[CH + 2];
+                    } else {  // past the block's points
+                        const int64_t mi = m + i;
+                        const int64_t oi = perm[mi];
+#pragma unroll
+                        for (int c = 0; c < CH; ++c)
+                            v[c] = c0 + c < C ? to_f<AT>(attrs[oi * C + c0 + c]) : 0.0f;
+                        const float4 wi = pts[mi].w;
+                        wx = wi.x; wy = wi.y; wz = wi.z;
+                    }
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        sacc[3 * c] = fmaf(wx, v[c], sacc[3 * c]);
+                        sacc[3 * c + 1] = fmaf(wy, v[c], sacc[3 * c + 1]);
+                        sacc[3 * c + 2] = fmaf(wz, v[c], sacc[3 * c + 2]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 3 * CH; ++j) {
+                    S[(int64_t)leaf * SR + 3 * c0 + j] = sacc[j];
+                    const unsigned bits = __float_as_uint(fabsf(sacc[j]));
+                    if (bits) atomicMax(&smax[3 * c0 + j], bits);
+                }
             }
         }
     }
@@ -176,10 +261,43 @@ __device__ __forceinline__ void block_exclusive_i64(long long (&v)[V], long long
     __syncthreads();
 }
 
-// Tile b = nodes [b kRefitTile, (b + 1) kRefitTile): the fixed-point sum of its
-// leaf moments per column.  The last tile to finish (an arrival counter; no
-// block waits for another) scans the tile sums into tile offsets, publishes
-// the column exponents and clears cmax and the counter for the next refit.
+// Leaf flags of nodes base .. base + kRefitPer (base a multiple of 4; false
+// past nn).
+__device__ __forceinline__ void leaf_flags(const int32_t* __restrict__ is_leaf, int64_t nn,
+                                           int64_t base, bool (&lf)[kRefitPer]) {
+    static_assert(kRefitPer == 4, "one int4 per thread");
+    if (base + 3 < nn) {
+        const int4 q = *reinterpret_cast<const int4*>(is_leaf + base);
+        lf[0] = q.x != 0; lf[1] = q.y != 0; lf[2] = q.z != 0; lf[3] = q.w != 0;
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRefitPer; ++r) lf[r] = base + r < nn && is_leaf[base + r] != 0;
+    }
+}
+
+// Sum over the thread's kRefitPer nodes of their fixed-point leaf moments,
+// columns j0 .. j0 + V.
+template <int SR, int V>
+__device__ __forceinline__ void thread_fixed_sum(const float* __restrict__ S, int64_t base,
+                                                 const bool (&lf)[kRefitPer], int j0,
+                                                 const int* sk, long long (&v)[V]) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) v[j] = 0;
+#pragma unroll
+    for (int r = 0; r < kRefitPer; ++r) {
+        if (!lf[r]) continue;
+        float x[V];
+        load_cols<SR, V>(S, base + r, j0, x);
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] += to_fixed(x[j], sk[j0 + j]);
+    }
+}
+
+// Tile b = nodes [b kRefitTile, (b + 1) kRefitTile), kRefitPer consecutive
+// nodes per thread: the fixed-point sum of its leaf moments per column.  The
+// last tile to finish (an arrival counter; no block waits for another) scans
+// the tile sums into tile offsets, publishes the column exponents and clears
+// cmax and the counter for the next refit.
 template <int CP>
 __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
     int64_t nn, const int32_t* __restrict__ is_leaf, const float* __restrict__ S,
@@ -195,17 +313,12 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRefitTile + (int64_t)threadIdx.x * kRefitPer;
     const int ntiles = gridDim.x;
+    bool lf[kRefitPer];
+    leaf_flags(is_leaf, nn, base, lf);
 #pragma unroll 1
     for (int j0 = 0; j0 < NC; j0 += V) {
         long long v[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = 0;
-        for (int r = 0; r < kRefitPer; ++r) {
-            const int64_t t = base + r;
-            if (t >= nn || !is_leaf[t]) continue;
-#pragma unroll
-            for (int j = 0; j < V; ++j) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
-        }
+        thread_fixed_sum<SR, V>(S, base, lf, j0, sk, v);
         block_sum_i64<V>(v, red);
         if (threadIdx.x == 0) {
 #pragma unroll
@@ -217,21 +330,27 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // exclusive scan of the tile sums, one warp per column, 32 tiles a round
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < NC; j += kRefitThreads / 32) {
-        long long carry = 0;
-        for (int b0 = 0; b0 < ntiles; b0 += 32) {
-            const int b = b0 + lane;
-            const long long x = b < ntiles ? __ldcg(tsum + (int64_t)b * NC + j) : 0ll;
-            long long inc = x;
+    // exclusive scan of the tile sums: thread i takes a run of seg tiles
+    const int seg = (ntiles + kRefitThreads - 1) / kRefitThreads;
+    const int b0 = threadIdx.x * seg, b1 = min(b0 + seg, ntiles);
+#pragma unroll 1
+    for (int j0 = 0; j0 < NC; j0 += V) {
+        long long v[V];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += u;
+        for (int j = 0; j < V; ++j) v[j] = 0;
+        for (int b = b0; b < b1; ++b) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) v[j] += __ldcg(tsum + (int64_t)b * NC + j0 + j);
+        }
+        block_exclusive_i64<V>(v, red);
+        for (int b = b0; b < b1; ++b) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                long long* e = tsum + (int64_t)b * NC + j0 + j;
+                const long long x = __ldcg(e);
+                *e = v[j];
+                v[j] += x;
             }
-            if (b < ntiles) tsum[(int64_t)b * NC + j] = carry + inc - x;
-            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
     }
     for (int j = threadIdx.x; j < NC; j += blockDim.x) {
@@ -241,11 +360,13 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
     if (threadIdx.x == 0) *done = 0u;
 }
 
-// P[t] for the tile's nodes (and P[nn], the total): the tile's offset plus the
-// exclusive prefix of the leaf moments inside the tile.
+// P for the tile's nodes (and P[nn], the total): the tile's offset plus the
+// exclusive prefix inside the tile.  P is column-major with leading dimension
+// ldP (a multiple of 4), so a thread's four nodes are 32 contiguous bytes of
+// each column.
 template <int CP>
 __global__ void __launch_bounds__(kRefitThreads) k_refit_prefix(
-    int64_t nn, const int32_t* __restrict__ is_leaf, const float* __restrict__ S,
+    int64_t nn, int64_t ldP, const int32_t* __restrict__ is_leaf, const float* __restrict__ S,
     const int* __restrict__ kexp, const long long* __restrict__ toff, long long* __restrict__ P) {
     constexpr int SR = srow(CP), NC = 3 * CP;
     constexpr int V = NC < kFixChunk ? NC : kFixChunk;
@@ -254,33 +375,35 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_prefix(
     for (int j = threadIdx.x; j < NC; j += blockDim.x) sk[j] = kexp[j];
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRefitTile + (int64_t)threadIdx.x * kRefitPer;
+    bool lf[kRefitPer];
+    leaf_flags(is_leaf, nn, base, lf);
 #pragma unroll 1
     for (int j0 = 0; j0 < NC; j0 += V) {
         long long v[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = 0;
-        for (int r = 0; r < kRefitPer; ++r) {
-            const int64_t t = base + r;
-            if (t >= nn || !is_leaf[t]) continue;
-#pragma unroll
-            for (int j = 0; j < V; ++j) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
-        }
+        thread_fixed_sum<SR, V>(S, base, lf, j0, sk, v);
         block_exclusive_i64<V>(v, red);
+        if (base >= nn) continue;
 #pragma unroll
-        for (int j = 0; j < V; ++j) v[j] += toff[(int64_t)blockIdx.x * NC + j0 + j];
-        for (int r = 0; r < kRefitPer; ++r) {
-            const int64_t t = base + r;
-            if (t >= nn) break;
-            const bool lf = is_leaf[t] != 0;
+        for (int j = 0; j < V; ++j) {
+            long long own[kRefitPer];
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                P[t * NC + j0 + j] = v[j];
-                if (lf) v[j] += to_fixed(S[t * SR + j0 + j], sk[j0 + j]);
+            for (int r = 0; r < kRefitPer; ++r)  // rows read above: L1 hits
+                own[r] = lf[r] ? to_fixed(S[(base + r) * SR + j0 + j], sk[j0 + j]) : 0ll;
+            long long* col = P + (int64_t)(j0 + j) * ldP;
+            long long q0 = v[j] + toff[(int64_t)blockIdx.x * NC + j0 + j];
+            const long long q1 = q0 + own[0], q2 = q1 + own[1], q3 = q2 + own[2];
+            if (base + 3 < nn) {
+                reinterpret_cast<longlong2*>(col + base)[0] = make_longlong2(q0, q1);
+                reinterpret_cast<longlong2*>(col + base)[1] = make_longlong2(q2, q3);
+            } else {
+                const long long q[4] = {q0, q1, q2, q3};
+#pragma unroll
+                for (int r = 0; r < kRefitPer; ++r)
+                    if (base + r < nn) col[base + r] = q[r];
             }
-            if (t == nn - 1) {
-#pragma unroll
-                for (int j = 0; j < V; ++j) P[nn * NC + j0 + j] = v[j];
-            }
+            const int64_t lastr = nn - 1 - base;  // the thread holding node nn - 1 writes P[nn]
+            if (lastr >= 0 && lastr < kRefitPer)
+                col[nn] = lastr == 0 ? q1 : lastr == 1 ? q2 : lastr == 2 ? q3 : q3 + own[3];
         }
     }
 }
@@ -288,7 +411,7 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_prefix(
 // Internal nodes: S_t = P[skip[t]] - P[t], back to float.
 template <int CP>
 __global__ void __launch_bounds__(128) k_refit_internal(
-    int64_t nn, const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ skip,
+    int64_t nn, int64_t ldP, const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ skip,
     const int* __restrict__ kexp, const long long* __restrict__ P, float* __restrict__ S) {
     constexpr int SR = srow(CP), NC = 3 * CP;
     __shared__ int sk[NC];
@@ -299,10 +422,11 @@ __global__ void __launch_bounds__(128) k_refit_internal(
         if (is_leaf[t]) continue;
         int64_t e = skip[t];
         if (e < t || e > nn) e = t;  // only an imported, corrupt tree gets here
-        const long long* hi = P + e * NC;
-        const long long* lo = P + t * NC;
 #pragma unroll 4
-        for (int j = 0; j < NC; ++j) S[t * SR + j] = from_fixed(hi[j] - lo[j], sk[j]);
+        for (int j = 0; j < NC; ++j) {
+            const long long* col = P + (int64_t)j * ldP;
+            S[t * SR + j] = from_fixed(col[e] - col[t], sk[j]);
+        }
     }
 }
 
@@ -435,19 +559,21 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     int64_t cap = (int64_t)num_sms() * 16;
     const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
     const unsigned ntiles = (unsigned)((t->nn + kRefitTile - 1) / kRefitTile);
+    const int64_t pblocks = (t->n + kLeafThreads - 1) / kLeafThreads, pcap = (int64_t)num_sms() * 8;
     note_launch();
-    k_refit_leaves<CP, AT><<<grid, 128, 0, s>>>(t->nn, t->pts, t->perm, t->first, t->count,
-                                                t->is_leaf, (const AT*)attrs, t->C, (AT*)t->mu,
-                                                t->S, t->fix_cmax);
+    k_refit_leaves<CP, AT><<<(unsigned)(pblocks < pcap ? pblocks : pcap), kLeafThreads, 0, s>>>(
+        t->n, t->pts, t->perm, t->leaf_of, t->count, (const AT*)attrs, t->C, (AT*)t->mu, t->S,
+        t->fix_cmax);
     note_launch();
     k_refit_tiles<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, t->is_leaf, t->S, t->fix_cmax,
                                                        t->fix_kexp, t->fix_tsum, t->fix_done);
+    const int64_t ldP = fix_ld(t->nn);
     note_launch();
-    k_refit_prefix<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, t->is_leaf, t->S, t->fix_kexp,
+    k_refit_prefix<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, ldP, t->is_leaf, t->S, t->fix_kexp,
                                                         t->fix_tsum, t->fix_P);
     note_launch();
-    k_refit_internal<CP><<<grid, 128, 0, s>>>(t->nn, t->is_leaf, t->skip, t->fix_kexp, t->fix_P,
-                                              t->S);
+    k_refit_internal<CP><<<grid, 128, 0, s>>>(t->nn, ldP, t->is_leaf, t->skip, t->fix_kexp,
+                                              t->fix_P, t->S);
 }
 
 template <int CP>
@@ -490,7 +616,7 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dS, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dmu, sizeof(float) * (size_t)t->n * Cp, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_P, sizeof(long long) * ((size_t)t->nn + 1) * NC, s));
+        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_P, sizeof(long long) * (size_t)fix_ld(t->nn) * NC, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_tsum, sizeof(long long) * ntiles * NC, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_cmax, sizeof(unsigned) * NC, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_kexp, sizeof(int) * NC, s));

@@ -45,7 +45,7 @@ struct dipole_tree {
     void* mu = nullptr;          // [n, Cp] float or bf16, Morton order
     float* S = nullptr;          // [nn, 3 Cp]
     // refit scratch: fixed-point prefix of the leaf moments over preorder
-    long long* fix_P = nullptr;     // [nn + 1, 3 Cp]
+    long long* fix_P = nullptr;     // [3 Cp, nn + 1 rounded up to 4], column-major
     long long* fix_tsum = nullptr;  // [tiles, 3 Cp] tile sums, then tile offsets
     unsigned* fix_cmax = nullptr;   // [3 Cp] largest |leaf moment| (float bits), 0 between refits
     int* fix_kexp = nullptr;        // [3 Cp] column scale exponents
