@@ -197,6 +197,39 @@ __device__ __forceinline__ void adjoint_point_reduce(float k, const float* gp, f
     if (lane_owns<CH>(lane) && a0 != 0.0f) atomicAdd(dst + kept, a0);
 }
 
+// Two opened-leaf points at once: ka, kb the lanes' kernel values for points
+// a and b; adds sum over lanes of ka g^c into dst_a[c] and of kb g^c into
+// dst_a[stride + c] (b's row; skipped when !two).  The channel exchanges are
+// those of adjoint_point_reduce; bit B then splits the pair (one shuffle)
+// where each point alone would need a full butterfly: 9 shuffles for two
+// points at CH = 4 instead of 12.
+template <int CH>
+__device__ __forceinline__ void adjoint_point_pair_reduce(float ka, float kb, const float* gp,
+                                                          float* dst_a, int stride, bool two,
+                                                          int kept, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float a0 = ka * gp[0], b0 = kb * gp[0];
+    if constexpr (CH == 4) {
+        float a1 = ka * gp[1], b1 = kb * gp[1];
+        a0 += __shfl_xor_sync(FULL, ka * gp[2], 16);
+        a1 += __shfl_xor_sync(FULL, ka * gp[3], 16);
+        b0 += __shfl_xor_sync(FULL, kb * gp[2], 16);
+        b1 += __shfl_xor_sync(FULL, kb * gp[3], 16);
+        a0 += __shfl_xor_sync(FULL, a1, 8);
+        b0 += __shfl_xor_sync(FULL, b1, 8);
+    } else if constexpr (CH == 2) {
+        a0 += __shfl_xor_sync(FULL, ka * gp[1], 16);
+        b0 += __shfl_xor_sync(FULL, kb * gp[1], 16);
+    }
+    constexpr int B = CH == 4 ? 4 : CH == 2 ? 8 : 16;
+    const bool hb = (lane & B) != 0;
+    float r = (hb ? b0 : a0) + __shfl_xor_sync(FULL, hb ? a0 : b0, B);
+#pragma unroll
+    for (int off = B / 2; off > 0; off >>= 1) r += __shfl_xor_sync(FULL, r, off);
+    if ((lane & (B - 1)) == 0 && (two || !hb) && r != 0.0f)
+        atomicAdd(dst_a + (hb ? stride : 0) + kept, r);
+}
+
 // Generalized forms of the two reductions above: the lane supplies its values
 // already in lane_channel_order (v[3i + k] for channel ord[i], axis k).
 template <int CH>

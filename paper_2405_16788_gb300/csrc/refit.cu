@@ -325,8 +325,10 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
             for (int j = 0; j < V; ++j) tsum[(int64_t)blockIdx.x * NC + j0 + j] = v[j];
         }
     }
-    __threadfence();
-    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == (unsigned)ntiles - 1u;
+    if (threadIdx.x == 0) {  // the only writer of this block's sums
+        __threadfence();
+        last = atomicAdd(done, 1u) == (unsigned)ntiles - 1u;
+    }
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -344,12 +346,14 @@ __global__ void __launch_bounds__(kRefitThreads) k_refit_tiles(
         }
         block_exclusive_i64<V>(v, red);
         for (int b = b0; b < b1; ++b) {
+            long long* e = tsum + (int64_t)b * NC + j0;
+            long long x[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) x[j] = __ldcg(e + j);  // all loads before the stores
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                long long* e = tsum + (int64_t)b * NC + j0 + j;
-                const long long x = __ldcg(e);
-                *e = v[j];
-                v[j] += x;
+                e[j] = v[j];
+                v[j] += x[j];
             }
         }
     }

@@ -211,19 +211,36 @@ k_query(const QueryArgs a) {
                     }
                 }
 
-                if (__any_sync(FULL, open_leaf)) {
+                // opened-leaf point term: the dipole kernel times A_m n_m . (p_m - x)
+                auto point_k = [&](const PointRec& pr) {
+                    float k = 0.f;
+                    if (open_leaf) {
+                        const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
+                        const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        if (r2 > 0.f)
+                            k = radial_over_d3(r2, pr.geo.w, KERN) *
+                                fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
+                    }
+                    return k;
+                };
+                if (MODE == kAdjoint && __any_sync(FULL, open_leaf)) {
+                    // opened leaf, points in pairs (adjoint_point_pair_reduce)
+                    const int f = meta.y, cnt = meta.z;
+                    for (int j = 0; j < cnt; j += 2) {
+                        const bool two = j + 1 < cnt;
+                        const float ka = point_k(pts[f + j]);
+                        const float kb = two ? point_k(pts[f + j + 1]) : 0.f;
+                        float* dst = a.dmu + (size_t)(f + j) * CP;
+#pragma unroll
+                        for (int c0 = 0; c0 < CP; c0 += CH)
+                            adjoint_point_pair_reduce<CH>(ka, kb, g + c0, dst + c0, CP, two, ord[0],
+                                                          lane);
+                    }
+                } else if (MODE != kAdjoint && __any_sync(FULL, open_leaf)) {
                     // opened leaf: exact sum over its points (eq. dipole_sum)
                     const int f = meta.y, cnt = meta.z;
                     for (int j = 0; j < cnt; ++j) {
-                        const PointRec pr = pts[f + j];
-                        float k = 0.f;
-                        if (open_leaf) {
-                            const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
-                            const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                            if (r2 > 0.f)
-                                k = radial_over_d3(r2, pr.geo.w, KERN) *
-                                    fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
-                        }
+                        const float k = point_k(pts[f + j]);
                         if (MODE == kForward) {
                             const AT* mrow = reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * CP;
 #pragma unroll
@@ -234,11 +251,6 @@ k_query(const QueryArgs a) {
                                 for (int c = 0; c < CH; ++c)
                                     if (open_leaf) add_term(c0 + c, k * m[c]);
                             }
-                        } else if (MODE == kAdjoint) {
-                            float* dst = a.dmu + (size_t)(f + j) * CP;
-#pragma unroll
-                            for (int c0 = 0; c0 < CP; c0 += CH)
-                                adjoint_point_reduce<CH>(k, g + c0, dst + c0, ord[0], lane);
                         }
                     }
                 }
