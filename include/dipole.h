@@ -143,7 +143,9 @@ int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t
  *   beta    > 0 (larger is more accurate; the paper gives no value)
  *   out     [q, channels] float (channels of the last refit)
  *
- * Queries are sorted by Morton code internally.  Reentrant: concurrent
+ * Queries are sorted internally along a Hilbert curve through the tree's
+ * cube (cells of 2^-5 of its side), so that the 32 queries of a warp are
+ * neighbours.  Reentrant: concurrent
  * forward calls on one tree are allowed.  Errors: DIPOLE_ESTATE before the
  * first refit; DIPOLE_EINVAL for null pointers or beta <= 0.
  */
@@ -200,7 +202,7 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
 
 /*
  * Forward and adjoint sharing a query plan (caller-owned device buffers):
- *   plan_perm [q]                  uint32, written by dipole_forward_planned: the Morton
+ *   plan_perm [q]                  uint32, written by dipole_forward_planned: the sorted
  *                                  order of the queries (a permutation of [0, q))
  *   plan_cost [8 * ceil(q / 32)]   uint32, written by dipole_forward_planned: 8 words per
  *                                  32-query packet: its traversal steps, the nodes its walk

@@ -56,6 +56,63 @@ struct TreeView {
     int* status;
 };
 
+// ---------------------------------------------------------- cube cells
+// Cell (10 bits per axis) of a point in the tree's bounding cube, clamped to
+// it: floor((x - lo) s) with one rounding per operation; cvt.rzi.u32
+// saturates negatives and NaN to 0.
+__device__ __forceinline__ void cube_cell(float x, float y, float z, const float* bbox,
+                                          uint32_t& qx, uint32_t& qy, uint32_t& qz) {
+    const float s = bbox[4];
+    qx = min(__float2uint_rz(__fmul_rn(__fsub_rn(x, bbox[0]), s)), 1023u);
+    qy = min(__float2uint_rz(__fmul_rn(__fsub_rn(y, bbox[1]), s)), 1023u);
+    qz = min(__float2uint_rz(__fmul_rn(__fsub_rn(z, bbox[2]), s)), 1023u);
+}
+
+__device__ __forceinline__ uint32_t spread_bits10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// 30-bit Morton code: bit k of qx, qy, qz goes to bit 3k+2, 3k+1, 3k.
+__device__ __forceinline__ uint32_t morton30(uint32_t qx, uint32_t qy, uint32_t qz) {
+    return (spread_bits10(qx) << 2) | (spread_bits10(qy) << 1) | spread_bits10(qz);
+}
+
+// 30-bit index of the cell on the 3-D Hilbert curve of order 10, by
+// Skilling's transform ("Programming the Hilbert curve", AIP Conf. Proc. 707,
+// 2004): the axes are turned into the curve's transposed index in place, whose
+// bits, interleaved like a Morton code, are the index.  Consecutive indices
+// are face-adjacent cells, so a run of them stays more compact than a run of
+// Morton codes (which jump at every octant boundary).
+__device__ __forceinline__ uint32_t hilbert30(uint32_t qx, uint32_t qy, uint32_t qz) {
+    uint32_t x[3] = {qx, qy, qz};
+#pragma unroll
+    for (uint32_t Q = 1u << 9; Q > 1u; Q >>= 1) {
+        const uint32_t P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (x[i] & Q) {
+                x[0] ^= P;
+            } else {
+                const uint32_t t = (x[0] ^ x[i]) & P;
+                x[0] ^= t;
+                x[i] ^= t;
+            }
+        }
+    }
+    x[1] ^= x[0];
+    x[2] ^= x[1];
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t Q = 1u << 9; Q > 1u; Q >>= 1)
+        if (x[2] & Q) t ^= Q - 1u;
+    return morton30(x[0] ^ t, x[1] ^ t, x[2] ^ t);
+}
+
 // ---------------------------------------------------------------- sorting
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 // keys/vals are sorted in place; tmp buffers hold n entries each.  hist must
@@ -68,14 +125,14 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
 int64_t scan_tmp_entries(int64_t n);
 void exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s);
 
-// 30-bit Morton code (shifted right by `shift`) of each point in the tree's
-// bounding cube (clamped to it) and the identity permutation; codes/idx hold
-// q entries.
+// 30-bit Morton code (Hilbert index with `hilbert`), shifted right by
+// `shift`, of each point in the tree's bounding cube (clamped to it) and the
+// identity permutation; codes/idx hold q entries.
 void query_codes(const float* queries, int64_t q, const float* bbox, int shift, uint32_t* codes,
-                 uint32_t* idx, int* status, cudaStream_t s);
+                 uint32_t* idx, int* status, cudaStream_t s, bool hilbert = false);
 
-// Query sort key: the top 16 bits of the Morton code keep warps as coherent
-// as all 30 bits do and take two radix passes instead of four.
+// Query sort key: the top 16 bits of the Hilbert index keep warps about as
+// coherent as all 30 bits do and take two radix passes instead of four.
 constexpr int kQueryKeyBits = 16;
 
 int num_sms();

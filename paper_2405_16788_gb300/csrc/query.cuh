@@ -43,7 +43,7 @@ struct QueryArgs {
     float* dgeo;        // [n, 4] opened-leaf normal (xyz) and radius (w) terms (kAdjointGeom)
     int32_t* counts;
     unsigned long long* work;
-    const uint32_t* porder;  // packet (or item) order, or NULL for Morton order
+    const uint32_t* porder;  // packet (or item) order, or NULL for sorted order
     GridSpec grid;           // dense-grid queries instead of q / qperm
     uint32_t* plan;          // query plan being written (forward): kPlanWords per packet
     const uint4* items;      // ranged work items {packet, lo, hi, part}, read in porder if set

@@ -135,28 +135,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
 }
 
-__device__ __forceinline__ uint32_t spread_bits10(uint32_t v) {
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
 __global__ void k_query_codes(const float* __restrict__ q, int64_t nq, const float* __restrict__ bbox,
                               int shift, uint32_t* __restrict__ codes, uint32_t* __restrict__ idx,
-                              int* status) {
-    const float lo0 = bbox[0], lo1 = bbox[1], lo2 = bbox[2], s = bbox[4];
+                              int* status, int hilbert) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float x = q[3 * i], y = q[3 * i + 1], z = q[3 * i + 2];
+        const float x = q[3 * i], y = q[3 * i + 1], z = q[3 * i + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(status, kStatusNonFinite);
-        // clamp to the cube: cvt.rzi.u32 saturates negatives and NaN to 0
-        uint32_t qx = min(__float2uint_rz(__fmul_rn(__fsub_rn(x, lo0), s)), 1023u);
-        uint32_t qy = min(__float2uint_rz(__fmul_rn(__fsub_rn(y, lo1), s)), 1023u);
-        uint32_t qz = min(__float2uint_rz(__fmul_rn(__fsub_rn(z, lo2), s)), 1023u);
-        codes[i] = ((spread_bits10(qx) << 2) | (spread_bits10(qy) << 1) | spread_bits10(qz)) >> shift;
+        uint32_t qx, qy, qz;
+        cube_cell(x, y, z, bbox, qx, qy, qz);
+        codes[i] = (hilbert ? hilbert30(qx, qy, qz) : morton30(qx, qy, qz)) >> shift;
         idx[i] = (uint32_t)i;
     }
 }
@@ -250,12 +238,12 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
 }
 
 void query_codes(const float* queries, int64_t q, const float* bbox, int shift, uint32_t* codes,
-                 uint32_t* idx, int* status, cudaStream_t s) {
+                 uint32_t* idx, int* status, cudaStream_t s, bool hilbert) {
     if (q <= 0) return;
     int64_t blocks = (q + 255) / 256;
     int64_t cap = (int64_t)num_sms() * 8;
-    note_launch(); k_query_codes<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(queries, q, bbox, shift,
-                                                                           codes, idx, status);
+    note_launch(); k_query_codes<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
+        queries, q, bbox, shift, codes, idx, status, hilbert ? 1 : 0);
 }
 
 }  // namespace dip

@@ -1,8 +1,8 @@
 // Barnes-Hut primal and adjoint queries (Alg. 1; Sec. 6.1, eq. farfield;
 // Sec. 6.2 and App. C, eq. farfield_gradient).
 //
-// Persistent, warp-cooperative, stackless traversal.  Queries are sorted by
-// Morton code, so the 32 queries of a warp are neighbours.  The tree is in
+// Persistent, warp-cooperative, stackless traversal.  Queries are sorted
+// along a Hilbert curve, so the 32 queries of a warp are neighbours.  The tree is in
 // depth-first preorder with skip indices: a query at node t moves to skip[t]
 // when t is far or a leaf, else to t+1 (its first child).  Every lane keeps
 // its own next node; the warp visits the smallest of them, so all lanes that
@@ -56,7 +56,7 @@ k_query(const QueryArgs a) {
             half = it.w;
         } else {
             if ((int64_t)pk * 32 >= a.nq) break;
-            pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // Morton packet index
+            pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // packet index in sorted order
         }
         bool valid;
         int64_t qo;
@@ -420,23 +420,33 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n,
     return lo;
 }
 
-// The forward's two items per packet: the walk is cut at the leaf holding the
-// middle point (Morton order) of those whose codes fall in the packet's code
-// range, which puts about half of a packet's near-field work on each side.
-// Both go to the bucket of that point count (a proxy of the walk's length).
-// The cut is also written to the plan (word 4) when one is recorded.
-__global__ void k_fwd_items(const uint32_t* qkeys, int64_t q, int64_t np, int key_shift,
-                            const uint32_t* pcode, int64_t n, const int32_t* leaf_of, unsigned nn,
-                            uint4* items, unsigned* n_items, uint32_t* plan, uint32_t* ibucket,
-                            uint32_t* ostate) {
+// The forward's two items per packet (one warp per packet): the walk is cut
+// at the leaf holding the middle point (Morton order) of those whose codes lie
+// between the smallest and largest Morton code of the packet's queries, which
+// puts about half of the packet's near-field work on each side.  Both items go
+// to the bucket of that point count (a proxy of the walk's length).  The cut
+// is also written to the plan (word 4) when one is recorded.
+__global__ void k_fwd_items(const float* q, const uint32_t* qperm, int64_t nq, int64_t np,
+                            const float* bbox, const uint32_t* pcode, int64_t n,
+                            const int32_t* leaf_of, unsigned nn, uint4* items, unsigned* n_items,
+                            uint32_t* plan, uint32_t* ibucket, uint32_t* ostate) {
     __shared__ uint32_t sh[kOrderBuckets];
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) sh[b] = 0u;
     __syncthreads();
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t first = p * 32, last = min(q, first + 32) - 1;
-        const uint32_t cmin = qkeys[first] << key_shift;
-        const uint32_t cmax = ((qkeys[last] + 1u) << key_shift) - 1u;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < np; p += warps) {
+        const int64_t i = p * 32 + lane;
+        uint32_t cmin = 0xffffffffu, cmax = 0u;
+        if (i < nq) {
+            const int64_t o = qperm[i];
+            uint32_t qx, qy, qz;
+            cube_cell(q[3 * o], q[3 * o + 1], q[3 * o + 2], bbox, qx, qy, qz);
+            cmin = cmax = morton30(qx, qy, qz);
+        }
+        cmin = __reduce_min_sync(0xffffffffu, cmin);
+        cmax = __reduce_max_sync(0xffffffffu, cmax);
+        if (lane != 0) continue;
         const int64_t ilo = lower_bound_u32(pcode, n, cmin);
         const int64_t ihi = lower_bound_u32(pcode, n, cmax + 1u);
         const int64_t imid = min((ilo + ihi) / 2, n - 1);
@@ -567,7 +577,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     unsigned long long* work = reinterpret_cast<unsigned long long*>(hist + kNoAllocHistEntries);
     // the previous call's contents stay in the array: only the counter must start at 0
     DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
-    query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+    query_codes(queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s, true);
     radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
     QueryArgs a;
     a.nodes = t->nodes;
@@ -593,7 +603,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.dgeo = nullptr;
     a.counts = nullptr;
     a.work = work;
-    a.porder = nullptr;  // Morton packet order
+    a.porder = nullptr;  // packets in sorted order
     a.plan = nullptr;
     a.items = nullptr;
     a.n_items = nullptr;
@@ -624,16 +634,17 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
         DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
         if (plan_in) {
-            idx = plan_perm;  // the Morton order computed by the forward on these queries
+            idx = plan_perm;  // the query order computed by the forward on these queries
         } else {
-            // Morton order of the queries: codes in the tree's cube, sorted with their indices
+            // query order: Hilbert indices of the cells in the tree's cube, sorted with the
+            // query indices (runs of the Hilbert curve are compact, so packets are too)
             if (plan_perm) idx = plan_perm;
             else DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
-            query_codes(call.queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s);
+            query_codes(call.queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s, true);
             radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
         }
     }
-    // Scheduling.  Packets run in Morton order, each recording its warp steps
+    // Scheduling.  Packets run in sorted order, each recording its warp steps
     // into the plan when one is given; a call that reads a plan runs the
     // packets longest first from those records.  The record only changes the
     // order of the packets, never a result.
@@ -677,8 +688,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         if (call.gout)
             DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
         note_launch();
-        k_fwd_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(
-            codes, q, np, 30 - kQueryKeyBits, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
+        k_fwd_items<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(
+            call.queries, idx, q, np, t->bbox, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
             n_items, plan_w, ibucket, ostate);
         order_place(ibucket, ni, ostate, iorder, s);
         porder = iorder;
