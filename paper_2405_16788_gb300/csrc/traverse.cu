@@ -147,7 +147,8 @@ k_query(const QueryArgs a) {
         for (;;) {
             const unsigned n = __reduce_min_sync(FULL, next);
             if (n >= hi) break;
-            if (++steps > nn) {  // a well-formed tree needs at most nn steps
+            ++steps;
+            if (MODE != kForward && steps > nn) {  // a well-formed tree needs at most nn steps
                 if (lane == 0) atomicOr(a.status, kStatusTraversal);
                 break;
             }
@@ -255,6 +256,10 @@ k_query(const QueryArgs a) {
                     }
                 }
                 if (MODE == kForward && (steps % kFoldSteps) == 0u) {
+                    if (steps > nn) {  // the forward checks the bound every kFoldSteps steps
+                        if (lane == 0) atomicOr(a.status, kStatusTraversal);
+                        break;
+                    }
                     if (kBlocked) {
 #pragma unroll
                         for (int c = 0; c < CP; ++c) {

@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
             for (;;) {
                 const unsigned n = __reduce_min_sync(FULL, next);
                 if (n >= hi) break;
-                if (++gsteps > nn) {  // a well-formed tree needs at most nn steps
+                ++gsteps;
+                if (!FWD && gsteps > nn) {  // a well-formed tree needs at most nn steps
                     if (lane == 0) atomicOr(a.status, kStatusTraversal);
                     break;
                 }
@@ -427,6 +428,10 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                     }
                 }
                 if (FWD && (gsteps % kFoldSteps) == 0u) {
+                    if (gsteps > nn) {  // checked every kFoldSteps steps
+                        if (lane == 0) atomicOr(a.status, kStatusTraversal);
+                        break;
+                    }
 #pragma unroll
                     for (int i = 0; i < NV; ++i) {
                         kahan_add(acc[i], cmp[i], part[i]);
