@@ -177,32 +177,12 @@ __device__ __forceinline__ void adjoint_far_reduce(float vx, float vy, float vz,
     if ((lane & (B / 2 - 1)) == 0 && axis < 3 && r != 0.0f) atomicAdd(dst + 3 * kept + axis, r);
 }
 
-// Opened-leaf point: adds sum over lanes of k g^c into dst[c] for the chunk.
-template <int CH>
-__device__ __forceinline__ void adjoint_point_reduce(float k, const float* gp, float* dst, int kept,
-                                                     int lane) {
-    constexpr unsigned FULL = 0xffffffffu;
-    float a0 = k * gp[0];
-    if constexpr (CH == 4) {
-        float a1 = k * gp[1];
-        a0 += __shfl_xor_sync(FULL, k * gp[2], 16);
-        a1 += __shfl_xor_sync(FULL, k * gp[3], 16);
-        a0 += __shfl_xor_sync(FULL, a1, 8);
-    } else if constexpr (CH == 2) {
-        a0 += __shfl_xor_sync(FULL, k * gp[1], 16);
-    }
-#pragma unroll
-    for (int off = (CH == 4 ? 4 : CH == 2 ? 8 : 16); off > 0; off >>= 1)
-        a0 += __shfl_xor_sync(FULL, a0, off);
-    if (lane_owns<CH>(lane) && a0 != 0.0f) atomicAdd(dst + kept, a0);
-}
-
-// Two opened-leaf points at once: ka, kb the lanes' kernel values for points
-// a and b; adds sum over lanes of ka g^c into dst_a[c] and of kb g^c into
-// dst_a[stride + c] (b's row; skipped when !two).  The channel exchanges are
-// those of adjoint_point_reduce; bit B then splits the pair (one shuffle)
-// where each point alone would need a full butterfly: 9 shuffles for two
-// points at CH = 4 instead of 12.
+// Opened-leaf points, two at once: ka, kb the lanes' kernel values for
+// points a and b; adds sum over lanes of ka g^c into dst_a[c] and of kb g^c
+// into dst_a[stride + c] (b's row; skipped when !two).  The channel exchanges
+// are those of adjoint_far_reduce (one value per channel instead of three);
+// bit B then splits the pair (one shuffle) where each point alone would need a
+// full butterfly: 9 shuffles for two points at CH = 4 instead of 12.
 template <int CH>
 __device__ __forceinline__ void adjoint_point_pair_reduce(float ka, float kb, const float* gp,
                                                           float* dst_a, int stride, bool two,
@@ -230,7 +210,8 @@ __device__ __forceinline__ void adjoint_point_pair_reduce(float ka, float kb, co
         atomicAdd(dst_a + (hb ? stride : 0) + kept, r);
 }
 
-// Generalized forms of the two reductions above: the lane supplies its values
+// Generalized forms of the far-node reduction (a vector per channel) and of a
+// one-point reduction (a scalar per channel): the lane supplies its values
 // already in lane_channel_order (v[3i + k] for channel ord[i], axis k).
 template <int CH>
 __device__ __forceinline__ void adjoint_vec_reduce(const float (&v)[3 * CH], float* dst, int kept,

@@ -146,12 +146,13 @@ k_query(const QueryArgs a) {
         unsigned steps = 0;
         for (;;) {
             const unsigned n = __reduce_min_sync(FULL, next);
-            if (n >= hi) break;
-            ++steps;
-            if (MODE != kForward && steps > nn) {  // a well-formed tree needs at most nn steps
-                if (lane == 0) atomicOr(a.status, kStatusTraversal);
+            if (MODE == kForward) {
+                if (n >= hi) break;
+            } else if ((n >= hi) | (steps >= nn)) {  // a well-formed tree needs at most nn steps
+                if (n < hi && lane == 0) atomicOr(a.status, kStatusTraversal);
                 break;
             }
+            ++steps;
             const float4 geo = __ldg(&nodes[n].geo);
             const int4 meta = __ldg(&nodes[n].meta);
             const bool act = next == n;

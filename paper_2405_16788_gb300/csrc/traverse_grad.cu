@@ -268,12 +268,13 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
             unsigned gsteps = 0;
             for (;;) {
                 const unsigned n = __reduce_min_sync(FULL, next);
-                if (n >= hi) break;
-                ++gsteps;
-                if (!FWD && gsteps > nn) {  // a well-formed tree needs at most nn steps
-                    if (lane == 0) atomicOr(a.status, kStatusTraversal);
+                if (FWD) {
+                    if (n >= hi) break;
+                } else if ((n >= hi) | (gsteps >= nn)) {  // a well-formed tree needs at most nn steps
+                    if (n < hi && lane == 0) atomicOr(a.status, kStatusTraversal);
                     break;
                 }
+                ++gsteps;
                 const float4 geo = __ldg(&nodes[n].geo);
                 const int4 meta = __ldg(&nodes[n].meta);
                 const bool act = next == n;

@@ -209,3 +209,26 @@ def test_ranged_walk_edge_cases():
     ot.update(w.mu)
     ref_a = ot.adjoint(w.queries[100:101], 2.0, g.astype(np.float64).sum(0, keepdims=True))
     assert np.all(normwise(ga, ref_a) <= 1e-3)
+
+
+def test_big_path_outside_queries_and_repeatability():
+    """The two-item path (>= 65,536 queries, Hilbert-ordered packets, cost
+    buckets) with a ragged count, a fifth of the queries far outside the
+    tree's cube (clamped to its border cells by the sort key only), matches
+    the oracle; two calls give bitwise the same sums."""
+    w = syn.workload("scene-200k", scale=0.05)
+    rng = np.random.default_rng(21)
+    q = syn.uniform_box_queries(70001, seed=22)
+    far = rng.random(len(q)) < 0.2
+    q[far] *= np.float32(40.0)
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(w.mu))
+    qd = to_dev(q)
+    y1 = gt.forward(qd, 2.0).cpu().numpy()
+    y2 = gt.forward(qd, 2.0).cpu().numpy()
+    gt.sync_status()
+    assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    ot = oracle_tree(w.cloud)
+    ot.update(w.mu)
+    ref = ot.forward(q, 2.0)
+    assert np.all(normwise(y1, ref) <= TOL)
