@@ -416,14 +416,27 @@ __global__ void k_plan_items(const uint32_t* plan, int64_t np, unsigned nn, uint
     order_counts_flush(sh, ostate);
 }
 
-__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* v, int64_t n, uint32_t x) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (v[mid] < x) lo = mid + 1;
-        else hi = mid;
+// First index i in [0, n) with v[i] >= x (n if none), v sorted, found by
+// the 32 lanes of a warp together: each round every lane probes one of 32
+// evenly spaced positions and a ballot keeps the interval between the last
+// probe below x and the first at or above it (a 32-ary search: four rounds of
+// one load each for a million entries).  Must be called by all 32 lanes with
+// the same x; every lane gets the result.
+__device__ __forceinline__ int64_t warp_lower_bound_u32(const uint32_t* v, int64_t n, uint32_t x,
+                                                        int lane) {
+    int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + (int64_t)(lane + 1) * step - 1;
+        const bool below = p < hi && v[p] < x;
+        const int k = __popc(__ballot_sync(0xffffffffu, below));
+        const int64_t nlo = lo + (int64_t)k * step;
+        hi = min(nlo + step - 1, hi);  // v[lo + (k + 1) step - 1] >= x, or hi
+        lo = min(nlo, hi);
     }
-    return lo;
+    const int64_t p = lo + lane;
+    const bool below = p < hi && v[p] < x;
+    return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 
 // The forward's two items per packet (one warp per packet): the walk is cut
@@ -452,9 +465,9 @@ __global__ void k_fwd_items(const float* q, const uint32_t* qperm, int64_t nq, i
         }
         cmin = __reduce_min_sync(0xffffffffu, cmin);
         cmax = __reduce_max_sync(0xffffffffu, cmax);
+        const int64_t ilo = warp_lower_bound_u32(pcode, n, cmin, lane);
+        const int64_t ihi = warp_lower_bound_u32(pcode, n, cmax + 1u, lane);
         if (lane != 0) continue;
-        const int64_t ilo = lower_bound_u32(pcode, n, cmin);
-        const int64_t ihi = lower_bound_u32(pcode, n, cmax + 1u);
         const int64_t imid = min((ilo + ihi) / 2, n - 1);
         unsigned cut = (unsigned)leaf_of[imid];
         if (cut == 0u || cut >= nn) cut = nn;  // one item holds the whole walk
