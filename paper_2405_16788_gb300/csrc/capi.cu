@@ -33,11 +33,8 @@ void configure_pool_once() {
 }
 
 void free_tree_memory(dipole_tree* t) {
-    void* bufs[] = {t->pts,    t->code,    t->perm,   t->leaf_of, t->nodes,  t->first,
-                    t->count,  t->level,   t->parent, t->skip,    t->is_leaf, t->nchild,
-                    t->agg64,  t->eps_node, t->bbox,  t->status, t->mu,     t->S,
-                    t->dS,     t->dmu,     t->lvl_list, t->lvl_off, t->dE,    t->dgeo,
-                    t->fix_P,  t->fix_tsum, t->fix_cmax, t->fix_kexp, t->fix_done};
+    // the arrays live in these blocks, except the lazily made normal/radius scratch
+    void* bufs[] = {t->point_block, t->topo_block, t->node_block, t->attr_block, t->dE, t->dgeo};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }

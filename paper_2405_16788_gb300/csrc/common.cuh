@@ -113,6 +113,22 @@ __device__ __forceinline__ uint32_t hilbert30(uint32_t qx, uint32_t qy, uint32_t
     return morton30(x[0] ^ t, x[1] ^ t, x[2] ^ t);
 }
 
+// ------------------------------------------------------- memory blocks
+// Several arrays in one device allocation (each API call costs the host
+// microseconds): call the same sequence of take() twice, first with base ==
+// nullptr to size the block, then with the block; each array starts on a
+// 256-byte boundary.
+struct Carve {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void take(T** p, int64_t count) {
+        off = (off + 255) & ~size_t(255);
+        *p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+    }
+};
+
 // ---------------------------------------------------------------- sorting
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 // keys/vals are sorted in place; tmp buffers hold n entries each.  hist must

@@ -605,26 +605,29 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
     const int Cp = padded_channels(C);
     const int SR = srow(Cp);
     if (t->attr_Cp_alloc != Cp || t->attr_dtype_alloc != dtype) {
-        // (re)allocate the attribute state; previous buffers are freed in stream order
-        void* bufs[] = {t->mu, t->S, t->dS, t->dmu, t->fix_P, t->fix_tsum, t->fix_cmax,
-                        t->fix_kexp, t->fix_done};
-        for (void* b : bufs)
-            if (b) cudaFreeAsync(b, s);
-        t->mu = nullptr; t->S = nullptr; t->dS = nullptr; t->dmu = nullptr;
-        t->fix_P = nullptr; t->fix_tsum = nullptr; t->fix_cmax = nullptr; t->fix_kexp = nullptr;
-        t->fix_done = nullptr;
-        const size_t esz = dtype == 1 ? 2 : 4;
-        const size_t NC = 3 * (size_t)Cp;
-        const size_t ntiles = (size_t)((t->nn + kRefitTile - 1) / kRefitTile);
-        DIP_CUDA_TRY(cudaMallocAsync(&t->mu, esz * (size_t)t->n * Cp, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->S, sizeof(float) * (size_t)t->nn * SR, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dS, sizeof(float) * (size_t)t->nn * SR, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dmu, sizeof(float) * (size_t)t->n * Cp, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_P, sizeof(long long) * (size_t)fix_ld(t->nn) * NC, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_tsum, sizeof(long long) * ntiles * NC, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_cmax, sizeof(unsigned) * NC, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_kexp, sizeof(int) * NC, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&t->fix_done, sizeof(unsigned), s));
+        // (re)allocate the attribute state in one block; the previous one is freed in stream order
+        if (t->attr_block) cudaFreeAsync(t->attr_block, s);
+        t->attr_block = nullptr;
+        const int64_t NC = 3 * (int64_t)Cp;
+        const int64_t ntiles = (t->nn + kRefitTile - 1) / kRefitTile;
+        auto take = [&](Carve& c) {
+            unsigned char* mu = nullptr;
+            c.take(&mu, (dtype == 1 ? 2 : 4) * t->n * Cp);
+            t->mu = mu;
+            c.take(&t->S, t->nn * SR);
+            c.take(&t->dS, t->nn * SR);
+            c.take(&t->dmu, t->n * Cp);
+            c.take(&t->fix_P, fix_ld(t->nn) * NC);
+            c.take(&t->fix_tsum, ntiles * NC);
+            c.take(&t->fix_cmax, NC);
+            c.take(&t->fix_kexp, NC);
+            c.take(&t->fix_done, 1);
+        };
+        Carve c;
+        take(c);
+        DIP_CUDA_TRY(cudaMallocAsync(&t->attr_block, c.off, s));
+        c = Carve{static_cast<char*>(t->attr_block), 0};
+        take(c);
         DIP_CUDA_TRY(cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->fix_cmax, 0, sizeof(unsigned) * NC, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->fix_done, 0, sizeof(unsigned), s));

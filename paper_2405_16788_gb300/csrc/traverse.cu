@@ -644,21 +644,49 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     const int SR = srow(t->Cp > 0 ? t->Cp : 1);
     const int64_t np = (q + 31) / 32;
     uint32_t *codes = nullptr, *idx = nullptr, *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr;
-    unsigned long long* work = nullptr;
-    DIP_CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(unsigned long long), s));
+    uint32_t* own_idx = nullptr;
+    uint4* items = nullptr;
+    uint32_t *ibucket = nullptr, *iorder = nullptr;
+    uint32_t* small = nullptr;  // work counter (two words), item order state, item count
     const bool grid = call.grid_dim[0] > 0;
-    if (q > 0 && !grid) {
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&codes, sizeof(uint32_t) * q, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ktmp, sizeof(uint32_t) * q, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&vtmp, sizeof(uint32_t) * q, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&hist, sizeof(uint32_t) * radix_hist_entries(q), s));
+    const bool sorted = q > 0 && !grid;
+    const bool big = sorted && np >= kOrderMinPackets;
+    const bool adj_items = big && adjoint && plan_in && plan_cost;
+    const bool fwd_items = big && mode != kCount && !plan_in;
+    const int64_t ni = adj_items ? np * kPlanWords : fwd_items ? 2 * np : 0;
+    // one allocation for the call's scratch (each API call costs the host microseconds)
+    auto take = [&](Carve& c) {
+        c.take(&small, 2 + kOrderStateWords + 1);
+        if (sorted) {
+            c.take(&codes, q);
+            c.take(&ktmp, q);
+            c.take(&vtmp, q);
+            c.take(&hist, radix_hist_entries(q));
+            if (!plan_in && !plan_perm) c.take(&own_idx, q);
+        }
+        if (ni) {
+            c.take(&items, ni);
+            c.take(&ibucket, ni);
+            c.take(&iorder, ni);
+        }
+    };
+    Carve cs;
+    take(cs);
+    void* block = nullptr;
+    DIP_CUDA_TRY(cudaMallocAsync(&block, cs.off, s));
+    cs = Carve{static_cast<char*>(block), 0};
+    take(cs);
+    unsigned long long* work = reinterpret_cast<unsigned long long*>(small);
+    uint32_t* ostate = small + 2;
+    unsigned* n_items = ostate + kOrderStateWords;
+    DIP_CUDA_TRY(cudaMemsetAsync(small, 0, sizeof(uint32_t) * (2 + kOrderStateWords + 1), s));
+    if (sorted) {
         if (plan_in) {
             idx = plan_perm;  // the query order computed by the forward on these queries
         } else {
             // query order: Hilbert indices of the cells in the tree's cube, sorted with the
             // query indices (runs of the Hilbert curve are compact, so packets are too)
-            if (plan_perm) idx = plan_perm;
-            else DIP_CUDA_TRY(cudaMallocAsync((void**)&idx, sizeof(uint32_t) * q, s));
+            idx = plan_perm ? plan_perm : own_idx;
             query_codes(call.queries, q, t->bbox, 30 - kQueryKeyBits, codes, idx, t->status, s, true);
             radix_sort_pairs(codes, idx, ktmp, vtmp, hist, q, kQueryKeyBits, s);
         }
@@ -669,20 +697,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     // order of the packets, never a result.
     const uint32_t* porder = nullptr;
     uint32_t* plan_w = nullptr;  // the plan this forward records
-    uint4* items = nullptr;
-    unsigned* n_items = nullptr;
-    uint32_t *ibucket = nullptr, *iorder = nullptr, *ostate = nullptr;
-    const bool big = q > 0 && !grid && np >= kOrderMinPackets;
-    if (big && (mode == kAdjoint || mode == kAdjointGrad || mode == kAdjointGeom) && plan_in &&
-        plan_cost) {
+    if (adj_items) {
         // ranged items from the walk cuts recorded by the forward, longest first
-        const int64_t ni = np * kPlanWords;
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ibucket, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&iorder, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ostate, sizeof(uint32_t) * (kOrderStateWords + 1), s));
-        n_items = ostate + kOrderStateWords;
-        DIP_CUDA_TRY(cudaMemsetAsync(ostate, 0, sizeof(uint32_t) * (kOrderStateWords + 1), s));
         note_launch();
         k_plan_items<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(plan_cost, np, (unsigned)t->nn,
                                                                   items, ibucket, n_items, ostate);
@@ -693,16 +709,9 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         plan_w = plan_cost;  // items add their steps and record their cuts
         DIP_CUDA_TRY(cudaMemsetAsync(plan_w, 0, sizeof(uint32_t) * kPlanWords * (size_t)np, s));
     }
-    if (big && mode != kCount && !plan_in) {
+    if (fwd_items) {
         // every packet's walk in two ranged items (the forward's add into the
         // zeroed outputs), longest predicted first
-        const int64_t ni = 2 * np;
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&items, sizeof(uint4) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ibucket, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&iorder, sizeof(uint32_t) * ni, s));
-        DIP_CUDA_TRY(cudaMallocAsync((void**)&ostate, sizeof(uint32_t) * (kOrderStateWords + 1), s));
-        n_items = ostate + kOrderStateWords;
-        DIP_CUDA_TRY(cudaMemsetAsync(ostate, 0, sizeof(uint32_t) * (kOrderStateWords + 1), s));
         if (call.out) DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
         if (call.gout)
             DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
@@ -713,7 +722,6 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         order_place(ibucket, ni, ostate, iorder, s);
         porder = iorder;
     }
-    DIP_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long), s));
     if (adjoint) {
         DIP_CUDA_TRY(cudaMemsetAsync(t->dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
         DIP_CUDA_TRY(cudaMemsetAsync(t->dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
@@ -773,18 +781,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     if (rc == 0 && adjoint && call.grad) rc = stage2(t, call.grad, call.accumulate, s);
     if (rc == 0 && mode == kAdjointGeom)
         rc = stage2_geom(t, call.grad_n, call.grad_eps, call.accumulate, s);
-    cudaFreeAsync(work, s);
-    if (items) {
-        cudaFreeAsync(items, s);
-        cudaFreeAsync(ibucket, s);
-        cudaFreeAsync(iorder, s);
-        cudaFreeAsync(ostate, s);
-    }
-    if (codes) {
-        cudaFreeAsync(codes, s); cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s);
-        cudaFreeAsync(hist, s);
-        if (idx && idx != plan_perm) cudaFreeAsync(idx, s);
-    }
+    cudaFreeAsync(block, s);
     if (rc) return rc;
     DIP_CUDA_TRY(cudaGetLastError());
     return 0;

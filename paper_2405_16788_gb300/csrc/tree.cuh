@@ -21,6 +21,13 @@ struct dipole_tree {
     uint32_t* perm = nullptr;
     int32_t* leaf_of = nullptr;  // [n] leaf node holding each point
 
+    // device memory is taken in a few blocks (one allocation each, the arrays
+    // below point into them): points, topology, nodes, attribute state
+    void* point_block = nullptr;
+    void* topo_block = nullptr;
+    void* node_block = nullptr;
+    void* attr_block = nullptr;
+
     // nodes, depth-first preorder
     dip::NodeRec* nodes = nullptr;
     int32_t* first = nullptr;

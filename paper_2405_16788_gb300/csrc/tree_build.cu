@@ -443,23 +443,41 @@ unsigned grid_for(int64_t work, int threads) {
     return (unsigned)b;
 }
 
-template <typename T>
-cudaError_t dalloc(T** p, int64_t count, cudaStream_t s) {
-    size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
-    return cudaMallocAsync((void**)p, bytes, s);
-}
 
-
-// Point arrays, status word and bounding box of a new tree.
+// Point arrays, status word and bounding box of a new tree (one block).
 int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     const int64_t n = t->n;
-    DIP_CUDA_TRY(dalloc(&t->pts, n, s));
-    DIP_CUDA_TRY(dalloc(&t->code, n, s));
-    DIP_CUDA_TRY(dalloc(&t->perm, n, s));
-    DIP_CUDA_TRY(dalloc(&t->leaf_of, n, s));
-    DIP_CUDA_TRY(dalloc(&t->bbox, 8, s));
-    DIP_CUDA_TRY(dalloc(&t->status, 1, s));
+    auto take = [&](Carve& c) {
+        c.take(&t->pts, n);
+        c.take(&t->code, n);
+        c.take(&t->perm, n);
+        c.take(&t->leaf_of, n);
+        c.take(&t->bbox, 8);
+        c.take(&t->status, 1);
+    };
+    Carve c;
+    take(c);
+    DIP_CUDA_TRY(cudaMallocAsync(&t->point_block, c.off, s));
+    c = Carve{static_cast<char*>(t->point_block), 0};
+    take(c);
     DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
+    return 0;
+}
+
+// The node ranges, levels, skip indices and leaf flags (one block).
+int alloc_topology(dipole_tree* t, int64_t nn, cudaStream_t s) {
+    auto take = [&](Carve& c) {
+        c.take(&t->first, nn);
+        c.take(&t->count, nn);
+        c.take(&t->level, nn);
+        c.take(&t->skip, nn);
+        c.take(&t->is_leaf, nn);
+    };
+    Carve c;
+    take(c);
+    DIP_CUDA_TRY(cudaMallocAsync(&t->topo_block, c.off, s));
+    c = Carve{static_cast<char*>(t->topo_block), 0};
+    take(c);
     return 0;
 }
 
@@ -477,18 +495,32 @@ int status_error(int status_host, const char* who) {
 // geometry (eq. farfield_dipole), radius, node records.
 int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
     const int64_t n = t->n, nn = t->nn;
-    DIP_CUDA_TRY(dalloc(&t->nodes, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->parent, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->nchild, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->agg64, nn * 5, s));
-    DIP_CUDA_TRY(dalloc(&t->eps_node, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->lvl_list, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->lvl_off, kMaxLevel + 2, s));
     float4* cen4 = nullptr;
     unsigned int *rbits = nullptr, *lvl_cnt = nullptr;
-    DIP_CUDA_TRY(dalloc(&cen4, nn, s));
-    DIP_CUDA_TRY(dalloc(&rbits, nn, s));
-    DIP_CUDA_TRY(dalloc(&lvl_cnt, 2 * (kMaxLevel + 1), s));
+    auto take = [&](Carve& c) {  // the node arrays, then this pass's scratch
+        c.take(&t->nodes, nn);
+        c.take(&t->parent, nn);
+        c.take(&t->nchild, nn);
+        c.take(&t->agg64, nn * 5);
+        c.take(&t->eps_node, nn);
+        c.take(&t->lvl_list, nn);
+        c.take(&t->lvl_off, kMaxLevel + 2);
+    };
+    auto take_tmp = [&](Carve& c) {
+        c.take(&cen4, nn);
+        c.take(&rbits, nn);
+        c.take(&lvl_cnt, 2 * (kMaxLevel + 1));
+    };
+    Carve c, ct;
+    take(c);
+    take_tmp(ct);
+    void* tmp = nullptr;
+    DIP_CUDA_TRY(cudaMallocAsync(&t->node_block, c.off, s));
+    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    c = Carve{static_cast<char*>(t->node_block), 0};
+    ct = Carve{static_cast<char*>(tmp), 0};
+    take(c);
+    take_tmp(ct);
 
     DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
     note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
@@ -515,9 +547,7 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
     note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
                                                                  t->first, t->count, t->is_leaf,
                                                                  t->eps_node, t->nodes);
-    cudaFreeAsync(cen4, s);
-    cudaFreeAsync(rbits, s);
-    cudaFreeAsync(lvl_cnt, s);
+    cudaFreeAsync(tmp, s);
     DIP_CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -535,18 +565,26 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     float* partial = nullptr;
     const unsigned nbb = grid_for(n, kThreads) < 2u * (unsigned)num_sms() ? grid_for(n, kThreads)
                                                                           : 2u * (unsigned)num_sms();
-    DIP_CUDA_TRY(dalloc(&ktmp, n, s));
-    DIP_CUDA_TRY(dalloc(&vtmp, n, s));
-    DIP_CUDA_TRY(dalloc(&hist, radix_hist_entries(n), s));
-    DIP_CUDA_TRY(dalloc(&off, n + 1, s));
-    DIP_CUDA_TRY(dalloc(&scan_tmp, scan_tmp_entries(n + 1), s));
-    DIP_CUDA_TRY(dalloc(&partial, (int64_t)nbb * 6, s));
     float* eps_sorted = nullptr;
     uint32_t* tmask = nullptr;
     int32_t* estage = nullptr;
-    DIP_CUDA_TRY(dalloc(&eps_sorted, n, s));
-    DIP_CUDA_TRY(dalloc(&tmask, n, s));
-    DIP_CUDA_TRY(dalloc(&estage, n * (kMaxLevel + 1), s));
+    auto take_tmp = [&](Carve& c) {
+        c.take(&ktmp, n);
+        c.take(&vtmp, n);
+        c.take(&hist, radix_hist_entries(n));
+        c.take(&off, n + 1);
+        c.take(&scan_tmp, scan_tmp_entries(n + 1));
+        c.take(&partial, (int64_t)nbb * 6);
+        c.take(&eps_sorted, n);
+        c.take(&tmask, n);
+        c.take(&estage, n * (kMaxLevel + 1));
+    };
+    Carve ct;
+    take_tmp(ct);
+    void* tmp = nullptr;
+    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    ct = Carve{static_cast<char*>(tmp), 0};
+    take_tmp(ct);
 
     note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
     note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
@@ -566,11 +604,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     DIP_CUDA_TRY(cudaStreamSynchronize(s));
     DIP_CUDA_TRY(cudaGetLastError());
 
-    auto free_tmp = [&]() {
-        cudaFreeAsync(ktmp, s); cudaFreeAsync(vtmp, s); cudaFreeAsync(hist, s);
-        cudaFreeAsync(off, s); cudaFreeAsync(scan_tmp, s); cudaFreeAsync(partial, s);
-        cudaFreeAsync(eps_sorted, s); cudaFreeAsync(tmask, s); cudaFreeAsync(estage, s);
-    };
+    auto free_tmp = [&]() { cudaFreeAsync(tmp, s); };
     rc = status_error(status_host, "dipole_build_tree");
     if (rc) {
         free_tmp();
@@ -578,11 +612,11 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     }
     const int64_t nn = nn_host;
     t->nn = nn;
-    DIP_CUDA_TRY(dalloc(&t->first, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->count, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->level, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->skip, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->is_leaf, nn, s));
+    rc = alloc_topology(t, nn, s);
+    if (rc) {
+        free_tmp();
+        return rc;
+    }
     note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, tmask, estage,
                                                            t->first, t->count, t->level,
                                                            t->skip, t->is_leaf, t->leaf_of);
@@ -602,13 +636,21 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
     float* eps_sorted = nullptr;
     const unsigned nbb = grid_for(n, kThreads) < 2u * (unsigned)num_sms() ? grid_for(n, kThreads)
                                                                           : 2u * (unsigned)num_sms();
-    DIP_CUDA_TRY(dalloc(&partial, (int64_t)nbb * 6, s));
-    DIP_CUDA_TRY(dalloc(&eps_sorted, n, s));
-    DIP_CUDA_TRY(dalloc(&t->first, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->count, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->level, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->skip, nn, s));
-    DIP_CUDA_TRY(dalloc(&t->is_leaf, nn, s));
+    auto take_tmp = [&](Carve& c) {
+        c.take(&partial, (int64_t)nbb * 6);
+        c.take(&eps_sorted, n);
+    };
+    Carve ct;
+    take_tmp(ct);
+    void* tmp = nullptr;
+    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    ct = Carve{static_cast<char*>(tmp), 0};
+    take_tmp(ct);
+    rc = alloc_topology(t, nn, s);
+    if (rc) {
+        cudaFreeAsync(tmp, s);
+        return rc;
+    }
     DIP_CUDA_TRY(cudaMemcpyAsync(t->perm, perm_h, 4 * n, cudaMemcpyHostToDevice, s));
     if (codes_h) DIP_CUDA_TRY(cudaMemcpyAsync(t->code, codes_h, 4 * n, cudaMemcpyHostToDevice, s));
     else DIP_CUDA_TRY(cudaMemsetAsync(t->code, 0, 4 * n, s));
@@ -631,8 +673,7 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
     DIP_CUDA_TRY(cudaGetLastError());
     rc = status_error(status_host, "dipole_tree_import");
     if (rc == 0) rc = derive_nodes(t, eps_sorted, s);
-    cudaFreeAsync(partial, s);
-    cudaFreeAsync(eps_sorted, s);
+    cudaFreeAsync(tmp, s);
     return rc;
 }
 
