@@ -137,9 +137,14 @@ int64_t radix_hist_entries(int64_t n);
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                       uint32_t* hist, int64_t n, int bits, cudaStream_t s);
 
-// Exclusive scan of n uint32 values in place; tmp holds scan_tmp_entries(n).
-int64_t scan_tmp_entries(int64_t n);
-void exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s);
+// Exclusive scan in one launch, tile-local: the scan's value at i is
+// data[i] + ws[i / kScanTileSize]; ws holds scan_local_entries(n) entries and
+// *grand (if given) receives the sum of all values.
+constexpr int kScanTileSize = 4096;
+int64_t scan_local_entries(int64_t n);
+void exclusive_scan_local(uint32_t* data, int64_t n, uint32_t* ws, uint32_t* grand,
+                          cudaStream_t s);
+
 
 // 30-bit Morton code (Hilbert index with `hilbert`), shifted right by
 // `shift`, of each point in the tree's bounding cube (clamped to it) and the

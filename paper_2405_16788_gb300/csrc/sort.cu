@@ -11,6 +11,7 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileSize, "the tile-local scan's tile");
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
@@ -21,44 +22,68 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
     return v;
 }
 
-// Exclusive scan of one tile in place; the tile total goes to totals[blockIdx].
-__global__ void __launch_bounds__(kScanThreads) k_scan_tile(uint32_t* data, int64_t n,
-                                                            uint32_t* totals) {
+// Exclusive scan in one launch, for consumers that add the tile offsets
+// themselves: the tiles write their local exclusive scans and totals, and the
+// last tile to finish (an arrival counter; no block waits for another) turns
+// the totals into exclusive tile offsets in place, 4,096 at a time, writes the
+// sum of all values to *grand (if given) and clears the counter.  The scan's
+// value at i is then data[i] + totals[i / kScanTile].
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile_last(uint32_t* data, int64_t n,
+                                                                 uint32_t* totals, unsigned* done,
+                                                                 uint32_t* grand) {
     __shared__ uint32_t warp_sums[32];
+    __shared__ bool last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t sum = 0;
+    auto block_exclusive = [&](uint32_t* a, int64_t m, int64_t base0, uint32_t carry) {
+        // exclusive scan of a[base0 .. base0 + kScanTile) (bounded by m) plus carry;
+        // returns the chunk's total through warp_sums[31] + last partial
+        const int64_t base = base0 + (int64_t)tid * kScanItems;
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = (base + k < n) ? data[base + k] : 0u;
-        sum += v[k];
-    }
-    uint32_t incl = warp_incl_scan(sum, lane);
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = warp_sums[lane];
-        uint32_t wi = warp_incl_scan(w, lane);
-        warp_sums[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = warp_sums[warp] + incl - sum;
+        for (int k = 0; k < kScanItems; ++k) {
+            v[k] = (base + k < m) ? __ldcg(a + base + k) : 0u;
+            sum += v[k];
+        }
+        const uint32_t incl = warp_incl_scan(sum, lane);
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = warp_sums[lane];
+            const uint32_t wi = warp_incl_scan(w, lane);
+            warp_sums[lane] = wi - w;
+        }
+        __syncthreads();
+        uint32_t run = carry + warp_sums[warp] + incl - sum;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) data[base + k] = run;
-        run += v[k];
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < m) a[base + k] = run;
+            run += v[k];
+        }
+        __syncthreads();  // warp_sums is reused
+        return run;       // the running total after this thread's items
+    };
+    const uint32_t tot = block_exclusive(data, n, (int64_t)blockIdx.x * kScanTile, 0u);
+    if (tid == kScanThreads - 1) {
+        totals[blockIdx.x] = tot;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1u;
     }
-    if (tid == kScanThreads - 1 && totals) totals[blockIdx.x] = run;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(uint32_t* data, int64_t n,
-                                                           const uint32_t* offsets) {
-    const uint32_t add = offsets[blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-        int64_t i = base + k;
-        if (i < n) data[i] += add;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ uint32_t carry_s;
+    uint32_t carry = 0;
+    for (int64_t c0 = 0; c0 < gridDim.x; c0 += kScanTile) {
+        const uint32_t r = block_exclusive(totals, gridDim.x, c0, carry);
+        if (tid == kScanThreads - 1) carry_s = r;
+        __syncthreads();
+        carry = carry_s;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *done = 0u;
+        if (grand) *grand = carry;  // the sum of all n values
     }
 }
 
@@ -93,13 +118,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* key
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, uint32_t mask,
-    const uint32_t* __restrict__ offsets, int nblocks) {
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tile_off, int nblocks) {
     __shared__ uint32_t wcnt[kSortWarps][kRadix];
     __shared__ uint32_t running[kRadix];
     __shared__ uint32_t gbase[kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     running[tid] = 0;
-    gbase[tid] = offsets[(int64_t)tid * nblocks + blockIdx.x];
+    {   // offsets: tile-local exclusive scan plus the tile's offset (k_scan_tile_last)
+        const int64_t i = (int64_t)tid * nblocks + blockIdx.x;
+        gbase[tid] = offsets[i] + tile_off[i / kScanTile];
+    }
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     for (int r = 0; r < kSortItems; ++r) {
@@ -183,50 +211,44 @@ int num_sms() {
     return sms;
 }
 
-int64_t scan_tmp_entries(int64_t n) {
-    int64_t total = 0;
-    int64_t m = n;
-    while (m > kScanTile) {
-        m = (m + kScanTile - 1) / kScanTile;
-        total += m + 32;
-    }
-    return total + 32;
-}
+int64_t scan_local_entries(int64_t n) { return (n + kScanTile - 1) / kScanTile + 4; }
 
-void exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s) {
+void exclusive_scan_local(uint32_t* data, int64_t n, uint32_t* ws, uint32_t* grand,
+                          cudaStream_t s) {
     if (n <= 0) return;
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb == 1) {
-        note_launch(); k_scan_tile<<<1, kScanThreads, 0, s>>>(data, n, nullptr);
-        return;
-    }
-    uint32_t* totals = tmp;
-    note_launch(); k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, totals);
-    exclusive_scan_u32(totals, nb, tmp + nb + 32, s);
-    note_launch(); k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, totals);
+    const unsigned st = (unsigned)((n + kScanTile - 1) / kScanTile);
+    unsigned* done = reinterpret_cast<unsigned*>(ws + st);
+    cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    note_launch(); k_scan_tile_last<<<st, kScanThreads, 0, s>>>(data, n, ws, done, grand);
 }
 
 int64_t radix_hist_entries(int64_t n) {
     int64_t nb = (n + kSortTile - 1) / kSortTile;
     if (nb < 1) nb = 1;
-    int64_t h = nb * kRadix;
-    return h + scan_tmp_entries(h);
+    const int64_t h = nb * kRadix;
+    return h + (h + kScanTile - 1) / kScanTile + 4;  // counts, tile totals, arrival counter
 }
 
+// Three launches per 8-bit pass: digit counts per tile of keys, their scan
+// (tile-local, the last tile scanning the tile totals), the stable scatter.
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
                       uint32_t* hist, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1) return;
     int nb = (int)((n + kSortTile - 1) / kSortTile);
     int64_t h = (int64_t)nb * kRadix;
-    uint32_t* scan_tmp = hist + h;
+    const unsigned st = (unsigned)((h + kScanTile - 1) / kScanTile);
+    uint32_t* totals = hist + h;                              // st entries
+    unsigned* done = reinterpret_cast<unsigned*>(totals + st);  // arrival counter
+    cudaMemsetAsync(done, 0, sizeof(unsigned), s);
     uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += kRadixBits) {
         int w = bits - shift < kRadixBits ? bits - shift : kRadixBits;
         uint32_t mask = (1u << w) - 1u;
         note_launch(); k_radix_hist<<<nb, kSortThreads, 0, s>>>(ki, n, shift, mask, hist, nb);
-        exclusive_scan_u32(hist, h, scan_tmp, s);
-        note_launch(); k_radix_scatter<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, mask, hist, nb);
+        note_launch(); k_scan_tile_last<<<st, kScanThreads, 0, s>>>(hist, h, totals, done, nullptr);
+        note_launch(); k_radix_scatter<<<nb, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, mask, hist,
+                                                                  totals, nb);
         uint32_t* t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
         ++passes;

@@ -18,6 +18,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <cstring>
 
 namespace dip {
 namespace {
@@ -204,7 +205,10 @@ __global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf
     }
 }
 
+// off: the tile-local exclusive scan of the per-point node counts, completed
+// by tile_off (exclusive_scan_local).
 __global__ void k_topo_emit(int64_t n, int max_depth, const uint32_t* __restrict__ off,
+                            const uint32_t* __restrict__ tile_off,
                             const uint32_t* __restrict__ tmask, const int32_t* __restrict__ estage,
                             int32_t* __restrict__ first, int32_t* __restrict__ count,
                             int32_t* __restrict__ level, int32_t* __restrict__ skip,
@@ -214,14 +218,14 @@ __global__ void k_topo_emit(int64_t n, int max_depth, const uint32_t* __restrict
         const uint32_t mk = tmask[i];
         const uint32_t mask = mk & 0xffffu, im = mk >> 16;
         if (!mask) continue;
-        uint32_t t = off[i];
+        uint32_t t = off[i] + tile_off[i / kScanTileSize];
         for (int l = 0; l <= max_depth; ++l) {
             if (!(mask & (1u << l))) continue;
             const int64_t e = estage[i * (kMaxLevel + 1) + l];
             first[t] = (int32_t)i;
             count[t] = (int32_t)(e - i);
             level[t] = l;
-            skip[t] = (int32_t)off[e];
+            skip[t] = (int32_t)(off[e] + tile_off[e / kScanTileSize]);
             const bool leaf = !(im & (1u << l));
             is_leaf[t] = leaf ? 1 : 0;
             if (leaf)
@@ -452,8 +456,11 @@ int alloc_point_state(dipole_tree* t, cudaStream_t s) {
         c.take(&t->code, n);
         c.take(&t->perm, n);
         c.take(&t->leaf_of, n);
-        c.take(&t->bbox, 8);
-        c.take(&t->status, 1);
+        // bbox (8 floats), the status word and the build's node count, one host read
+        float* small = nullptr;
+        c.take(&small, 16);
+        t->bbox = small;
+        t->status = reinterpret_cast<int*>(small + 8);
     };
     Carve c;
     take(c);
@@ -561,7 +568,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     if (rc) return rc;
 
     // temporaries
-    uint32_t *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr, *off = nullptr, *scan_tmp = nullptr;
+    uint32_t *ktmp = nullptr, *vtmp = nullptr, *hist = nullptr, *off = nullptr, *scan_ws = nullptr;
     float* partial = nullptr;
     const unsigned nbb = grid_for(n, kThreads) < 2u * (unsigned)num_sms() ? grid_for(n, kThreads)
                                                                           : 2u * (unsigned)num_sms();
@@ -573,7 +580,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
         c.take(&vtmp, n);
         c.take(&hist, radix_hist_entries(n));
         c.take(&off, n + 1);
-        c.take(&scan_tmp, scan_tmp_entries(n + 1));
+        c.take(&scan_ws, scan_local_entries(n + 1));
         c.take(&partial, (int64_t)nbb * 6);
         c.take(&eps_sorted, n);
         c.take(&tmask, n);
@@ -595,13 +602,16 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     note_launch(); k_topo_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size,
                                                             t->max_depth, off, tmask, estage);
     DIP_CUDA_TRY(cudaMemsetAsync(off + n, 0, sizeof(uint32_t), s));
-    exclusive_scan_u32(off, n + 1, scan_tmp, s);
-    uint32_t nn_host = 0;
-    int status_host = 0;
-    DIP_CUDA_TRY(cudaMemcpyAsync(&nn_host, off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    DIP_CUDA_TRY(cudaMemcpyAsync(&status_host, t->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    DIP_CUDA_TRY(cudaMemcpyAsync(t->bbox_host, t->bbox, 5 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    exclusive_scan_local(off, n + 1, scan_ws, reinterpret_cast<uint32_t*>(t->bbox + 9), s);
+    // one read: bbox (5 floats), the status word (float 8), the node count (float 9)
+    float hs[10];
+    DIP_CUDA_TRY(cudaMemcpyAsync(hs, t->bbox, sizeof(hs), cudaMemcpyDeviceToHost, s));
     DIP_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(t->bbox_host, hs, 5 * sizeof(float));
+    int status_host = 0;
+    uint32_t nn_host = 0;
+    std::memcpy(&status_host, hs + 8, sizeof(int));
+    std::memcpy(&nn_host, hs + 9, sizeof(uint32_t));
     DIP_CUDA_TRY(cudaGetLastError());
 
     auto free_tmp = [&]() { cudaFreeAsync(tmp, s); };
@@ -617,7 +627,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
         free_tmp();
         return rc;
     }
-    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, tmask, estage,
+    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, scan_ws, tmask, estage,
                                                            t->first, t->count, t->level,
                                                            t->skip, t->is_leaf, t->leaf_of);
     rc = derive_nodes(t, eps_sorted, s);
