@@ -134,8 +134,11 @@ struct Carve {
 // keys/vals are sorted in place; tmp buffers hold n entries each.  hist must
 // hold radix_hist_entries(n) uint32 entries.
 int64_t radix_hist_entries(int64_t n);
+// done_zero: an arrival counter that is zero (kept zero), else one in hist is
+// cleared first.
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
-                      uint32_t* hist, int64_t n, int bits, cudaStream_t s);
+                      uint32_t* hist, int64_t n, int bits, cudaStream_t s,
+                      unsigned* done_zero = nullptr);
 
 // Exclusive scan in one launch, tile-local: the scan's value at i is
 // data[i] + ws[i / kScanTileSize]; ws holds scan_local_entries(n) entries and
@@ -143,7 +146,7 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32
 constexpr int kScanTileSize = 4096;
 int64_t scan_local_entries(int64_t n);
 void exclusive_scan_local(uint32_t* data, int64_t n, uint32_t* ws, uint32_t* grand,
-                          cudaStream_t s);
+                          cudaStream_t s, unsigned* done_zero = nullptr);
 
 
 // 30-bit Morton code (Hilbert index with `hilbert`), shifted right by

@@ -214,11 +214,14 @@ int num_sms() {
 int64_t scan_local_entries(int64_t n) { return (n + kScanTile - 1) / kScanTile + 4; }
 
 void exclusive_scan_local(uint32_t* data, int64_t n, uint32_t* ws, uint32_t* grand,
-                          cudaStream_t s) {
+                          cudaStream_t s, unsigned* done_zero) {
     if (n <= 0) return;
     const unsigned st = (unsigned)((n + kScanTile - 1) / kScanTile);
-    unsigned* done = reinterpret_cast<unsigned*>(ws + st);
-    cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    unsigned* done = done_zero;
+    if (!done) {
+        done = reinterpret_cast<unsigned*>(ws + st);
+        cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    }
     note_launch(); k_scan_tile_last<<<st, kScanThreads, 0, s>>>(data, n, ws, done, grand);
 }
 
@@ -232,14 +235,17 @@ int64_t radix_hist_entries(int64_t n) {
 // Three launches per 8-bit pass: digit counts per tile of keys, their scan
 // (tile-local, the last tile scanning the tile totals), the stable scatter.
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp, uint32_t* vals_tmp,
-                      uint32_t* hist, int64_t n, int bits, cudaStream_t s) {
+                      uint32_t* hist, int64_t n, int bits, cudaStream_t s, unsigned* done_zero) {
     if (n <= 1) return;
     int nb = (int)((n + kSortTile - 1) / kSortTile);
     int64_t h = (int64_t)nb * kRadix;
     const unsigned st = (unsigned)((h + kScanTile - 1) / kScanTile);
-    uint32_t* totals = hist + h;                              // st entries
-    unsigned* done = reinterpret_cast<unsigned*>(totals + st);  // arrival counter
-    cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    uint32_t* totals = hist + h;  // st entries
+    unsigned* done = done_zero;   // arrival counter of the scans, zero between passes
+    if (!done) {
+        done = reinterpret_cast<unsigned*>(totals + st);
+        cudaMemsetAsync(done, 0, sizeof(unsigned), s);
+    }
     uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += kRadixBits) {

@@ -36,12 +36,39 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Input validation and per-block bounding boxes.
-__global__ void __launch_bounds__(kThreads) k_bbox_partial(const float* __restrict__ p,
-                                                           const float* __restrict__ nrm,
-                                                           const float* __restrict__ A,
-                                                           const float* __restrict__ eps,
-                                                           int64_t n, float* partial, int* status) {
+// Bounding cube from the per-block boxes: lo = per-axis minimum; ext = largest
+// per-axis extent (float subtraction), 1 if 0; scale = 1024 / ext (correctly
+// rounded division).  One warp reduces the partials.
+__device__ void bbox_final(const float* partial, int nb, float* bbox) {
+    const int lane = threadIdx.x & 31;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int b = lane; b < nb; b += 32)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __ldcg(partial + b * 6 + a));
+            hi[a] = fmaxf(hi[a], __ldcg(partial + b * 6 + 3 + a));
+        }
+    for (int a = 0; a < 3; ++a) { lo[a] = warp_min(lo[a]); hi[a] = warp_max(hi[a]); }
+    if (lane != 0) return;
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float e = __fsub_rn(hi[a], lo[a]);
+        if (e > ext) ext = e;
+    }
+    if (!(ext > 0.0f)) ext = 1.0f;
+    bbox[0] = lo[0]; bbox[1] = lo[1]; bbox[2] = lo[2];
+    bbox[3] = ext;
+    bbox[4] = __fdiv_rn(1024.0f, ext);
+}
+
+// Input validation and per-block bounding boxes; the last block to finish
+// (an arrival counter, zero on entry; no block waits for another) reduces them
+// into the bounding cube.
+__global__ void __launch_bounds__(kThreads) k_bbox(const float* __restrict__ p,
+                                                   const float* __restrict__ nrm,
+                                                   const float* __restrict__ A,
+                                                   const float* __restrict__ eps, int64_t n,
+                                                   float* partial, int* status, unsigned* done,
+                                                   float* bbox) {
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -61,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_bbox_partial(const float* __restri
     }
     if (bad) atomicOr(status, bad);
     __shared__ float sh[6][kThreads / 32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -73,31 +101,32 @@ __global__ void __launch_bounds__(kThreads) k_bbox_partial(const float* __restri
         for (int w = 1; w < kThreads / 32; ++w)
             v = threadIdx.x < 3 ? fminf(v, sh[threadIdx.x][w]) : fmaxf(v, sh[threadIdx.x][w]);
         partial[blockIdx.x * 6 + threadIdx.x] = v;
+        __threadfence();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    bbox_final(partial, (int)gridDim.x, bbox);
 }
 
-// Bounding cube: lo = per-axis minimum; ext = largest per-axis extent (float
-// subtraction), 1 if 0; scale = 1024 / ext (correctly rounded division).
-// One warp reduces the per-block partials.
-__global__ void k_bbox_final(const float* partial, int nb, float* bbox) {
-    const int lane = threadIdx.x & 31;
-    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (int b = lane; b < nb; b += 32)
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fminf(lo[a], partial[b * 6 + a]);
-            hi[a] = fmaxf(hi[a], partial[b * 6 + 3 + a]);
-        }
-    for (int a = 0; a < 3; ++a) { lo[a] = warp_min(lo[a]); hi[a] = warp_max(hi[a]); }
-    if (lane != 0) return;
-    float ext = 0.0f;
-    for (int a = 0; a < 3; ++a) {
-        float e = __fsub_rn(hi[a], lo[a]);
-        if (e > ext) ext = e;
-    }
-    if (!(ext > 0.0f)) ext = 1.0f;
-    bbox[0] = lo[0]; bbox[1] = lo[1]; bbox[2] = lo[2];
-    bbox[3] = ext;
-    bbox[4] = __fdiv_rn(1024.0f, ext);
+// Point record of sorted point i (input point perm[i]).
+__device__ __forceinline__ void pack_point(int64_t i, const uint32_t* __restrict__ perm,
+                                           const float* __restrict__ p,
+                                           const float* __restrict__ nrm,
+                                           const float* __restrict__ A,
+                                           const float* __restrict__ eps,
+                                           PointRec* __restrict__ pts, float* __restrict__ eps_sorted) {
+    int64_t m = perm[i];
+    float a = A[m];
+    float e = eps ? eps[m] : 0.0f;
+    PointRec r;
+    r.geo = make_float4(p[3 * m], p[3 * m + 1], p[3 * m + 2], __frcp_rn(e));
+    r.w = make_float4(__fmul_rn(a, nrm[3 * m]), __fmul_rn(a, nrm[3 * m + 1]),
+                      __fmul_rn(a, nrm[3 * m + 2]), a);
+    pts[i] = r;
+    eps_sorted[i] = e;
 }
 
 __global__ void k_pack(const uint32_t* __restrict__ perm, const float* __restrict__ p,
@@ -105,17 +134,8 @@ __global__ void k_pack(const uint32_t* __restrict__ perm, const float* __restric
                        const float* __restrict__ eps, int64_t n, PointRec* __restrict__ pts,
                        float* __restrict__ eps_sorted) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t m = perm[i];
-        float a = A[m];
-        float e = eps ? eps[m] : 0.0f;
-        PointRec r;
-        r.geo = make_float4(p[3 * m], p[3 * m + 1], p[3 * m + 2], __frcp_rn(e));
-        r.w = make_float4(__fmul_rn(a, nrm[3 * m]), __fmul_rn(a, nrm[3 * m + 1]),
-                          __fmul_rn(a, nrm[3 * m + 2]), a);
-        pts[i] = r;
-        eps_sorted[i] = e;
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        pack_point(i, perm, p, nrm, A, eps, pts, eps_sorted);
 }
 
 // ------------------------------------------------------------- topology
@@ -190,11 +210,18 @@ __device__ uint32_t analyze_point(const uint32_t* __restrict__ c, int64_t n, int
 // node/internal masks (mask | imask << 16) and, for every level with a node,
 // the end of its run (estage[11 i + l]), so that the emit pass need not search
 // again.
+// Also packs the point records (one launch for two per-point passes) and
+// sets the count after the last point, cnt[n], to 0.
 __global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf_size,
                              int max_depth, uint32_t* __restrict__ cnt, uint32_t* __restrict__ tmask,
-                             int32_t* __restrict__ estage) {
+                             int32_t* __restrict__ estage, const uint32_t* __restrict__ perm,
+                             const float* __restrict__ p, const float* __restrict__ nrm,
+                             const float* __restrict__ A, const float* __restrict__ eps,
+                             PointRec* __restrict__ pts, float* __restrict__ eps_sorted) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[n] = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        pack_point(i, perm, p, nrm, A, eps, pts, eps_sorted);
         int64_t e[kMaxLevel + 2];
         uint32_t im;
         const uint32_t mask = analyze_point(c, n, i, leaf_size, max_depth, e, &im);
@@ -207,14 +234,23 @@ __global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf
 
 // off: the tile-local exclusive scan of the per-point node counts, completed
 // by tile_off (exclusive_scan_local).
-__global__ void k_topo_emit(int64_t n, int max_depth, const uint32_t* __restrict__ off,
-                            const uint32_t* __restrict__ tile_off,
+// It also sets what the node pass expects cleared: parent[t] = -1 and
+// rbits[t] = 0 for the nn nodes, and the level counters.
+__global__ void k_topo_emit(int64_t n, int64_t nn, int max_depth, const uint32_t* __restrict__ off,
+                            const uint32_t* __restrict__ tile_off, int32_t* __restrict__ parent,
+                            unsigned int* __restrict__ rbits, unsigned int* __restrict__ lvl_cnt,
                             const uint32_t* __restrict__ tmask, const int32_t* __restrict__ estage,
                             int32_t* __restrict__ first, int32_t* __restrict__ count,
                             int32_t* __restrict__ level, int32_t* __restrict__ skip,
                             int32_t* __restrict__ is_leaf, int32_t* __restrict__ leaf_of) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t t = g; t < nn; t += stride) {
+        parent[t] = -1;
+        rbits[t] = 0u;
+    }
+    if (g < 2 * (kMaxLevel + 1)) lvl_cnt[g] = 0u;
+    for (int64_t i = g; i < n; i += stride) {
         const uint32_t mk = tmask[i];
         const uint32_t mask = mk & 0xffffu, im = mk >> 16;
         if (!mask) continue;
@@ -456,7 +492,9 @@ int alloc_point_state(dipole_tree* t, cudaStream_t s) {
         c.take(&t->code, n);
         c.take(&t->perm, n);
         c.take(&t->leaf_of, n);
-        // bbox (8 floats), the status word and the build's node count, one host read
+        // small[0..5) bbox, [8] status word, [9] the build's node count, [10..13)
+        // arrival counters of the build's one-launch reductions; [8..16) zeroed at
+        // once, [0..10) read back at once
         float* small = nullptr;
         c.take(&small, 16);
         t->bbox = small;
@@ -467,9 +505,12 @@ int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     DIP_CUDA_TRY(cudaMallocAsync(&t->point_block, c.off, s));
     c = Carve{static_cast<char*>(t->point_block), 0};
     take(c);
-    DIP_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), s));
+    DIP_CUDA_TRY(cudaMemsetAsync(t->bbox + 8, 0, 8 * sizeof(float), s));
     return 0;
 }
+
+// The small area's arrival counters (zero from alloc_point_state).
+unsigned* build_counter(dipole_tree* t, int k) { return reinterpret_cast<unsigned*>(t->bbox + 10 + k); }
 
 // The node ranges, levels, skip indices and leaf flags (one block).
 int alloc_topology(dipole_tree* t, int64_t nn, cudaStream_t s) {
@@ -500,11 +541,17 @@ int status_error(int status_host, const char* who) {
 // Everything that follows from the node ranges (first, count, level, skip,
 // is_leaf, already on the device) and leaf_of: parents, level lists, node
 // geometry (eq. farfield_dipole), radius, node records.
-int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
-    const int64_t n = t->n, nn = t->nn;
+// The node arrays (one block) and the node pass's scratch (another).
+struct NodeScratch {
     float4* cen4 = nullptr;
-    unsigned int *rbits = nullptr, *lvl_cnt = nullptr;
-    auto take = [&](Carve& c) {  // the node arrays, then this pass's scratch
+    unsigned int* rbits = nullptr;
+    unsigned int* lvl_cnt = nullptr;  // [kMaxLevel + 1] counts, [kMaxLevel + 1] fill cursors
+    void* tmp = nullptr;
+};
+
+int alloc_nodes(dipole_tree* t, NodeScratch& ns, cudaStream_t s) {
+    const int64_t nn = t->nn;
+    auto take = [&](Carve& c) {
         c.take(&t->nodes, nn);
         c.take(&t->parent, nn);
         c.take(&t->nchild, nn);
@@ -514,25 +561,36 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
         c.take(&t->lvl_off, kMaxLevel + 2);
     };
     auto take_tmp = [&](Carve& c) {
-        c.take(&cen4, nn);
-        c.take(&rbits, nn);
-        c.take(&lvl_cnt, 2 * (kMaxLevel + 1));
+        c.take(&ns.cen4, nn);
+        c.take(&ns.rbits, nn);
+        c.take(&ns.lvl_cnt, 2 * (kMaxLevel + 1));
     };
     Carve c, ct;
     take(c);
     take_tmp(ct);
-    void* tmp = nullptr;
     DIP_CUDA_TRY(cudaMallocAsync(&t->node_block, c.off, s));
-    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    DIP_CUDA_TRY(cudaMallocAsync(&ns.tmp, ct.off, s));
     c = Carve{static_cast<char*>(t->node_block), 0};
-    ct = Carve{static_cast<char*>(tmp), 0};
+    ct = Carve{static_cast<char*>(ns.tmp), 0};
     take(c);
     take_tmp(ct);
+    return 0;
+}
 
-    DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
+// inited: parent (-1), rbits and lvl_cnt (0) were set by the topology pass.
+int derive_nodes(dipole_tree* t, const float* eps_sorted, NodeScratch& ns, bool inited,
+                 cudaStream_t s) {
+    const int64_t n = t->n, nn = t->nn;
+    float4* cen4 = ns.cen4;
+    unsigned int *rbits = ns.rbits, *lvl_cnt = ns.lvl_cnt;
+    void* tmp = ns.tmp;
+    if (!inited) {
+        DIP_CUDA_TRY(cudaMemsetAsync(t->parent, 0xff, sizeof(int32_t) * nn, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(lvl_cnt, 0, sizeof(unsigned int) * 2 * (kMaxLevel + 1), s));
+        DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
+    }
     note_launch(); k_children<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->skip, t->is_leaf, t->parent,
                                                            t->nchild, t->status);
-    DIP_CUDA_TRY(cudaMemsetAsync(lvl_cnt, 0, sizeof(unsigned int) * (kMaxLevel + 1), s));
     note_launch(); k_level_count<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, t->level, t->is_leaf,
                                                                             lvl_cnt);
     note_launch(); k_level_offsets<<<1, 32, 0, s>>>(lvl_cnt, t->lvl_off, lvl_cnt + kMaxLevel + 1);
@@ -548,7 +606,6 @@ int derive_nodes(dipole_tree* t, const float* eps_sorted, cudaStream_t s) {
     note_launch();
     k_geom_level<<<1, kTopThreads, 0, s>>>(min(kTopLevel, t->max_depth - 1), 0, t->lvl_off,
                                           t->lvl_list, t->skip, t->agg64, cen4, t->eps_node);
-    DIP_CUDA_TRY(cudaMemsetAsync(rbits, 0, sizeof(unsigned int) * nn, s));
     note_launch(); k_radius<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->pts, t->leaf_of, t->parent, cen4,
                                                         rbits);
     note_launch(); k_finalize_nodes<<<grid_for(nn, kThreads), kThreads, 0, s>>>(nn, cen4, rbits, t->skip,
@@ -593,16 +650,15 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     ct = Carve{static_cast<char*>(tmp), 0};
     take_tmp(ct);
 
-    note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
-    note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
+    note_launch(); k_bbox<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status,
+                                                   build_counter(t, 0), t->bbox);
     query_codes(points, n, t->bbox, 0, t->code, t->perm, t->status, s);
-    radix_sort_pairs(t->code, t->perm, ktmp, vtmp, hist, n, 30, s);
-    note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
-                                                      t->pts, eps_sorted);
-    note_launch(); k_topo_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->code, n, t->leaf_size,
-                                                            t->max_depth, off, tmask, estage);
-    DIP_CUDA_TRY(cudaMemsetAsync(off + n, 0, sizeof(uint32_t), s));
-    exclusive_scan_local(off, n + 1, scan_ws, reinterpret_cast<uint32_t*>(t->bbox + 9), s);
+    radix_sort_pairs(t->code, t->perm, ktmp, vtmp, hist, n, 30, s, build_counter(t, 1));
+    note_launch(); k_topo_count<<<grid_for(n, kThreads), kThreads, 0, s>>>(
+        t->code, n, t->leaf_size, t->max_depth, off, tmask, estage, t->perm, points, normals, areas,
+        radii, t->pts, eps_sorted);
+    exclusive_scan_local(off, n + 1, scan_ws, reinterpret_cast<uint32_t*>(t->bbox + 9), s,
+                         build_counter(t, 2));
     // one read: bbox (5 floats), the status word (float 8), the node count (float 9)
     float hs[10];
     DIP_CUDA_TRY(cudaMemcpyAsync(hs, t->bbox, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -623,14 +679,17 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     const int64_t nn = nn_host;
     t->nn = nn;
     rc = alloc_topology(t, nn, s);
+    NodeScratch ns;
+    if (rc == 0) rc = alloc_nodes(t, ns, s);
     if (rc) {
         free_tmp();
         return rc;
     }
-    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, t->max_depth, off, scan_ws, tmask, estage,
+    note_launch(); k_topo_emit<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, nn, t->max_depth, off, scan_ws,
+                                                           t->parent, ns.rbits, ns.lvl_cnt, tmask, estage,
                                                            t->first, t->count, t->level,
                                                            t->skip, t->is_leaf, t->leaf_of);
-    rc = derive_nodes(t, eps_sorted, s);
+    rc = derive_nodes(t, eps_sorted, ns, true, s);
     free_tmp();
     return rc;
 }
@@ -669,8 +728,8 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
     DIP_CUDA_TRY(cudaMemcpyAsync(t->level, level_h, 4 * nn, cudaMemcpyHostToDevice, s));
     DIP_CUDA_TRY(cudaMemcpyAsync(t->skip, skip_h, 4 * nn, cudaMemcpyHostToDevice, s));
     DIP_CUDA_TRY(cudaMemcpyAsync(t->is_leaf, is_leaf_h, 4 * nn, cudaMemcpyHostToDevice, s));
-    note_launch(); k_bbox_partial<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status);
-    note_launch(); k_bbox_final<<<1, 32, 0, s>>>(partial, (int)nbb, t->bbox);
+    note_launch(); k_bbox<<<nbb, kThreads, 0, s>>>(points, normals, areas, radii, n, partial, t->status,
+                                                   build_counter(t, 0), t->bbox);
     note_launch(); k_pack<<<grid_for(n, kThreads), kThreads, 0, s>>>(t->perm, points, normals, areas, radii, n,
                                                       t->pts, eps_sorted);
     DIP_CUDA_TRY(cudaMemsetAsync(t->leaf_of, 0xff, sizeof(int32_t) * n, s));
@@ -682,7 +741,9 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
     DIP_CUDA_TRY(cudaStreamSynchronize(s));
     DIP_CUDA_TRY(cudaGetLastError());
     rc = status_error(status_host, "dipole_tree_import");
-    if (rc == 0) rc = derive_nodes(t, eps_sorted, s);
+    NodeScratch ns;
+    if (rc == 0) rc = alloc_nodes(t, ns, s);
+    if (rc == 0) rc = derive_nodes(t, eps_sorted, ns, false, s);
     cudaFreeAsync(tmp, s);
     return rc;
 }
