@@ -619,18 +619,17 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
             c.take(&t->dmu, t->n * Cp);
             c.take(&t->fix_P, fix_ld(t->nn) * NC);
             c.take(&t->fix_tsum, ntiles * NC);
-            c.take(&t->fix_cmax, NC);
+            c.take(&t->fix_cmax, NC + 1);  // the column maxima, then the arrival counter
+            t->fix_done = t->fix_cmax ? t->fix_cmax + NC : nullptr;
             c.take(&t->fix_kexp, NC);
-            c.take(&t->fix_done, 1);
         };
         Carve c;
         take(c);
         DIP_CUDA_TRY(cudaMallocAsync(&t->attr_block, c.off, s));
         c = Carve{static_cast<char*>(t->attr_block), 0};
         take(c);
-        DIP_CUDA_TRY(cudaMemsetAsync(t->S, 0, sizeof(float) * (size_t)t->nn * SR, s));
-        DIP_CUDA_TRY(cudaMemsetAsync(t->fix_cmax, 0, sizeof(unsigned) * NC, s));
-        DIP_CUDA_TRY(cudaMemsetAsync(t->fix_done, 0, sizeof(unsigned), s));
+        // (the moment rows' padding columns are never read)
+        DIP_CUDA_TRY(cudaMemsetAsync(t->fix_cmax, 0, sizeof(unsigned) * (NC + 1), s));
         t->attr_Cp_alloc = Cp;
         t->attr_dtype_alloc = dtype;
     }
