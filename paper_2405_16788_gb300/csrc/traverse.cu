@@ -144,13 +144,14 @@ k_query(const QueryArgs a) {
             }
         }
         unsigned steps = 0;
-        for (;;) {
+        // one warp step of the walk; false once the walk is over
+        auto walk_step = [&](const bool fold_here) -> bool {
             const unsigned n = __reduce_min_sync(FULL, next);
             if (MODE == kForward) {
-                if (n >= hi) break;
+                if (n >= hi) return false;
             } else if ((n >= hi) | (steps >= nn)) {  // a well-formed tree needs at most nn steps
                 if (n < hi && lane == 0) atomicOr(a.status, kStatusTraversal);
-                break;
+                return false;
             }
             ++steps;
             const float4 geo = __ldg(&nodes[n].geo);
@@ -256,10 +257,10 @@ k_query(const QueryArgs a) {
                         }
                     }
                 }
-                if (MODE == kForward && (steps % kFoldSteps) == 0u) {
+                if (MODE == kForward && fold_here && (steps % kFoldSteps) == 0u) {
                     if (steps > nn) {  // the forward checks the bound every kFoldSteps steps
                         if (lane == 0) atomicOr(a.status, kStatusTraversal);
-                        break;
+                        return false;
                     }
                     if (kBlocked) {
 #pragma unroll
@@ -273,6 +274,18 @@ k_query(const QueryArgs a) {
                         steps <= kCutSteps * kPartCuts)
                         a.plan[(size_t)pm * kPlanWords + 1u + 4u * half + steps / kCutSteps - 1u] = n;
                 }
+            }
+            return true;
+        };
+        if (MODE == kForward) {
+            // two steps per turn: the fold (every kFoldSteps steps, an even count)
+            // is only tested after the second
+            for (;;) {
+                if (!walk_step(false)) break;
+                if (!walk_step(true)) break;
+            }
+        } else {
+            while (walk_step(true)) {
             }
         }
         if (MODE == kForward && kBlocked) {
