@@ -266,13 +266,14 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                 }
             }
             unsigned gsteps = 0;
-            for (;;) {
+            // one warp step of the walk; false once the walk is over
+            auto walk_step = [&](const bool fold_here) -> bool {
                 const unsigned n = __reduce_min_sync(FULL, next);
                 if (FWD) {
-                    if (n >= hi) break;
+                    if (n >= hi) return false;
                 } else if ((n >= hi) | (gsteps >= nn)) {  // a well-formed tree needs at most nn steps
                     if (n < hi && lane == 0) atomicOr(a.status, kStatusTraversal);
-                    break;
+                    return false;
                 }
                 ++gsteps;
                 const float4 geo = __ldg(&nodes[n].geo);
@@ -428,10 +429,10 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                         }
                     }
                 }
-                if (FWD && (gsteps % kFoldSteps) == 0u) {
+                if (FWD && fold_here && (gsteps % kFoldSteps) == 0u) {
                     if (gsteps > nn) {  // checked every kFoldSteps steps
                         if (lane == 0) atomicOr(a.status, kStatusTraversal);
-                        break;
+                        return false;
                     }
 #pragma unroll
                     for (int i = 0; i < NV; ++i) {
@@ -442,6 +443,18 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                     if (RANGED && a.plan && c0 == 0 && lane == 0 && (gsteps & (kCutSteps - 1u)) == 0u &&
                         gsteps <= kCutSteps * kPartCuts)
                         a.plan[(size_t)pm * kPlanWords + 1u + 4u * half + gsteps / kCutSteps - 1u] = n;
+                }
+                return true;
+            };
+            if (FWD) {
+                // two steps per turn: the fold (every kFoldSteps steps, an even
+                // count) is only tested after the second
+                for (;;) {
+                    if (!walk_step(false)) break;
+                    if (!walk_step(true)) break;
+                }
+            } else {
+                while (walk_step(true)) {
                 }
             }
             steps += gsteps;
