@@ -420,7 +420,10 @@ __global__ void __launch_bounds__(kTopThreads) k_geom_level(int l_hi, int l_lo,
 
 // r~_t = max over the node's points of the float distance to the float
 // centroid (fixed operation order).  One thread per point walks its ancestors;
-// lanes at the same node combine with a warp max before one atomicMax.
+// lanes at the same node combine with a warp max before one atomicMax, which is
+// skipped when the node already holds as much: the values only grow, so a
+// stale read can only cost an atomic, and the upper nodes (the root takes one
+// candidate per warp of the whole cloud) stop serialising on one address.
 __global__ void k_radius(int64_t n, const PointRec* __restrict__ pts,
                          const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ parent,
                          const float4* __restrict__ cen4, unsigned int* __restrict__ rbits) {
@@ -442,7 +445,7 @@ __global__ void k_radius(int64_t n, const PointRec* __restrict__ pts,
             }
             const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)t);
             const unsigned int m = __reduce_max_sync(peers, bits);
-            if (t >= 0 && lane == __ffs(peers) - 1) atomicMax(&rbits[t], m);
+            if (t >= 0 && lane == __ffs(peers) - 1 && m > rbits[t]) atomicMax(&rbits[t], m);
             if (t >= 0) t = parent[t];
         }
     }
