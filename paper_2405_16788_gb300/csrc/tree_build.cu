@@ -171,20 +171,27 @@ __device__ int64_t run_end(const uint32_t* __restrict__ c, int64_t n, uint32_t c
 // Runs starting at sorted point i that are nodes.  Bit l of the returned mask:
 // the level-l run starting at i is a node; bit l of *imask: it is internal.
 // e[l] receives the end of the level-l run holding i, for the levels visited.
-__device__ uint32_t analyze_point(const uint32_t* __restrict__ c, int64_t n, int64_t i,
-                                  int leaf_size, int max_depth, int64_t* e, uint32_t* imask) {
+// The loops run over all kMaxLevel + 1 levels with the bounds as guards, so
+// that they unroll and e stays in registers.
+__device__ __forceinline__ uint32_t analyze_point(const uint32_t* __restrict__ c, int64_t n,
+                                                  int64_t i, int leaf_size, int max_depth,
+                                                  int64_t (&e)[kMaxLevel + 2], uint32_t* imask) {
     const uint32_t ci = c[i];
     const int s = (i == 0) ? 0 : lcp_digits(c[i - 1], ci) + 1;
     *imask = 0;
     if (s > max_depth) return 0;
     const int lmin = s > 0 ? s - 1 : 0;
     int64_t lb = i + 1;
-    for (int l = max_depth; l >= lmin; --l) {
+#pragma unroll
+    for (int l = kMaxLevel; l >= 0; --l) {
+        if (l > max_depth || l < lmin) continue;
         lb = run_end(c, n, ci, l, lb);
         e[l] = lb;
     }
     uint32_t mask = 0;
-    for (int l = s; l <= max_depth; ++l) {
+#pragma unroll
+    for (int l = 0; l <= kMaxLevel; ++l) {
+        if (l < s || l > max_depth) continue;
         const int64_t cnt = e[l] - i;
         if (l < max_depth && cnt > leaf_size && e[l + 1] < e[l]) {  // branches at digit l
             mask |= 1u << l;
@@ -227,7 +234,8 @@ __global__ void k_topo_count(const uint32_t* __restrict__ c, int64_t n, int leaf
         const uint32_t mask = analyze_point(c, n, i, leaf_size, max_depth, e, &im);
         cnt[i] = __popc(mask);
         tmask[i] = mask | (im << 16);
-        for (int l = 0; l <= max_depth; ++l)
+#pragma unroll
+        for (int l = 0; l <= kMaxLevel; ++l)  // no bit above max_depth is set
             if (mask & (1u << l)) estage[i * (kMaxLevel + 1) + l] = (int32_t)e[l];
     }
 }
