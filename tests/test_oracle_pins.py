@@ -355,3 +355,19 @@ def test_node_moments_follow_definition():
     bf = oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, far)
     rel = np.abs(bh - bf) / np.abs(bf)
     assert np.all(rel[0] < 0.05) and np.all(rel[2] < rel[0] + 1e-9)
+
+
+def test_far_test_is_strict_and_scales_with_beta():
+    """Alg. 1's far test ||x - p~|| > beta r~ (reading: strict).  Values chosen
+    so that every float operation is exact: a 3-4-5 triangle."""
+    c = [0.0, 0.0, 0.0]
+    assert not oracle.far_test([3.0, 4.0, 0.0], c, 2.5, 2.0)   # on the sphere: not far
+    assert oracle.far_test([3.0, 4.0, 0.125], c, 2.5, 2.0)     # just outside
+    assert not oracle.far_test([3.0, 3.875, 0.0], c, 2.5, 2.0)  # just inside
+    assert oracle.far_test([3.0, 4.0, 0.0], c, 2.5, 1.5)       # beta scales the radius
+    assert not oracle.far_test([3.0, 4.0, 0.0], c, 2.5, 2.5)
+    assert oracle.far_test([0.0, 0.0, 1e-3], c, 0.0, 2.0)      # a zero-radius node is far ...
+    assert not oracle.far_test(c, c, 0.0, 2.0)                 # ... unless the query is on it
+    # the offset is taken from the node centre, per axis
+    assert not oracle.far_test([10.0, 20.0, 30.0], [7.0, 16.0, 30.0], 2.5, 2.0)
+    assert oracle.far_test([10.0, 20.0, 30.0], [7.0, 16.0, 29.5], 2.5, 2.0)
