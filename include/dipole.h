@@ -323,23 +323,27 @@ int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
                         const int64_t* dims, float beta, float* out, void* stream);
 
 /*
- * Per-query traversal counts: counts[j] = {nodes tested, nodes taken as far,
- * leaf points summed} (int32 [q,3], device).  Same traversal and decisions as
- * dipole_forward; used for the roofline's algorithmic bytes and to check the
- * traversal decisions against the oracle.
+ * Per-query traversal counts of Alg. 1's PrimalQuery: counts[j] = {nodes
+ * tested, nodes taken as far, leaf points summed} (int32 [q,3], device).  Same
+ * traversal and decisions as dipole_forward; used for the roofline's
+ * algorithmic bytes and to check the traversal decisions against the oracle.
  */
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                         int32_t* counts, void* stream);
 
 /* Synchronize `stream`, then return and clear the device status word:
- * DIPOLE_OK, DIPOLE_ETRAVERSAL or DIPOLE_ENONFINITE. */
+ * DIPOLE_OK, DIPOLE_ETRAVERSAL or DIPOLE_ENONFINITE.  Error reporting of
+ * this library; the paper has no counterpart. */
 int dipole_sync_status(dipole_tree* tree, void* stream);
 
-/* Sizes and parameters of the tree (host struct; no device work). */
+/* Sizes and parameters of the tree (host struct; no device work).  The
+ * paper has no counterpart. */
 int dipole_tree_info_get(const dipole_tree* tree, dipole_tree_info* info);
 
 /*
- * Copy the tree to HOST arrays (synchronizes `stream`).  Any pointer may be
+ * Copy the tree to HOST arrays (synchronizes `stream`): the octree of Sec. 6.1
+ * with its node aggregates (eq. farfield_dipole) and moments (eq.
+ * farfield_dipole_features), for checkpoints and checks.  Any pointer may be
  * NULL.  Node arrays have n_nodes entries in preorder; point arrays n_points
  * entries in Morton order.
  *   codes, perm              uint32 [n]   sorted codes; perm[i] = caller index of point i
@@ -386,14 +390,18 @@ int dipole_tree_import(const float* points, const float* normals, const float* a
                        const int32_t* skip, const int32_t* is_leaf, int64_t n_nodes,
                        const dipole_build_params* params, void* stream, dipole_tree** out);
 
-/* Release the tree and its device memory (synchronizes the device).  NULL is a no-op. */
+/* Release the tree and its device memory (synchronizes the device).  NULL is
+ * a no-op.  Resource management; the paper has no counterpart. */
 void dipole_tree_destroy(dipole_tree* tree);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none); owned by the
+ * library, valid until the next failed call on this thread.  The paper has no
+ * counterpart. */
 const char* dipole_last_error(void);
 
 /* Number of CUDA kernels this library has launched in this process (all
- * threads, all trees).  Host counter, no device work; for accounting. */
+ * threads, all trees).  Host counter, no device work; for accounting.  The
+ * paper has no counterpart. */
 uint64_t dipole_kernel_launches(void);
 
 #ifdef __cplusplus

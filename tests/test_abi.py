@@ -109,3 +109,24 @@ def test_tree_import_validates_host_arrays_before_device_work(lib_path):
     assert call(level=np.array([0, 11, 1], np.int32)) == dipole.DIPOLE_EINVAL
     assert call(leaf=np.array([0, 2, 1], np.int32)) == dipole.DIPOLE_EINVAL
     assert call(nn=0) == dipole.DIPOLE_EINVAL
+
+
+def test_every_entry_point_is_documented_with_its_passage():
+    """Each declaration in include/dipole.h follows a comment that names the
+    paper passage it implements (section, equation, algorithm, appendix) or
+    states that the paper has no counterpart (one comment may head a group of
+    declarations)."""
+    src = open(HEADER).read()
+    for n in _declared():
+        i = re.search(r"^[A-Za-z].*\b%s\(" % n, src, re.M).start()  # the declaration
+        j = src.rfind("*/", 0, i)
+        k = src.rfind("/*", 0, j)
+        assert j >= 0 and k >= 0, n
+        doc = " ".join(src[k:j].replace("*", " ").split())
+        assert re.search(r"Sec\.|eq\.|Alg\.|App\.|no counterpart", doc), n
+
+
+def test_binding_has_the_same_names():
+    txt = open(os.path.join(ROOT, "paper_2405_16788_gb300", "dipole.py")).read()
+    missing = [n for n in _declared() if not re.search(r"^def %s\(" % n, txt, re.M)]
+    assert not missing, missing
