@@ -156,7 +156,7 @@ def brute_adjoint(points, normals, areas, eps, queries, g):
 
 
 def brute_forward_grad(points, normals, areas, eps, mu, queries):
-    """Plain O(NQ) spatial gradient of the dipole sum (reading R9): [Q, C, 3]."""
+    """Plain O(NQ) spatial gradient of the dipole sum (reading R9 of dipole_oracle.c): [Q, C, 3]."""
     p, nr, a = _f32(points), _f32(normals), _f32(areas)
     e = None if eps is None else _f32(eps)
     mu = _f32(mu)
@@ -172,7 +172,7 @@ def brute_forward_grad(points, normals, areas, eps, mu, queries):
 
 def brute_adjoint_geom(points, normals, areas, eps, mu, queries, g=None, gg=None):
     """Plain O(NQ) gradients of L(D, grad D) with respect to mu, the normals and
-    eps (readings R9, R10): (dmu [N, C], dn [N, 3], deps [N]) float64."""
+    eps (readings R9, R10 of dipole_oracle.c): (dmu [N, C], dn [N, 3], deps [N]) float64."""
     p, nr, a = _f32(points), _f32(normals), _f32(areas)
     e = None if eps is None else _f32(eps)
     mu = _f32(mu)
@@ -192,7 +192,7 @@ def brute_adjoint_geom(points, normals, areas, eps, mu, queries, g=None, gg=None
 
 
 class kernel:
-    """Context manager selecting the oracle's kernel (reading R11):
+    """Context manager selecting the oracle's kernel (reading R11 of dipole_oracle.c):
     "regularized" (the paper's, the default) or "desingularized"."""
 
     _codes = {"regularized": 0, "desingularized": 1}

@@ -18,7 +18,7 @@
  *   adjoint, stage 2    Sec. 6.2 (two-stage scheme); App. C, eq. (farfield_features_gradient)
  *
  * Readings of the paper that this file takes where the paper is silent or
- * ambiguous (each one is also listed in the design notes):
+ * ambiguous (the tests and the CUDA library follow the same readings):
  *   R1  The 1/(4 pi) of eq. (pcwn) is kept in the far field, in GetContribution
  *       and in IncrementGradient (the printed forms drop it).
  *   R2  rho(t) = erf(t) - 2t/sqrt(pi) exp(-t^2) with t = r/eps, as printed.

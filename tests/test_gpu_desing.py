@@ -1,4 +1,4 @@
-"""The desingularized kernel (reading R11: 1/max(r, eps)^3, the paper's
+"""The desingularized kernel (the oracle's reading R11: 1/max(r, eps)^3, the paper's
 ablation baseline) on the GPU against the oracle with the same kernel: forward
 1e-4, adjoints 1e-3, decisions bit-exact."""
 import numpy as np

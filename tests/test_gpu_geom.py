@@ -1,4 +1,4 @@
-"""GPU adjoint with respect to the normals and radii (reading R10) vs the
+"""GPU adjoint with respect to the normals and radii (the oracle's reading R10) vs the
 oracle's double-precision Barnes-Hut on the same tree: norm-wise error <= 1e-3
 per column (the adjoint tolerance), for upstream gradients of D, of grad D,
 or both; the linearity identity on the GPU; the autograd path."""

@@ -1,4 +1,4 @@
-"""GPU spatial gradient of the dipole sum (reading R9: the x-gradient of
+"""GPU spatial gradient of the dipole sum (the oracle's reading R9: the x-gradient of
 eq. dipole_sum and eq. farfield under the walk of Alg. 1) and its adjoint, vs
 the oracle's double-precision Barnes-Hut on the same tree: forward norm-wise
 error <= 1e-4 per channel and axis, adjoint <= 1e-3 (the tolerances of the

@@ -1,4 +1,4 @@
-"""Pins for the oracle's desingularized kernel (reading R11: 1/r^3 ->
+"""Pins for the oracle's desingularized kernel (the oracle's reading R11: 1/r^3 ->
 1/max(r, eps)^3, the paper's ablation baseline): equality with the singular
 kernel outside every cutoff, the closed form inside one, Barnes-Hut = brute
 force when nothing is far, and its gradients against central differences."""

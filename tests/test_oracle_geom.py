@@ -1,5 +1,5 @@
 """Pins for the oracle's gradients with respect to the normals and the
-regularization radii (reading R10): central differences of the plain sum and
+regularization radii (the oracle's reading R10): central differences of the plain sum and
 of the Barnes-Hut sum (whose far decisions do not depend on n or eps), the
 linearity of D in the normals and in mu, and the eps-derivative of the
 closed-form blurred ball indicator (Prop. 1)."""
@@ -111,7 +111,7 @@ def test_bh_geom_gradients_match_central_differences_of_bh_sum():
         e[m] = vm
         lm, _ = _bh_loss(c, w.mu, x, g, G, beta, eps=e)
         # rounding of L itself limits the difference quotient to ~1e-13 |L| / step;
-        # eps~ of a leaf is a float sum (reading R7), whose rounding moves by whole
+        # eps~ of a leaf is a float sum (the oracle's reading R7), whose rounding moves by whole
         # float units under a step of 1e-4 eps_m: 2e-4 relative
         assert abs((lp - lm) / st - deps[m]) <= 2e-4 * abs(deps[m]) + 1e-13 * abs(lp) / st
 

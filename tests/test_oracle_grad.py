@@ -1,4 +1,4 @@
-"""Pins for the oracle's spatial gradient of the dipole sum (reading R9) and its
+"""Pins for the oracle's spatial gradient of the dipole sum (the oracle's reading R9) and its
 adjoint, against finite differences of the plain sum, closed forms and the
 adjoint identity."""
 import math

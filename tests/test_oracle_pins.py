@@ -214,7 +214,7 @@ def test_bh_equals_brute_force_when_nothing_is_far():
 def test_bh_single_point_leaves_far_field_is_exact_per_point():
     """With single-point leaves (the paper's tree, Sec. 6.1) a leaf has radius 0,
     so it is always far and its far field (eq. farfield) is that point's exact
-    term, up to the float rounding of the leaf's sums (reading R7): a two-point
+    term, up to the float rounding of the leaf's sums (the oracle's reading R7): a two-point
     cloud with leaf size 1, queried inside beta times the root radius,
     reproduces brute force."""
     p = np.array([[0.0, 0, 0], [0.3, 0.1, -0.2]], np.float32)
@@ -344,7 +344,7 @@ def test_node_moments_follow_definition():
     e = T.export()
     A = c.areas.astype(np.float64)
     P = c.points.astype(np.float64)
-    # leaves sum in float (reading R7): a few float roundings of the exact sums
+    # leaves sum in float (the oracle's reading R7): a few float roundings of the exact sums
     assert abs(e["area"][0] - A.sum()) < 1e-6 * A.sum()
     cen = (A[:, None] * P).sum(0) / A.sum()
     assert np.allclose(e["cen"][0], cen, rtol=0, atol=2e-6)

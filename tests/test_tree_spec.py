@@ -177,7 +177,7 @@ def test_tree_invariants_scene():
         s, k = e["first"][t], e["count"][t]
         a = A[s:s + k]
         cen = (a[:, None] * P[s:s + k]).sum(0) / a.sum()
-        # leaves sum in float (reading R7): a few float roundings of the exact sums
+        # leaves sum in float (the oracle's reading R7): a few float roundings of the exact sums
         assert abs(e["area"][t] - a.sum()) <= 1e-6 * a.sum()
         assert np.allclose(e["cen"][t], cen, rtol=0, atol=2e-6)
         d = np.linalg.norm(P[s:s + k] - e["cen32"][t].astype(np.float64), axis=1).max()
