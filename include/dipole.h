@@ -170,7 +170,10 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
  * The array (about 4.5 MB) exists on every GPU that loads this library and
  * stays there until the process exits.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) for that device; make
- * that first call before any stream capture.  Every call uses the same array
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: after a cudaDeviceReset it is stale, and this entry
+ * point must not be called again in that process.  The tree's device must be
+ * the current device (else DIPOLE_EINVAL).  Every call uses the same array
  * and leaves its contents behind; the work counter is cleared at the start of
  * each call.  Calls that overlap on the GPU (different streams or threads,
  * any tree) race on the array and give wrong results: serialize them.
@@ -199,6 +202,35 @@ int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_
  */
 int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float beta,
                    const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream);
+
+/*
+ * The adjoint in its two stages as separate calls, for a data-parallel step
+ * (Sec. 6.2, App. C): stage 1 is a sum over queries, so ranks holding
+ * disjoint query batches can each run stage 1 into their own accumulator,
+ * sum the accumulators (an all-reduce), and run stage 2 once on the sum; the
+ * result equals dipole_adjoint over all the queries (up to float rounding
+ * of the sums' order).
+ *
+ * dipole_adjoint_acc_size: *floats = entries of an accumulator for the tree's
+ *   current channel count (node sums dS_t^c, then opened-leaf sums
+ *   dmu_near_m^c; the layout is internal to the library and fixed between
+ *   refits with the same channel count; entries are summed elementwise).
+ * dipole_adjoint_stage1: Alg. 1 AdjointQuery (eq. farfield_gradient) for the
+ *   given queries into acc [floats] float, device; accumulate 0 overwrites
+ *   acc, 1 adds to it.  plan_perm, plan_cost: NULL, or the plan of a
+ *   dipole_forward_planned on the same queries.  Does not touch the tree's
+ *   own adjoint scratch: stage-1 calls with different accumulators may
+ *   overlap.
+ * dipole_adjoint_stage2: eq. farfield_features_gradient from acc into
+ *   grad_attrs [n, channels] float (caller's point order); accumulate 0 or 1.
+ * Errors: as dipole_adjoint; DIPOLE_ESTATE before the first refit.
+ */
+int dipole_adjoint_acc_size(const dipole_tree* tree, int64_t* floats);
+int dipole_adjoint_stage1(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                          const float* grad_out, float* acc, int32_t accumulate,
+                          const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream);
+int dipole_adjoint_stage2(const dipole_tree* tree, const float* acc, float* grad_attrs,
+                          int32_t accumulate, void* stream);
 
 /*
  * Forward and adjoint sharing a query plan (caller-owned device buffers):
@@ -274,6 +306,23 @@ int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, floa
                         void* stream);
 
 /*
+ * Gradient of a loss of D with respect to the query positions (the chain
+ * rule through the spatial gradient of dipole_forward_grad; the paper does not
+ * differentiate in x, Sec. 6.2, but its renderer samples along rays whose
+ * positions may be trained):
+ *   grad_queries[j, k] (+)= sum_c grad_out[j, c] dD^c/dx_k (queries[j]).
+ * Same walk and far decisions as dipole_forward_grad; the per-channel
+ * gradients are summed in the kernel and never stored.
+ *
+ *   grad_out     [q, channels] float
+ *   grad_queries [q, 3] float; accumulate 0 overwrites, 1 adds
+ * Errors: as dipole_forward_grad.
+ */
+int dipole_adjoint_queries(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           const float* grad_out, float* grad_queries, int32_t accumulate,
+                           void* stream);
+
+/*
  * Adjoint with respect to the attributes, the normals and the radii.  The
  * paper trains the normals and the regularization eps besides the attributes
  * (Sec. 7, inverse rendering) but states the adjoint only for the attributes
@@ -330,6 +379,20 @@ int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
  */
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                         int32_t* counts, void* stream);
+
+/*
+ * The traversal counts of each 32-query packet as the warp walks it (the
+ * packets of the internal Hilbert-curve sort, in that order), for the
+ * roofline's per-warp bytes: packet_counts[p] = {warp steps (the union of the
+ * lanes' tested nodes), steps at which some lane took the node as far (the
+ * warp fetches its moment row), points of leaves some lane opened (the warp
+ * fetches their records), valid lanes}, int32 [ceil(q/32), 4], device.
+ * counts [q, 3] as dipole_query_counts, or NULL.  Diagnostics; the paper has
+ * no counterpart (packet queries are its future work, Sec. 6.3).
+ */
+int dipole_query_packet_counts(const dipole_tree* tree, const float* queries, int64_t q,
+                               float beta, int32_t* counts, int32_t* packet_counts,
+                               void* stream);
 
 /* Synchronize `stream`, then return and clear the device status word:
  * DIPOLE_OK, DIPOLE_ETRAVERSAL or DIPOLE_ENONFINITE.  Error reporting of
@@ -403,6 +466,13 @@ const char* dipole_last_error(void);
  * threads, all trees).  Host counter, no device work; for accounting.  The
  * paper has no counterpart. */
 uint64_t dipole_kernel_launches(void);
+
+/* Number of device allocations this library has made in this process (all
+ * threads, all trees): every one is a stream-ordered cudaMallocAsync from the
+ * device's default memory pool.  Host counter, no device work; lets a caller
+ * (or a test) check that a call allocates nothing.  The paper has no
+ * counterpart. */
+uint64_t dipole_device_allocations(void);
 
 #ifdef __cplusplus
 }

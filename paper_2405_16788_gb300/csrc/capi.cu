@@ -14,6 +14,7 @@
 namespace {
 thread_local std::string g_last_error;
 std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_allocs{0};
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -39,6 +40,18 @@ void free_tree_memory(dipole_tree* t) {
         if (b) cudaFree(b);
 }
 
+// Kernels of a query run on the current device and follow the tree's device
+// pointers: the tree's device must be current.
+int check_device(const dipole_tree* t, const char* fn) {
+    int dev = -1;
+    DIP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != t->device)
+        return dip_fail(DIPOLE_EINVAL, std::string(fn) + ": the current CUDA device (" +
+                                           std::to_string(dev) + ") is not the tree's device (" +
+                                           std::to_string(t->device) + "); make it current first");
+    return DIPOLE_OK;
+}
+
 int status_to_code(int st) {
     if (st & dip::kStatusTraversal) return DIPOLE_ETRAVERSAL;
     if (st & dip::kStatusNonFinite) return DIPOLE_ENONFINITE;
@@ -47,6 +60,11 @@ int status_to_code(int st) {
 }  // namespace
 
 void dip::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t dip::dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(p, bytes, s);
+}
 
 int dip_fail(int code, const std::string& msg) {
     g_last_error = msg;
@@ -66,6 +84,8 @@ extern "C" {
 const char* dipole_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t dipole_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t dipole_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 int dipole_build_tree(const float* points, const float* normals, const float* areas,
                       const float* radii, int64_t n, const dipole_build_params* params,
@@ -170,6 +190,7 @@ int dipole_tree_import(const float* points, const float* normals, const float* a
 int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,
                  void* stream) {
     if (!tree || !attrs) return dip_fail(DIPOLE_EINVAL, "dipole_refit: tree and attrs are required");
+    if (int rc_dev = check_device(tree, "dipole_refit")) return rc_dev;
     if (channels < 1 || channels > dip::kMaxChannels)
         return dip_fail(DIPOLE_EINVAL, "dipole_refit: channels must be in [1, 64]");
     if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
@@ -180,6 +201,7 @@ int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t
 int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                    float* out, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_forward")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward: call dipole_refit first");
     if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_forward: q must be >= 0");
     if (q > 0 && (!queries || !out))
@@ -196,6 +218,7 @@ int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, flo
 int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                            float* out, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_forward_noalloc")) return rc_dev;
     if (tree->C == 0)
         return dip_fail(DIPOLE_ESTATE, "dipole_forward_noalloc: call dipole_refit first");
     if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_forward_noalloc: q must be >= 0");
@@ -213,6 +236,7 @@ int dipole_forward_noalloc(const dipole_tree* tree, const float* queries, int64_
 int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float beta,
                    const float* grad_out, float* grad_attrs, int32_t accumulate, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint: call dipole_refit first");
     if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: q must be >= 0");
     if (!grad_attrs) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint: grad_attrs is required");
@@ -229,9 +253,78 @@ int dipole_adjoint(dipole_tree* tree, const float* queries, int64_t q, float bet
     return dip::query(tree, c, as_stream(stream));
 }
 
+int dipole_adjoint_acc_size(const dipole_tree* tree, int64_t* floats) {
+    if (!tree || !floats) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_acc_size: NULL argument");
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_acc_size: call dipole_refit first");
+    *floats = dip::adjoint_acc_floats(tree);
+    return DIPOLE_OK;
+}
+
+int dipole_adjoint_stage1(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                          const float* grad_out, float* acc, int32_t accumulate,
+                          const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_stage1")) return rc_dev;
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_stage1: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: q must be in [0, 2^31)");
+    if (!acc) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: acc is required");
+    if (q > 0 && (!queries || !grad_out))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: queries and grad_out are required");
+    if ((plan_perm == nullptr) != (plan_cost == nullptr))
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: plan_perm and plan_cost go together");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage1: accumulate must be 0 or 1");
+    dip::QueryCall c;
+    c.mode = dip::kAdjoint;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.acc = acc; c.accumulate = accumulate;
+    c.plan_perm = const_cast<uint32_t*>(plan_perm);
+    c.plan_cost = const_cast<uint32_t*>(plan_cost);
+    c.plan_in = plan_perm != nullptr;
+    return dip::query(tree, c, as_stream(stream));
+}
+
+int dipole_adjoint_stage2(const dipole_tree* tree, const float* acc, float* grad_attrs,
+                          int32_t accumulate, void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage2: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_stage2")) return rc_dev;
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_stage2: call dipole_refit first");
+    if (!acc || !grad_attrs)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage2: acc and grad_attrs are required");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_stage2: accumulate must be 0 or 1");
+    const int64_t nodes = tree->nn * (int64_t)dip::srow(tree->Cp);
+    return dip::stage2(tree, acc, acc + nodes, grad_attrs, accumulate, as_stream(stream));
+}
+
+int dipole_adjoint_queries(const dipole_tree* tree, const float* queries, int64_t q, float beta,
+                           const float* grad_out, float* grad_queries, int32_t accumulate,
+                           void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_queries")) return rc_dev;
+    if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_queries: call dipole_refit first");
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: q must be in [0, 2^31)");
+    if (q > 0 && (!queries || !grad_out || !grad_queries))
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_adjoint_queries: queries, grad_out and grad_queries are required");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: beta must be > 0");
+    if (accumulate != 0 && accumulate != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: accumulate must be 0 or 1");
+    if (q == 0) return DIPOLE_OK;
+    dip::QueryCall c;
+    c.mode = dip::kForwardGradDot;
+    c.queries = queries; c.q = q; c.beta = beta;
+    c.g = grad_out; c.gq = grad_queries; c.accumulate = accumulate;
+    return dip::query(tree, c, as_stream(stream));
+}
+
 int dipole_forward_planned(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                            float* out, uint32_t* plan_perm, uint32_t* plan_cost, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_forward_planned")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_planned: call dipole_refit first");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_forward_planned: q must be in [0, 2^31)");
@@ -250,6 +343,7 @@ int dipole_adjoint_planned(dipole_tree* tree, const float* queries, int64_t q, f
                            const float* grad_out, float* grad_attrs, int32_t accumulate,
                            const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_planned")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_planned: call dipole_refit first");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_planned: q must be in [0, 2^31)");
@@ -273,6 +367,7 @@ int dipole_forward_grad(const dipole_tree* tree, const float* queries, int64_t q
                         float* out, float* grad_x, uint32_t* plan_perm, uint32_t* plan_cost,
                         void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_forward_grad")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_grad: call dipole_refit first");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: q must be in [0, 2^31)");
@@ -294,6 +389,7 @@ int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, floa
                         int32_t accumulate, const uint32_t* plan_perm, const uint32_t* plan_cost,
                         void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_grad")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_grad: call dipole_refit first");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: q must be in [0, 2^31)");
@@ -321,6 +417,7 @@ int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, floa
                         float* grad_normals, float* grad_radii, int32_t accumulate,
                         const uint32_t* plan_perm, const uint32_t* plan_cost, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_adjoint_geom")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_geom: call dipole_refit first");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: q must be in [0, 2^31)");
@@ -353,6 +450,7 @@ int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, floa
 int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
                         const int64_t* dims, float beta, float* out, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_forward_grid")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_grid: call dipole_refit first");
     if (!lo || !dims || !out)
         return dip_fail(DIPOLE_EINVAL, "dipole_forward_grid: lo, dims and out are required");
@@ -382,6 +480,7 @@ int dipole_forward_grid(const dipole_tree* tree, const float* lo, float spacing,
 int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q, float beta,
                         int32_t* counts, void* stream) {
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_query_counts")) return rc_dev;
     if (q < 0) return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: q must be >= 0");
     if (q > 0 && (!queries || !counts))
         return dip_fail(DIPOLE_EINVAL, "dipole_query_counts: queries and counts are required");
@@ -391,6 +490,24 @@ int dipole_query_counts(const dipole_tree* tree, const float* queries, int64_t q
     dip::QueryCall c;
     c.mode = dip::kCount;
     c.queries = queries; c.q = q; c.beta = beta; c.counts = counts;
+    return dip::query(tree, c, as_stream(stream));
+}
+
+int dipole_query_packet_counts(const dipole_tree* tree, const float* queries, int64_t q,
+                               float beta, int32_t* counts, int32_t* packet_counts,
+                               void* stream) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_query_packet_counts: tree is NULL");
+    if (int rc_dev = check_device(tree, "dipole_query_packet_counts")) return rc_dev;
+    if (q < 0 || q > (int64_t)INT32_MAX)
+        return dip_fail(DIPOLE_EINVAL, "dipole_query_packet_counts: q must be in [0, 2^31)");
+    if (q > 0 && (!queries || !packet_counts))
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_query_packet_counts: queries and packet_counts are required");
+    if (!(beta > 0.0f)) return dip_fail(DIPOLE_EINVAL, "dipole_query_packet_counts: beta must be > 0");
+    if (q == 0) return DIPOLE_OK;
+    dip::QueryCall c;
+    c.mode = dip::kCount;
+    c.queries = queries; c.q = q; c.beta = beta; c.counts = counts; c.ucounts = packet_counts;
     return dip::query(tree, c, as_stream(stream));
 }
 

@@ -167,6 +167,10 @@ void probe_l2(const void* buf, int64_t bytes, int passes, float* sink, cudaStrea
 // Counts the library's kernel launches (dipole_kernel_launches).
 void note_launch();
 
+// Every device allocation of the library goes through here: stream-ordered
+// cudaMallocAsync, counted for dipole_device_allocations.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+
 
 // Padded channel counts with a compiled kernel instantiation.
 int padded_channels(int C);

@@ -41,7 +41,10 @@ struct QueryArgs {
     float* dmu;
     float* dE;          // [nn] d eps~_t sums (kAdjointGeom)
     float* dgeo;        // [n, 4] opened-leaf normal (xyz) and radius (w) terms (kAdjointGeom)
+    float* gq;          // dL/dx [q, 3] (kForwardGradDot)
+    int accumulate;     // gq: add to it (non-ranged; ranged items always add)
     int32_t* counts;
+    int32_t* ucounts;   // [packets, 4] warp steps, far steps, opened-leaf point loads, lanes (kCount)
     unsigned long long* work;
     const uint32_t* porder;  // packet (or item) order, or NULL for sorted order
     GridSpec grid;           // dense-grid queries instead of q / qperm

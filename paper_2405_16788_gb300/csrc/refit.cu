@@ -581,11 +581,12 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
 }
 
 template <int CP>
-void launch_stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s) {
+void launch_stage2(const dipole_tree* t, const float* dS, const float* dmu, float* grad,
+                   int accumulate, cudaStream_t s) {
     int64_t blocks = (t->nn + 127) / 128;
     int64_t cap = (int64_t)num_sms() * 16;
     note_launch(); k_stage2<CP><<<(unsigned)(blocks < cap ? blocks : cap), 128, 0, s>>>(
-        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, t->dS, t->dmu, t->C,
+        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, dS, dmu, t->C,
         accumulate, grad);
 }
 
@@ -625,7 +626,7 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
         };
         Carve c;
         take(c);
-        DIP_CUDA_TRY(cudaMallocAsync(&t->attr_block, c.off, s));
+        DIP_CUDA_TRY(dev_alloc((void**)&t->attr_block, c.off, s));
         c = Carve{static_cast<char*>(t->attr_block), 0};
         take(c);
         // (the moment rows' padding columns are never read)
@@ -657,15 +658,20 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
     return 0;
 }
 
-int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s) {
+int64_t adjoint_acc_floats(const dipole_tree* t) {
+    return t->nn * (int64_t)srow(t->Cp) + t->n * (int64_t)t->Cp;
+}
+
+int stage2(const dipole_tree* t, const float* dS, const float* dmu, float* grad, int accumulate,
+           cudaStream_t s) {
     switch (t->Cp) {
-        case 1: launch_stage2<1>(t, grad, accumulate, s); break;
-        case 2: launch_stage2<2>(t, grad, accumulate, s); break;
-        case 4: launch_stage2<4>(t, grad, accumulate, s); break;
-        case 8: launch_stage2<8>(t, grad, accumulate, s); break;
-        case 16: launch_stage2<16>(t, grad, accumulate, s); break;
-        case 32: launch_stage2<32>(t, grad, accumulate, s); break;
-        case 64: launch_stage2<64>(t, grad, accumulate, s); break;
+        case 1: launch_stage2<1>(t, dS, dmu, grad, accumulate, s); break;
+        case 2: launch_stage2<2>(t, dS, dmu, grad, accumulate, s); break;
+        case 4: launch_stage2<4>(t, dS, dmu, grad, accumulate, s); break;
+        case 8: launch_stage2<8>(t, dS, dmu, grad, accumulate, s); break;
+        case 16: launch_stage2<16>(t, dS, dmu, grad, accumulate, s); break;
+        case 32: launch_stage2<32>(t, dS, dmu, grad, accumulate, s); break;
+        case 64: launch_stage2<64>(t, dS, dmu, grad, accumulate, s); break;
         default: return dip_fail(-1, "dipole_adjoint: unsupported channel count");
     }
     DIP_CUDA_TRY(cudaGetLastError());
@@ -673,8 +679,8 @@ int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s) {
 }
 
 int ensure_geom_scratch(dipole_tree* t, cudaStream_t s) {
-    if (!t->dE) DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dE, sizeof(float) * (size_t)t->nn, s));
-    if (!t->dgeo) DIP_CUDA_TRY(cudaMallocAsync((void**)&t->dgeo, sizeof(float) * 4 * (size_t)t->n, s));
+    if (!t->dE) DIP_CUDA_TRY(dev_alloc((void**)&t->dE, sizeof(float) * (size_t)t->nn, s));
+    if (!t->dgeo) DIP_CUDA_TRY(dev_alloc((void**)&t->dgeo, sizeof(float) * 4 * (size_t)t->n, s));
     return 0;
 }
 

@@ -124,6 +124,7 @@ k_query(const QueryArgs a) {
             }
         };
         int n_tested = 0, n_far = 0, n_pts = 0;
+        unsigned u_far = 0, u_pts = 0;  // warp counts (kCount with a.ucounts)
 
         unsigned next = valid ? lo : nn;
         if (RANGED && lo > 0u && lo < nn) {
@@ -182,6 +183,12 @@ k_query(const QueryArgs a) {
                     ++n_tested;
                     if (far) ++n_far;
                     else if (leaf) n_pts += meta.z;
+                }
+                if (a.ucounts) {
+                    // the warp's own fetches: the moment row of a node some lane
+                    // takes as far, the points of a leaf some lane opens
+                    if (__any_sync(FULL, far)) ++u_far;
+                    if (__any_sync(FULL, open_leaf)) u_pts += (unsigned)meta.z;
                 }
             } else {
                 if (__any_sync(FULL, far)) {
@@ -304,10 +311,20 @@ k_query(const QueryArgs a) {
                     if (RANGED) atomicAdd(a.out + qo * a.C + c, v);  // the two parts of a packet
                     else a.out[qo * a.C + c] = v;
                 }
-            } else if (MODE == kCount) {
+            } else if (MODE == kCount && a.counts) {
                 a.counts[3 * qo] = n_tested;
                 a.counts[3 * qo + 1] = n_far;
                 a.counts[3 * qo + 2] = n_pts;
+            }
+        }
+        if (MODE == kCount && a.ucounts) {
+            const unsigned lanes = __popc(__ballot_sync(FULL, valid));
+            if (lane == 0) {
+                int32_t* u = a.ucounts + 4 * pm;
+                u[0] = (int32_t)steps;
+                u[1] = (int32_t)u_far;
+                u[2] = (int32_t)u_pts;
+                u[3] = (int32_t)lanes;
             }
         }
     }
@@ -633,7 +650,10 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.dmu = nullptr;
     a.dE = nullptr;
     a.dgeo = nullptr;
+    a.gq = nullptr;
+    a.accumulate = 0;
     a.counts = nullptr;
+    a.ucounts = nullptr;
     a.work = work;
     a.porder = nullptr;  // packets in sorted order
     a.plan = nullptr;
@@ -686,7 +706,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     Carve cs;
     take(cs);
     void* block = nullptr;
-    DIP_CUDA_TRY(cudaMallocAsync(&block, cs.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&block, cs.off, s));
     cs = Carve{static_cast<char*>(block), 0};
     take(cs);
     unsigned long long* work = reinterpret_cast<unsigned long long*>(small);
@@ -728,6 +748,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         if (call.out) DIP_CUDA_TRY(cudaMemsetAsync(call.out, 0, sizeof(float) * (size_t)q * t->C, s));
         if (call.gout)
             DIP_CUDA_TRY(cudaMemsetAsync(call.gout, 0, sizeof(float) * 3 * (size_t)q * t->C, s));
+        if (call.gq && !call.accumulate)
+            DIP_CUDA_TRY(cudaMemsetAsync(call.gq, 0, sizeof(float) * 3 * (size_t)q, s));
         note_launch();
         k_fwd_items<<<(unsigned)((np + 7) / 8), 256, 0, s>>>(
             call.queries, idx, q, np, t->bbox, t->code, t->n, t->leaf_of, (unsigned)t->nn, items,
@@ -735,9 +757,12 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         order_place(ibucket, ni, ostate, iorder, s);
         porder = iorder;
     }
-    if (adjoint) {
-        DIP_CUDA_TRY(cudaMemsetAsync(t->dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
-        DIP_CUDA_TRY(cudaMemsetAsync(t->dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
+    // stage-1 sums: the tree's scratch, or the caller's accumulator
+    float* dS = call.acc ? call.acc : t->dS;
+    float* dmu = call.acc ? call.acc + (size_t)t->nn * SR : t->dmu;
+    if (adjoint && !(call.acc && call.accumulate)) {
+        DIP_CUDA_TRY(cudaMemsetAsync(dS, 0, sizeof(float) * (size_t)t->nn * SR, s));
+        DIP_CUDA_TRY(cudaMemsetAsync(dmu, 0, sizeof(float) * (size_t)t->n * t->Cp, s));
     }
     if (mode == kAdjointGeom) {
         DIP_CUDA_TRY(cudaMemsetAsync(t->dE, 0, sizeof(float) * (size_t)t->nn, s));
@@ -763,11 +788,14 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.gout = call.gout;
         a.g = call.g;
         a.gg = call.gg;
-        a.dS = t->dS;
-        a.dmu = t->dmu;
+        a.dS = dS;
+        a.dmu = dmu;
         a.dE = t->dE;
         a.dgeo = t->dgeo;
+        a.gq = call.gq;
+        a.accumulate = call.accumulate;
         a.counts = call.counts;
+        a.ucounts = call.ucounts;
         a.work = work;
         a.porder = porder;
         a.plan = plan_w;
@@ -791,7 +819,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         else if (mode == kCount) rc = dispatch<kCount>(t, a, s);
         else rc = dispatch_grad(t, mode, a, s);
     }
-    if (rc == 0 && adjoint && call.grad) rc = stage2(t, call.grad, call.accumulate, s);
+    if (rc == 0 && adjoint && call.grad && !call.acc)
+        rc = stage2(t, t->dS, t->dmu, call.grad, call.accumulate, s);
     if (rc == 0 && mode == kAdjointGeom)
         rc = stage2_geom(t, call.grad_n, call.grad_eps, call.accumulate, s);
     cudaFreeAsync(block, s);

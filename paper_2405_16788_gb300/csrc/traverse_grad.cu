@@ -160,10 +160,11 @@ __device__ __forceinline__ void desing_factors(float d2, float inv_eps, float& a
 // traversal (two per packet in the forward, the plan's cuts in the adjoints);
 // the same range holds for every channel group, whose walks are identical.
 template <int CG, typename AT, int MODE, bool RANGED>
-__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kAdjointGeom) ? 3 : 2)
+__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kForwardGradDot || MODE == kAdjointGeom) ? 3 : 2)
     k_query_grad(const QueryArgs a) {
     static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
-    constexpr bool FWD = MODE == kForwardGrad;
+    constexpr bool FWD = MODE == kForwardGrad || MODE == kForwardGradDot;
+    constexpr bool DOT = MODE == kForwardGradDot;  // only sum_c g^c grad D^c
     constexpr bool GEOM = MODE == kAdjointGeom;  // also the normal and radius gradients
     constexpr unsigned FULL = 0xffffffffu;
     constexpr unsigned kFoldSteps = 16;
@@ -200,6 +201,9 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
         int ord[CG];
         lane_channel_order<CG>(lane, ord);
         unsigned steps = 0;
+        float gq[DOT ? 3 : 1];  // kForwardGradDot: sum_c g^c grad D^c
+#pragma unroll
+        for (int k = 0; k < (DOT ? 3 : 1); ++k) gq[k] = 0.f;
 
         for (int c0 = 0; c0 < Cp; c0 += CG) {
             // forward: blocked Kahan sums (plain partial sums folded every
@@ -466,6 +470,13 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                     for (int c = 0; c < CG; ++c) {
                         if (c0 + c >= a.C) continue;
                         const int64_t o = qo * a.C + c0 + c;
+                        if constexpr (DOT) {
+                            const float gc = a.g[o];
+#pragma unroll
+                            for (int k = 0; k < 3; ++k)
+                                gq[k] = fmaf(gc, __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi, gq[k]);
+                            continue;
+                        }
                         // ranged: the two parts of a packet add into the zeroed outputs
                         const float d = __fsub_rn(acc[4 * c], cmp[4 * c]) * kInv4Pi;
                         if (a.out) {
@@ -480,6 +491,15 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kA
                         }
                     }
                 }
+            }
+        }
+        if (DOT && valid) {
+            // dL/dx of the query; ranged: the two parts add into the output
+#pragma unroll
+            for (int k = 0; k < (DOT ? 3 : 0); ++k) {
+                float* dst = a.gq + 3 * qo + k;
+                if (RANGED) atomicAdd(dst, gq[k]);
+                else *dst = a.accumulate ? *dst + gq[k] : gq[k];
             }
         }
         if (a.plan && lane == 0) atomicAdd(a.plan + (size_t)pm * kPlanWords, steps);
@@ -521,6 +541,7 @@ void launch_grad_cg(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
 int dispatch_grad(const dipole_tree* t, int mode, const QueryArgs& a, cudaStream_t s) {
     if (t->Cp != 1 && t->Cp != 2 && t->Cp % 4 != 0) return dip_fail(-1, "unsupported channel count");
     if (mode == kForwardGrad) launch_grad_cg<kForwardGrad>(t, a, s);
+    else if (mode == kForwardGradDot) launch_grad_cg<kForwardGradDot>(t, a, s);
     else if (mode == kAdjointGrad) launch_grad_cg<kAdjointGrad>(t, a, s);
     else if (mode == kAdjointGeom) launch_grad_cg<kAdjointGeom>(t, a, s);
     else return dip_fail(-1, "dispatch_grad: not a gradient mode");

@@ -100,7 +100,11 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
 // Query modes: the dipole sum (eq. dipole_sum with Alg. 1), its adjoint, the
 // traversal counters, the sum with its spatial gradient, the adjoint of both,
 // and that adjoint extended to the normals and radii.
-enum { kForward = 0, kAdjoint = 1, kCount = 2, kForwardGrad = 3, kAdjointGrad = 4, kAdjointGeom = 5 };
+// kForwardGradDot: the spatial-gradient walk that returns only
+// sum_c g^c grad D^c per query (the chain rule of a loss of D in the query
+// positions).
+enum { kForward = 0, kAdjoint = 1, kCount = 2, kForwardGrad = 3, kAdjointGrad = 4, kAdjointGeom = 5,
+       kForwardGradDot = 6 };
 
 // One query call.  Query plan (caller-owned, optional): plan_in = false writes
 // the Morton permutation into plan_perm [q] and each packet's warp steps into
@@ -119,7 +123,13 @@ struct QueryCall {
     float* grad_n = nullptr;         // dL/dn [n, 3] (optional in kAdjointGeom)
     float* grad_eps = nullptr;       // dL/deps [n] (optional in kAdjointGeom)
     int accumulate = 0;
+    float* gq = nullptr;             // dL/dx [q, 3] = sum_c g^c grad D^c (kForwardGradDot)
+    // stage 1 only: the adjoint's node and opened-leaf sums go to acc
+    // (adjoint_acc_floats entries: dS, then dmu_near) instead of the tree's
+    // scratch, and stage 2 is not run
+    float* acc = nullptr;
     int32_t* counts = nullptr;       // [q, 3] (kCount)
+    int32_t* ucounts = nullptr;      // [ceil(q/32), 4] per-packet warp counts (kCount, optional)
     uint32_t* plan_perm = nullptr;
     uint32_t* plan_cost = nullptr;
     bool plan_in = false;
@@ -138,8 +148,13 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
                   cudaStream_t s);
 int64_t noalloc_max_queries();
 
-// Stage 2 of the adjoint (eq. farfield_features_gradient) into grad [n, C].
-int stage2(const dipole_tree* t, float* grad, int accumulate, cudaStream_t s);
+// Stage 2 of the adjoint (eq. farfield_features_gradient) into grad [n, C],
+// from the node sums dS [nn, srow(Cp)] and opened-leaf sums dmu [n, Cp].
+int stage2(const dipole_tree* t, const float* dS, const float* dmu, float* grad, int accumulate,
+           cudaStream_t s);
+
+// Entries of a stage-1 accumulator: dS [nn, srow(Cp)], then dmu [n, Cp].
+int64_t adjoint_acc_floats(const dipole_tree* t);
 
 // Scratch of the normal/radius adjoint (dE, dgeo), allocated on first use.
 int ensure_geom_scratch(dipole_tree* t, cudaStream_t s);

@@ -513,7 +513,7 @@ int alloc_point_state(dipole_tree* t, cudaStream_t s) {
     };
     Carve c;
     take(c);
-    DIP_CUDA_TRY(cudaMallocAsync(&t->point_block, c.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&t->point_block, c.off, s));
     c = Carve{static_cast<char*>(t->point_block), 0};
     take(c);
     DIP_CUDA_TRY(cudaMemsetAsync(t->bbox + 8, 0, 8 * sizeof(float), s));
@@ -534,7 +534,7 @@ int alloc_topology(dipole_tree* t, int64_t nn, cudaStream_t s) {
     };
     Carve c;
     take(c);
-    DIP_CUDA_TRY(cudaMallocAsync(&t->topo_block, c.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&t->topo_block, c.off, s));
     c = Carve{static_cast<char*>(t->topo_block), 0};
     take(c);
     return 0;
@@ -579,8 +579,8 @@ int alloc_nodes(dipole_tree* t, NodeScratch& ns, cudaStream_t s) {
     Carve c, ct;
     take(c);
     take_tmp(ct);
-    DIP_CUDA_TRY(cudaMallocAsync(&t->node_block, c.off, s));
-    DIP_CUDA_TRY(cudaMallocAsync(&ns.tmp, ct.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&t->node_block, c.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&ns.tmp, ct.off, s));
     c = Carve{static_cast<char*>(t->node_block), 0};
     ct = Carve{static_cast<char*>(ns.tmp), 0};
     take(c);
@@ -657,7 +657,7 @@ int build_tree(dipole_tree* t, const float* points, const float* normals, const 
     Carve ct;
     take_tmp(ct);
     void* tmp = nullptr;
-    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&tmp, ct.off, s));
     ct = Carve{static_cast<char*>(tmp), 0};
     take_tmp(ct);
 
@@ -723,7 +723,7 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
     Carve ct;
     take_tmp(ct);
     void* tmp = nullptr;
-    DIP_CUDA_TRY(cudaMallocAsync(&tmp, ct.off, s));
+    DIP_CUDA_TRY(dev_alloc((void**)&tmp, ct.off, s));
     ct = Carve{static_cast<char*>(tmp), 0};
     take_tmp(ct);
     rc = alloc_topology(t, nn, s);

@@ -36,7 +36,9 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_kernel_launches", "dipole_forward_noalloc", "dipole_probe_l2",
             "dipole_tree_import", "dipole_forward_planned", "dipole_adjoint_planned",
             "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom",
-            "dipole_forward_grid"]
+            "dipole_forward_grid", "dipole_adjoint_acc_size", "dipole_adjoint_stage1",
+            "dipole_adjoint_stage2", "dipole_adjoint_queries", "dipole_query_packet_counts",
+            "dipole_device_allocations"]
 
 
 class DipoleError(RuntimeError):
@@ -100,6 +102,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_tree_export": [P] * 15,
             "dipole_probe_l2": [P, I64, I32, P, P],
             "dipole_tree_import": [P, P, P, P, I64, P, P, P, P, P, P, P, I64, P, P, P],
+            "dipole_adjoint_acc_size": [P, P],
+            "dipole_adjoint_stage1": [P, P, I64, F, P, P, I32, P, P, P],
+            "dipole_adjoint_stage2": [P, P, P, I32, P],
+            "dipole_adjoint_queries": [P, P, I64, F, P, P, I32, P],
+            "dipole_query_packet_counts": [P, P, I64, F, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -111,6 +118,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.dipole_last_error.restype = ctypes.c_char_p
         lib.dipole_kernel_launches.argtypes = []
         lib.dipole_kernel_launches.restype = ctypes.c_uint64
+        lib.dipole_device_allocations.argtypes = []
+        lib.dipole_device_allocations.restype = ctypes.c_uint64
         _lib = lib
         return lib
 
@@ -122,6 +131,11 @@ def dipole_last_error() -> str:
 def dipole_kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load_library().dipole_kernel_launches())
+
+
+def dipole_device_allocations() -> int:
+    """Device allocations made by the library so far in this process."""
+    return int(load_library().dipole_device_allocations())
 
 
 def _check(rc: int):
@@ -202,6 +216,42 @@ def dipole_adjoint(tree: int, queries: torch.Tensor, beta: float, grad_out: torc
                                          q, float(beta), _dev(grad_out, "grad_out"),
                                          _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)),
                                          _stream(stream)))
+
+
+def dipole_adjoint_acc_size(tree: int) -> int:
+    """Entries of a stage-1 accumulator for the tree's current channel count."""
+    n = ctypes.c_int64(0)
+    _check(load_library().dipole_adjoint_acc_size(ctypes.c_void_p(tree), ctypes.byref(n)))
+    return int(n.value)
+
+
+def dipole_adjoint_stage1(tree: int, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                          acc: torch.Tensor, accumulate: bool = False, plan=None, stream=None):
+    """Stage 1 of the adjoint (node and opened-leaf sums) into acc [acc_size] float."""
+    q = int(queries.shape[0])
+    pp, pc = _plan_ptrs(plan, q)
+    _check(load_library().dipole_adjoint_stage1(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _dev(grad_out, "grad_out"), _dev(acc, "acc", shape=(dipole_adjoint_acc_size(tree),)),
+        int(bool(accumulate)), pp, pc, _stream(stream)))
+
+
+def dipole_adjoint_stage2(tree: int, acc: torch.Tensor, grad_attrs: torch.Tensor,
+                          accumulate: bool = False, stream=None):
+    """Stage 2 of the adjoint from a (possibly all-reduced) accumulator."""
+    _check(load_library().dipole_adjoint_stage2(
+        ctypes.c_void_p(tree), _dev(acc, "acc", shape=(dipole_adjoint_acc_size(tree),)),
+        _dev(grad_attrs, "grad_attrs"), int(bool(accumulate)), _stream(stream)))
+
+
+def dipole_adjoint_queries(tree: int, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                           grad_queries: torch.Tensor, accumulate: bool = False, stream=None):
+    """grad_queries [q, 3] (+)= sum_c grad_out[:, c] grad_x D^c at the queries."""
+    q = int(queries.shape[0])
+    _check(load_library().dipole_adjoint_queries(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        _dev(grad_out, "grad_out"), _dev(grad_queries, "grad_queries", shape=(q, 3)),
+        int(bool(accumulate)), _stream(stream)))
 
 
 class QueryPlan:
@@ -312,6 +362,18 @@ def dipole_query_counts(tree: int, queries: torch.Tensor, beta: float, counts: t
                                               _dev(counts, "counts", dtype=torch.int32,
                                                    shape=(q, 3)),
                                               _stream(stream)))
+
+
+def dipole_query_packet_counts(tree: int, queries: torch.Tensor, beta: float,
+                               packet_counts: torch.Tensor, counts=None, stream=None):
+    """Per 32-query packet {warp steps, far steps, opened-leaf points, lanes}."""
+    q = int(queries.shape[0])
+    _check(load_library().dipole_query_packet_counts(
+        ctypes.c_void_p(tree), _dev(queries, "queries", shape=(q, 3)), q, float(beta),
+        ctypes.c_void_p(None) if counts is None else _dev(counts, "counts", dtype=torch.int32,
+                                                          shape=(q, 3)),
+        _dev(packet_counts, "packet_counts", dtype=torch.int32, shape=((q + 31) // 32, 4)),
+        _stream(stream)))
 
 
 def dipole_sync_status(tree: int, stream=None):
@@ -517,6 +579,40 @@ class DipoleTree:
         dipole_forward_grid(self.handle, lo, spacing, (nx, ny, nz), beta, out, stream)
         return out
 
+    def adjoint_queries(self, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                        stream=None) -> torch.Tensor:
+        """dL/dx [q, 3] = sum_c grad_out[:, c] grad_x D^c (the library does the sum)."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        gq = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.float32)
+        dipole_adjoint_queries(self.handle, queries, beta, grad_out.to(torch.float32).contiguous(),
+                               gq, False, stream)
+        return gq
+
+    def adjoint_acc_size(self) -> int:
+        return dipole_adjoint_acc_size(self.handle)
+
+    def adjoint_stage1(self, queries: torch.Tensor, beta: float, grad_out: torch.Tensor,
+                       acc: torch.Tensor | None = None, accumulate: bool = False,
+                       plan: QueryPlan | None = None, stream=None) -> torch.Tensor:
+        """Stage 1 of the adjoint into an accumulator (summable across ranks)."""
+        if self.C == 0:
+            raise DipoleError(DIPOLE_ESTATE, "refit first")
+        if acc is None:
+            acc = torch.empty(self.adjoint_acc_size(), device=queries.device, dtype=torch.float32)
+            accumulate = False
+        dipole_adjoint_stage1(self.handle, queries, beta, grad_out.to(torch.float32).contiguous(),
+                              acc, accumulate, plan, stream)
+        return acc
+
+    def adjoint_stage2(self, acc: torch.Tensor, grad_attrs: torch.Tensor | None = None,
+                       accumulate: bool = False, stream=None) -> torch.Tensor:
+        if grad_attrs is None:
+            grad_attrs = torch.empty((self.n, self.C), device=acc.device, dtype=torch.float32)
+            accumulate = False
+        dipole_adjoint_stage2(self.handle, acc, grad_attrs, accumulate, stream)
+        return grad_attrs
+
     def query_counts(self, queries: torch.Tensor, beta: float, stream=None) -> torch.Tensor:
         counts = torch.empty((queries.shape[0], 3), device=queries.device, dtype=torch.int32)
         dipole_query_counts(self.handle, queries, beta, counts, stream)
@@ -561,10 +657,9 @@ class DipoleSum(torch.autograd.Function):
             g = tree.adjoint(queries, ctx.beta, go, plan=ctx.plan)
             g = g.to(ctx.attr_dtype).reshape(ctx.attr_shape)
         if ctx.needs_input_grad[2]:
-            # dL/dx_j = sum_c dL/dD^c grad_x D^c(x_j); the tree still holds the
-            # forward's moments (refit in forward, not since)
-            _, gx = tree.forward_grad(queries.detach(), ctx.beta, value=False)
-            gq = torch.einsum("qc,qck->qk", go, gx).to(queries.dtype)
+            # dL/dx_j = sum_c dL/dD^c grad_x D^c(x_j), summed in the library; the
+            # tree still holds the forward's moments (refit in forward, not since)
+            gq = tree.adjoint_queries(queries.detach(), ctx.beta, go).to(queries.dtype)
         return g, None, gq, None
 
 
@@ -653,8 +748,7 @@ class DipoleField(torch.autograd.Function):
         if need[5]:
             if ctx.with_grad and grad_gx is not None and bool(torch.any(grad_gx != 0)):
                 raise NotImplementedError("second derivatives in the query position")
-            _, gx = tree.forward_grad(q, ctx.beta, value=False)
-            gq = torch.einsum("qc,qck->qk", grad_out.to(torch.float32), gx)
+            gq = tree.adjoint_queries(q, ctx.beta, grad_out)
         return None, gn, None, ge, gm, gq, None, None, None
 
 

@@ -42,12 +42,3 @@ def bf16_round(a):
     u = a.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).reshape(a.shape)
-
-
-def rel_l2(y, ref):
-    """Per channel: ||y - ref||_2 / ||ref||_2 (the relative error of the vector)."""
-    y = np.asarray(y, np.float64)
-    ref = np.asarray(ref, np.float64)
-    if y.ndim == 1:
-        y, ref = y[:, None], ref[:, None]
-    return np.linalg.norm(y - ref, axis=0) / np.maximum(np.linalg.norm(ref, axis=0), 1e-300)

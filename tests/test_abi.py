@@ -59,6 +59,12 @@ def test_argument_errors_without_gpu(lib_path):
     assert lib.dipole_adjoint(None, None, 0, 2.0, None, None, 0, None) == -1
     assert lib.dipole_forward_grad(None, None, 0, 2.0, None, None, None, None, None) == -1
     assert lib.dipole_adjoint_grad(None, None, 0, 2.0, None, None, None, 0, None, None, None) == -1
+    assert lib.dipole_adjoint_stage1(None, None, 0, 2.0, None, None, 0, None, None, None) == -1
+    assert lib.dipole_adjoint_stage2(None, None, None, 0, None) == -1
+    assert lib.dipole_adjoint_acc_size(None, None) == -1
+    assert lib.dipole_adjoint_queries(None, None, 0, 2.0, None, None, 0, None) == -1
+    assert lib.dipole_query_packet_counts(None, None, 0, 2.0, None, None, None) == -1
+    assert isinstance(dipole.dipole_device_allocations(), int)
     lib.dipole_tree_destroy(None)  # a no-op
     fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
     bad_kernel = dipole._BuildParams(8, 10, 2)

@@ -8,9 +8,11 @@ keeps the forward pass's scratch (query sort buffers and the work counter) in a
 static device array.  This test calls that entry point through the C ABI,
 twice in a row on different query sets (the second call finds the first call's
 leftovers in the shared array), and checks each result against dipole_forward
-with the forward tolerance used everywhere else (1e-4, max norm per channel).
-It lives in a file that pytest collects last and passes both alone and after
-the other tests.
+and against the CPU oracle with the forward tolerance used everywhere else
+(1e-4, max norm per channel); it also checks, through the library's
+allocation counter, that those calls allocated nothing, and that q = 0 is a
+no-op.  It lives in a file that pytest collects last and passes both alone and
+after the other tests.
 """
 import ctypes
 
@@ -31,8 +33,17 @@ def _normwise(y, ref):
     return np.max(np.abs(y - ref), axis=0) / den
 
 
-def test_forward_noalloc_matches_forward_twice():
+def _call(lib, tree, q, n, out, stream):
+    return lib.dipole_forward_noalloc(ctypes.c_void_p(tree.handle),
+                                      ctypes.c_void_p(q.data_ptr() if q is not None else None),
+                                      n, ctypes.c_float(2.0),
+                                      ctypes.c_void_p(out.data_ptr() if out is not None else None),
+                                      stream)
+
+
+def test_forward_noalloc_matches_forward_and_oracle_twice():
     import torch
+    import oracle
     from paper_2405_16788_gb300 import dipole
 
     lib = dipole.load_library()
@@ -43,20 +54,30 @@ def test_forward_noalloc_matches_forward_twice():
     tree = dipole.DipoleTree(t(c.points), t(c.normals), t(c.areas), t(c.eps))
     tree.refit(t(w.mu))
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ot = oracle.Tree(c.points, c.normals, c.areas, c.eps)
+    ot.update(w.mu)
 
     # two calls in a row with different sizes; the second one reuses the array
     for qs in (w.queries[:50000], w.queries[60000:60000 + 3001]):
         q = t(qs)
         ref = tree.forward(q, 2.0).cpu().numpy()
         out = torch.full((len(qs), tree.C), float("nan"), device=dev)
-        rc = lib.dipole_forward_noalloc(ctypes.c_void_p(tree.handle),
-                                        ctypes.c_void_p(q.data_ptr()), len(qs),
-                                        ctypes.c_float(2.0), ctypes.c_void_p(out.data_ptr()),
-                                        stream)
+        torch.cuda.synchronize()
+        allocs0 = dipole.dipole_device_allocations()
+        rc = _call(lib, tree, q, len(qs), out, stream)
         assert rc == dipole.DIPOLE_OK, dipole.dipole_last_error()
+        assert dipole.dipole_device_allocations() == allocs0  # nothing allocated
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.all(_normwise(got, ref) <= TOL), _normwise(got, ref)
+        # against the oracle's FP64 Barnes-Hut on a sample of the queries
+        idx = np.random.default_rng(len(qs)).choice(len(qs), 2000, replace=False)
+        oref = ot.forward(qs[idx], 2.0)
+        assert np.all(_normwise(got[idx], oref) <= TOL), _normwise(got[idx], oref)
+    # q = 0 is a no-op that touches nothing
+    allocs0 = dipole.dipole_device_allocations()
+    assert _call(lib, tree, None, 0, None, stream) == dipole.DIPOLE_OK
+    assert dipole.dipole_device_allocations() == allocs0
     tree.sync_status()
 
 
