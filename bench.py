@@ -52,7 +52,10 @@ def parse_args():
     p.add_argument("--no-bf16", action="store_true")
     p.add_argument("--no-next", action="store_true",
                    help="skip the timings of the gradient, grid and training-loop rows")
-    p.add_argument("--loop-steps", type=int, default=10)
+    p.add_argument("--loop-steps", type=int, default=200,
+                   help="Adam steps of the 5M-point training-loop row")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the rows of the other workloads (sphere-2k, scene-200k, scene-3m-bf16)")
     return p.parse_args()
 
 
@@ -91,7 +94,9 @@ def config_of(w, flush: str):
             "channels": int(w.mu.shape[1]), "attr_dtype": "f32", "beta": BETA,
             "leaf_size": LEAF, "tree": "built every step",
             "api": "dipole_build_tree, dipole_refit, dipole_forward_planned, dipole_adjoint_planned",
-            "l2": flush, "step": "build + refit + forward + adjoint (stage 1 + 2)"}
+            "l2": flush, "step": "build + refit + forward + adjoint (stage 1 + 2)",
+            "cpu_baseline": "the oracle (FP64 CPU Barnes-Hut) timed on a sample of the queries "
+                            "and extrapolated to the full step (sampled and extrapolated)"}
 
 
 # ------------------------------------------------------------------ oracle
@@ -234,7 +239,7 @@ class ClockSampler:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ["traverse.cu", "query.cuh", "kernels.cuh", "common.cuh"]:
+    for f in ["traverse.cu", "traverse_grad.cu", "query.cuh", "kernels.cuh", "common.cuh", "tree.cuh"]:
         with open(os.path.join(ROOT, "paper_2405_16788_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -273,6 +278,92 @@ def l2_probe(torch, dev, dp):
         e1.synchronize()
         best = max(best, passes * buf.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
     return best
+
+
+def l2_size_bytes(torch, dev) -> int:
+    """The GPU's L2 size (cudaDevAttrL2CacheSize, as torch reports it)."""
+    return int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
+
+
+def roofline_block(torch, dev, dp, C, Q, N, NN, sums, usums, kernel_ms, clocks, rank):
+    """The roofline of the dominant traversal kernel (the slower of the
+    forward and the adjoint stage 1, each timed by CUDA events around its
+    launches in the timed region).
+
+    The bound follows the workload: L2 when the working set (node records and
+    moments, point records and attributes) fits in the L2, else HBM; the
+    L2 peak is measured here (dipole_probe_l2, best of 10), the HBM peak is
+    MEASURED_PEAKS.json's copy bandwidth.  Three figures side by side:
+      per_lane  the algorithmic bytes of every query's own walk (tested node
+                16 B, far node 4 + 12C B, leaf point 28 + 4C B, query 12 + 4C B),
+                what a query must touch; the lanes of a warp share most of it
+                as broadcasts, so this can exceed the memory peaks;
+      per_warp  what the warps must fetch: a 32-byte node record per warp
+                step, a 12C-byte moment row when some lane takes the node as
+                far, 32 + 4C bytes per point of a leaf some lane opens, and the
+                queries' own 12 + 4C bytes (dipole_query_packet_counts);
+      issue     warp instructions per launch (ncu smsp__inst_executed.sum
+                from profiles/traffic.json, taken on the current kernel
+                source) over (SMs x 4 schedulers x SM clock x kernel time),
+                the SM clock being the median sampled in the timed region.
+    `frac` is the per-lane figure against the bound's peak; `binding` names
+    the largest of the per-warp and issue fractions."""
+    Tn, An, Ln = sums
+    Us, Uf, Up, _ = usums
+    per_lane = 16 * Tn + (4 + 12 * C) * An + (28 + 4 * C) * Ln + (12 + 4 * C) * Q
+    per_warp = 32 * Us + 12 * C * Uf + (32 + 4 * C) * Up + (12 + 4 * C) * Q
+    dom = "adjoint" if kernel_ms["adjoint"] >= kernel_ms["forward"] else "forward"
+    t_k = kernel_ms[dom]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback (profiling recipe, 6.8 TB/s)"
+    hbm = hbm or 6800.0
+    l2_bytes = l2_size_bytes(torch, dev)
+    ws = N * (32 + 4 * C) + NN * (32 + 4 * srow(C))
+    l2_probe_gbs = l2_probe(torch, dev, dp) if rank == 0 else None
+    if l2_bytes and ws <= l2_bytes and l2_probe_gbs:
+        bound, peak, peak_src = "l2", l2_probe_gbs, "measured in this run (dipole_probe_l2, 48 MB x 20, best of 10)"
+    else:
+        bound, peak, peak_src = "hbm", hbm, hbm_src
+    kern = f"k_query<{dp_cp(C)},float,{dom}>"
+    tr = measured_traffic(kern)
+    gbs = lambda b: b / (t_k * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue = None
+    if tr and tr.get("inst_executed") and clocks and clocks.get("sm_mhz"):
+        cap = sms * 4 * clocks["sm_mhz"] * 1e6 * t_k * 1e-3
+        issue = {"warp_inst_per_launch": tr["inst_executed"], "sm_mhz": clocks["sm_mhz"],
+                 "schedulers": sms * 4, "frac": tr["inst_executed"] / cap,
+                 "inst_per_warp_step": tr["inst_executed"] / max(Us, 1),
+                 "source": "profiles/traffic.json (ncu, same kernel source)"}
+    figures = {
+        "per_lane": {"bytes": per_lane, "achieved_gbs": gbs(per_lane), "frac": gbs(per_lane) / peak,
+                     "formula": "16*tested + (4+12C)*far + (28+4C)*leaf_points + (12+4C)*queries"},
+        "per_warp": {"bytes": per_warp, "achieved_gbs": gbs(per_warp), "frac": gbs(per_warp) / peak,
+                     "formula": "32*warp_steps + 12C*far_steps + (32+4C)*opened_leaf_points + (12+4C)*queries"},
+        "issue": issue,
+    }
+    cands = [("per_warp", figures["per_warp"]["frac"])] + ([("issue", issue["frac"])] if issue else [])
+    binding = max(cands, key=lambda kv: kv[1])[0]
+    return {"bound": bound, "achieved": gbs(per_lane), "peak": peak, "unit": "GB/s",
+            "frac": gbs(per_lane) / peak, "peak_source": peak_src,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "kernel": kern + " (its traversal launches only: CUDA events in the timed region)",
+            "launch_ms": t_k, "figures": figures, "binding": binding,
+            "algorithmic_bytes_per_launch": per_lane,
+            "per_query": {"tested": Tn / Q, "far": An / Q, "leaf_points": Ln / Q},
+            "per_packet": {"warp_steps": Us / ((Q + 31) // 32), "far_steps": Uf / ((Q + 31) // 32),
+                           "opened_leaf_points": Up / ((Q + 31) // 32)},
+            "working_set_mb": ws / 2 ** 20, "l2_mb": l2_bytes / 2 ** 20, "hbm_peak_gbs": hbm,
+            "l2_probe_gbs": l2_probe_gbs,
+            "ncu": ({k: tr.get(k) for k in ("lts_pct", "dram_pct", "issue_active_pct",
+                                               "warps_active_pct", "long_scoreboard_per_issue")}
+                    if tr else None)}
 
 
 def run_ours(args):
@@ -324,6 +415,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(gpu_uuid) if rank == 0 else None
     launches0 = dp.dipole_kernel_launches()
+    dp.dipole_traversal_elapsed("forward")  # drop anything recorded before
+    dp.dipole_traversal_elapsed("adjoint")
+    dp.dipole_traversal_timer(True)  # CUDA events around each traversal kernel
     total_ms = 0.0
     for _ in range(args.steps):
         flush.fill_(1)  # evict L2 between timed steps (not timed)
@@ -335,7 +429,11 @@ def run_ours(args):
         total_ms += e0.elapsed_time(e1)
         dp.dipole_tree_destroy(h)
     launches = (dp.dipole_kernel_launches() - launches0) // args.steps
+    dp.dipole_traversal_timer(False)
     torch.cuda.synchronize()
+    kf_ms, kf_n = dp.dipole_traversal_elapsed("forward")
+    ka_ms, ka_n = dp.dipole_traversal_elapsed("adjoint")
+    kernel_ms = {"forward": kf_ms / max(kf_n, 1), "adjoint": ka_ms / max(ka_n, 1)}
     barrier()
     clocks = sampler.stop() if sampler else None
     max_ms = max_over_ranks(total_ms, td, dev)
@@ -364,43 +462,22 @@ def run_ours(args):
 
     ph = phase_times()
     h = step()
+    npk = (Q + 31) // 32
     cnt = torch.empty((Q, 3), dtype=torch.int32, device=dev)
-    dp.dipole_query_counts(h, X, BETA, cnt)
+    pcnt = torch.empty((npk, 4), dtype=torch.int32, device=dev)
+    dp.dipole_query_packet_counts(h, X, BETA, pcnt, counts=cnt)
     sums = cnt.to(torch.int64).sum(0).tolist()
+    usums = pcnt.to(torch.int64).sum(0).tolist()
     info = dp.dipole_tree_info_get(h)
     dp.dipole_tree_destroy(h)
-    Tn, An, Ln = sums
-    alg_bytes = 16 * Tn + (4 + 12 * C) * An + (16 + 12 + 4 * C) * Ln + (12 + 4 * C) * Q
-    dom = "adjoint" if ph[3] >= ph[2] else "forward"
-    t_dom = ph[3] if dom == "adjoint" else ph[2]
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm_peak else "fallback"
-    hbm_peak = hbm_peak or 6800.0
-    achieved = alg_bytes / (t_dom * 1e-3) / 1e9
-    kern = f"k_query<{dp_cp(C)},float,{dom}>"
-    tr = measured_traffic(kern)
-    l2 = l2_probe(torch, dev, dp) if rank == 0 else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": kern + f" (the dipole_{dom} call, incl. its query sort)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "bytes_formula": "16*tested + (4+12C)*far + (28+4C)*leaf_points + (12+4C)*queries",
-                "per_query": {"tested": Tn / Q, "far": An / Q, "leaf_points": Ln / Q},
-                "launch_ms": t_dom,
-                "l2_probe_gbs": l2, "frac_of_l2_probe": (achieved / l2) if l2 else None,
-                "working_set_mb": (N * (32 + 4 * C) + info["n_nodes"] * (32 + 4 * srow(C))) / 2 ** 20}
+    roofline = roofline_block(torch, dev, dp, C, Q, N, info["n_nodes"], sums, usums, kernel_ms,
+                              clocks, rank)
     breakdown = {"build_ms": ph[0], "refit_ms": ph[1], "forward_ms": ph[2], "adjoint_ms": ph[3],
                  "forward_queries_per_s": Q / (ph[2] * 1e-3),
                  "adjoint_queries_per_s": Q / (ph[3] * 1e-3),
                  "refit_forward_adjoint_queries_per_s": Q / ((ph[1] + ph[2] + ph[3]) * 1e-3),
-                 "interactions_per_s": world * (An + Ln) * 2 / (ms_per_step * 1e-3),
+                 "interactions_per_s": world * (sums[1] + sums[2]) * 2 / (ms_per_step * 1e-3),
+                 "forward_kernel_ms": kernel_ms["forward"], "adjoint_kernel_ms": kernel_ms["adjoint"],
                  "nodes": info["n_nodes"]}
 
     # ---- bf16 attribute storage, same workload ----
@@ -421,7 +498,7 @@ def run_ours(args):
     nxt = None
     if rank == 0 and not args.no_next:
         nxt = next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args,
-                        (Tn, An, Ln), hbm_peak)
+                        sums, roofline["peak"])
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -481,6 +558,13 @@ def run_ours(args):
         cpu, ref = oracle_sample(w, args.cpu_seconds, keep=True)
         accuracy = sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref)
 
+    # ---- the other workloads, each with its error against the oracle ----
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        del flush
+        torch.cuda.empty_cache()
+        configs = config_rows(torch, dp, dev, stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -489,11 +573,162 @@ def run_ours(args):
                 "config": config_of(w, "flushed between timed steps (512 MB write)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "breakdown": breakdown,
-                "bf16_attrs": bf16, "next_rows": nxt, "accuracy": accuracy, "impl": "ours"}
+                "bf16_attrs": bf16, "next_rows": nxt, "accuracy": accuracy,
+                "configs": configs, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:
         td.destroy_process_group()
     return 0
+
+
+def _normwise(y, r):
+    y, r = np.asarray(y, np.float64), np.asarray(r, np.float64)
+    den = np.max(np.abs(r), axis=0)
+    return np.max(np.abs(y - r), axis=0) / np.where(den > 0, den, 1.0)
+
+
+def _rel2(y, r):
+    y, r = np.asarray(y, np.float64), np.asarray(r, np.float64)
+    return np.linalg.norm(y - r, axis=0) / np.maximum(np.linalg.norm(r, axis=0), 1e-300)
+
+
+def _bf16_round(a):
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32).reshape(a.shape)
+
+
+def config_rows(torch, dp, dev, stream):
+    """The workloads besides the headline one (sphere-2k and scene-200k
+    forward only, scene-3m-bf16 forward + adjoint in bf16 and in float32),
+    each timed with CUDA events (median of 5, a 512 MB L2 flush before each)
+    and checked against the oracle's FP64 Barnes-Hut on a query sample (all
+    queries for sphere-2k, where the plain O(NQ) sum is also given)."""
+    import oracle
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    def kernel_ms(mode):
+        ms, n = dp.dipole_traversal_elapsed(mode)
+        return ms / max(n, 1)
+
+    rows = {}
+    for name, n_err in (("sphere-2k", None), ("scene-200k", 4096)):
+        w = syn.workload(name)
+        c = w.cloud
+        Q, C = len(w.queries), w.mu.shape[1]
+        P_, N_, A_, E_ = T(c.points), T(c.normals), T(c.areas), T(c.eps)
+        X_, MU_ = T(w.queries), T(w.mu)
+        out = torch.empty((Q, C), device=dev)
+        b_ms = timed(lambda: dp.dipole_tree_destroy(dp.dipole_build_tree(P_, N_, A_, E_, LEAF, 10)))
+        h = dp.dipole_build_tree(P_, N_, A_, E_, LEAF, 10)
+        dp.dipole_refit(h, MU_)
+        dp.dipole_traversal_elapsed("forward")
+        dp.dipole_traversal_timer(True)
+        f_ms = timed(lambda: dp.dipole_forward(h, X_, BETA, out))
+        dp.dipole_traversal_timer(False)
+        fk_ms = kernel_ms("forward")
+        y = out.cpu().numpy()
+        dp.dipole_sync_status(h)
+        dp.dipole_tree_destroy(h)
+        ot = oracle.Tree(c.points, c.normals, c.areas, c.eps, leaf_size=LEAF)
+        ot.update(w.mu)
+        idx = np.arange(Q) if n_err is None else np.random.default_rng(7).choice(Q, n_err, replace=False)
+        t0 = time.perf_counter()
+        ref = ot.forward(w.queries[idx], BETA)
+        cpu_qps = len(idx) / (time.perf_counter() - t0)
+        row = {"points": c.n, "queries": Q, "channels": C, "build_ms": b_ms, "forward_ms": f_ms,
+               "forward_kernel_ms": fk_ms, "forward_queries_per_s": Q / (f_ms * 1e-3),
+               "error_vs_oracle_bh_normwise": _normwise(y[idx], ref).tolist(),
+               "error_queries": int(len(idx)),
+               "cpu_oracle_forward_queries_per_s": cpu_qps, "cpu_cores": oracle.num_threads(),
+               "cpu_sample": f"oracle FP64 Barnes-Hut forward on {len(idx)} queries (wall clock)"}
+        if n_err is None:
+            bf = oracle.brute_forward(c.points, c.normals, c.areas, c.eps, w.mu, w.queries)
+            row["bh_vs_brute_force_normwise"] = _normwise(ref, bf).tolist()
+            row["gpu_vs_brute_force_normwise"] = _normwise(y, bf).tolist()
+        rows[name] = row
+        del P_, N_, A_, E_, X_, MU_, out
+
+    # scene-3m-bf16: float32 and bf16 attribute storage on the same GPU
+    w = syn.workload("scene-3m-bf16")
+    c = w.cloud
+    Q, C = len(w.queries), w.mu.shape[1]
+    P_, N_, A_, E_ = T(c.points), T(c.normals), T(c.areas), T(c.eps)
+    X_ = T(w.queries)
+    G_ = T(syn.upstream_grad(Q, C, seed=404))
+    out = torch.empty((Q, C), device=dev)
+    grad = torch.empty((c.n, C), device=dev)
+    plan = dp.QueryPlan(Q, dev)
+    b_ms = timed(lambda: dp.dipole_tree_destroy(dp.dipole_build_tree(P_, N_, A_, E_, LEAF, 10)), reps=3)
+    h = dp.dipole_build_tree(P_, N_, A_, E_, LEAF, 10)
+    res = {"points": c.n, "queries": Q, "channels": C, "build_ms": b_ms}
+    idx = np.random.default_rng(4).choice(Q, 10000, replace=False)
+    outs = {}
+    for dt, mu in (("f32", T(w.mu)), ("bf16", T(w.mu).to(torch.bfloat16))):
+        r_ms = timed(lambda: dp.dipole_refit(h, mu), reps=3)
+        dp.dipole_traversal_elapsed("forward")
+        dp.dipole_traversal_elapsed("adjoint")
+        dp.dipole_traversal_timer(True)
+        f_ms = timed(lambda: dp.dipole_forward_planned(h, X_, BETA, out, plan), reps=3)
+        a_ms = timed(lambda: dp.dipole_adjoint_planned(h, X_, BETA, G_, grad, plan, False), reps=3)
+        dp.dipole_traversal_timer(False)
+        res[dt] = {"refit_ms": r_ms, "forward_ms": f_ms, "adjoint_ms": a_ms,
+                   "forward_kernel_ms": kernel_ms("forward"), "adjoint_kernel_ms": kernel_ms("adjoint"),
+                   "refit_forward_adjoint_ms": r_ms + f_ms + a_ms,
+                   "queries_per_s": Q / ((r_ms + f_ms + a_ms) * 1e-3)}
+        dp.dipole_refit(h, mu)
+        dp.dipole_forward(h, X_, BETA, out)
+        outs[dt] = out[torch.from_numpy(idx).to(dev)].cpu().numpy()
+        # the adjoint with the upstream gradient on the sample only
+        gs = torch.zeros((Q, C), device=dev)
+        gs[torch.from_numpy(idx).to(dev)] = G_[torch.from_numpy(idx).to(dev)]
+        dp.dipole_adjoint(h, X_, BETA, gs, grad, False)
+        outs[dt + "_adj"] = grad.cpu().numpy()
+        del mu
+    dp.dipole_sync_status(h)
+    dp.dipole_tree_destroy(h)
+    res["speedup_bf16_vs_f32"] = {
+        "refit_forward_adjoint": res["f32"]["refit_forward_adjoint_ms"] / res["bf16"]["refit_forward_adjoint_ms"],
+        "step_with_build": (b_ms + res["f32"]["refit_forward_adjoint_ms"]) /
+                           (b_ms + res["bf16"]["refit_forward_adjoint_ms"]),
+        "forward_kernel": res["f32"]["forward_kernel_ms"] / res["bf16"]["forward_kernel_ms"],
+        "adjoint_kernel": res["f32"]["adjoint_kernel_ms"] / res["bf16"]["adjoint_kernel_ms"]}
+    ot = oracle.Tree(c.points, c.normals, c.areas, c.eps, leaf_size=LEAF)
+    g_s = syn.upstream_grad(Q, C, seed=404)[idx].astype(np.float64)
+    ot.update(w.mu)
+    ref_f = ot.forward(w.queries[idx], BETA)
+    aref_f = ot.adjoint(w.queries[idx], BETA, g_s)
+    ot.update(_bf16_round(w.mu))
+    ref_b = ot.forward(w.queries[idx], BETA)
+    aref_b = ot.adjoint(w.queries[idx], BETA, g_s)
+    res["accuracy"] = {
+        "queries": 10000,
+        "f32_forward_normwise": _normwise(outs["f32"], ref_f).tolist(),
+        "f32_adjoint_normwise": _normwise(outs["f32_adj"], aref_f).tolist(),
+        "bf16_forward_normwise_vs_f32_attrs": _normwise(outs["bf16"], ref_f).tolist(),
+        "bf16_forward_rel_l2_vs_f32_attrs": _rel2(outs["bf16"], ref_f).tolist(),
+        "bf16_forward_normwise_vs_bf16_attrs": _normwise(outs["bf16"], ref_b).tolist(),
+        "bf16_adjoint_normwise_vs_bf16_attrs": _normwise(outs["bf16_adj"], aref_b).tolist(),
+        "input_rounding_alone_normwise": _normwise(ref_b, ref_f).tolist(),
+        "input_rounding_alone_rel_l2": _rel2(ref_b, ref_f).tolist(),
+        "gate": "3e-3 max-norm per channel vs the float32 attributes (met where the input "
+                "rounding alone is below it); 1e-4 vs the oracle on the bf16-rounded inputs"}
+    rows["scene-3m-bf16"] = res
+    return rows
 
 
 def sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref):
@@ -524,7 +759,7 @@ def sample_errors(torch, dp, dev, P, Nr, A, E, MU, X, Q, C, N, ref):
 
 
 def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, args, counts,
-              hbm_peak):
+              peak):
     """Timings of the rows built beyond the forward/adjoint step, each the
     median of 5 launches after one warm-up, L2 flushed before each."""
     def timed(fn, reps=5):
@@ -565,9 +800,9 @@ def next_rows(torch, dp, dev, stream, flush, P, Nr, A, E, MU, X, G, Q, C, N, arg
         "queries_per_s_fwd_adj": Q / ((f_ms + a_ms) * 1e-3),
         "adjoint_geom_ms": geo_ms,
         "forward_grad_logical_gbs": b_fg / (f_ms * 1e-3) / 1e9,
-        "forward_grad_frac_of_hbm": b_fg / (f_ms * 1e-3) / 1e9 / hbm_peak,
+        "forward_grad_frac_of_peak": b_fg / (f_ms * 1e-3) / 1e9 / peak,
         "adjoint_geom_logical_gbs": b_geo / (geo_ms * 1e-3) / 1e9,
-        "adjoint_geom_frac_of_hbm": b_geo / (geo_ms * 1e-3) / 1e9 / hbm_peak,
+        "adjoint_geom_frac_of_peak": b_geo / (geo_ms * 1e-3) / 1e9 / peak,
         "bytes_formulas": {"forward_grad": "16*tested + (4+12C)*far + (28+4C)*leaf + (12+16C)*queries",
                            "adjoint_geom": "16*tested + (4+12C)*far + (32+4C)*leaf + (12+16C)*queries"},
         "workload": "the bench workload's tree and queries, C=4, plan from forward_grad"}}

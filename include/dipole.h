@@ -474,6 +474,30 @@ uint64_t dipole_kernel_launches(void);
  * counterpart. */
 uint64_t dipole_device_allocations(void);
 
+/* Query modes of the traversal timer below. */
+typedef enum {
+    DIPOLE_TIMER_FORWARD = 0,       /* dipole_forward*, dipole_forward_grid */
+    DIPOLE_TIMER_ADJOINT = 1,       /* dipole_adjoint*, dipole_adjoint_stage1 (stage 1) */
+    DIPOLE_TIMER_COUNTS = 2,        /* dipole_query_counts, dipole_query_packet_counts */
+    DIPOLE_TIMER_FORWARD_GRAD = 3,  /* dipole_forward_grad */
+    DIPOLE_TIMER_ADJOINT_GRAD = 4,  /* dipole_adjoint_grad (stage 1) */
+    DIPOLE_TIMER_ADJOINT_GEOM = 5,  /* dipole_adjoint_geom (stage 1) */
+    DIPOLE_TIMER_QUERY_GRAD = 6     /* dipole_adjoint_queries */
+} dipole_timer_mode;
+/*
+ * Timing of the traversal kernels, for the roofline of the dominant kernel
+ * (diagnostics; the paper has no counterpart).  dipole_traversal_timer(1)
+ * makes every later query call record a CUDA event pair on its stream
+ * directly before and after its traversal kernel (query sort, work-item
+ * setup and stage 2 are outside the pair); dipole_traversal_timer(0) stops
+ * it.  dipole_traversal_elapsed(mode, &ms, &launches) waits for the recorded
+ * events of that mode, returns their summed elapsed time and count, and
+ * forgets them.  mode: a dipole_timer_mode.  Costs two event records per call
+ * while enabled; off by default.
+ */
+int dipole_traversal_timer(int32_t enable);
+int dipole_traversal_elapsed(int32_t mode, float* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,19 @@ uint64_t dipole_kernel_launches(void) { return g_launches.load(std::memory_order
 
 uint64_t dipole_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
+int dipole_traversal_timer(int32_t enable) {
+    if (enable != 0 && enable != 1)
+        return dip_fail(DIPOLE_EINVAL, "dipole_traversal_timer: enable must be 0 or 1");
+    dip::timer_enable(enable != 0);
+    return DIPOLE_OK;
+}
+
+int dipole_traversal_elapsed(int32_t mode, float* total_ms, int64_t* launches) {
+    if (!total_ms || !launches)
+        return dip_fail(DIPOLE_EINVAL, "dipole_traversal_elapsed: total_ms and launches are required");
+    return dip::timer_elapsed(mode, total_ms, launches);
+}
+
 int dipole_build_tree(const float* points, const float* normals, const float* areas,
                       const float* radii, int64_t n, const dipole_build_params* params,
                       void* stream, dipole_tree** out) {

@@ -16,6 +16,8 @@
 // same step, so their contributions to dS_t are summed inside the warp before
 // one set of atomics; the same holds for the points of an opened leaf.
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "query.cuh"
 
@@ -606,7 +608,63 @@ int noalloc_scratch(void** out) {
     return 0;
 }
 
+// ------------------------------------------------------------ traversal timer
+constexpr int kTimerModes = 8;
+struct TimerState {
+    std::mutex m;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kTimerModes];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
+};
+TimerState g_timer;
+
+// Event pair for one launch of `mode`, or {nullptr, nullptr} when the timer is off.
+std::pair<cudaEvent_t, cudaEvent_t> timer_pair(int mode) {
+    std::lock_guard<std::mutex> lock(g_timer.m);
+    if (!g_timer.on || mode < 0 || mode >= kTimerModes) return {nullptr, nullptr};
+    std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+    if (!g_timer.spare.empty()) {
+        p = g_timer.spare.back();
+        g_timer.spare.pop_back();
+    } else if (cudaEventCreate(&p.first) != cudaSuccess || cudaEventCreate(&p.second) != cudaSuccess) {
+        return {nullptr, nullptr};
+    }
+    g_timer.pending[mode].push_back(p);
+    return p;
+}
+
 }  // namespace
+
+void timer_enable(bool on) {
+    std::lock_guard<std::mutex> lock(g_timer.m);
+    g_timer.on = on;
+}
+
+int timer_elapsed(int mode, float* total_ms, int64_t* launches) {
+    if (mode < 0 || mode >= kTimerModes) return dip_fail(-1, "dipole_traversal_elapsed: bad mode");
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ps;
+    {
+        std::lock_guard<std::mutex> lock(g_timer.m);
+        ps.swap(g_timer.pending[mode]);
+    }
+    float sum = 0.f;
+    cudaError_t err = cudaSuccess;
+    for (auto& p : ps) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.first, p.second);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+        sum += ms;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_timer.m);
+        g_timer.spare.insert(g_timer.spare.end(), ps.begin(), ps.end());
+    }
+    DIP_CUDA_TRY(err);
+    *total_ms = sum;
+    *launches = (int64_t)ps.size();
+    return 0;
+}
 
 int64_t noalloc_max_queries() { return kNoAllocMaxQueries; }
 
@@ -814,10 +872,13 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
             a.grid.nb[2] = (call.grid_dim[2] + 1) / 2;
             a.nq = 32 * a.grid.nb[0] * a.grid.nb[1] * a.grid.nb[2];  // one packet per brick
         }
+        const auto ev = timer_pair(mode);
+        if (ev.first) DIP_CUDA_TRY(cudaEventRecord(ev.first, s));
         if (mode == kForward) rc = dispatch<kForward>(t, a, s);
         else if (mode == kAdjoint) rc = dispatch<kAdjoint>(t, a, s);
         else if (mode == kCount) rc = dispatch<kCount>(t, a, s);
         else rc = dispatch_grad(t, mode, a, s);
+        if (ev.second) DIP_CUDA_TRY(cudaEventRecord(ev.second, s));
     }
     if (rc == 0 && adjoint && call.grad && !call.acc)
         rc = stage2(t, t->dS, t->dmu, call.grad, call.accumulate, s);

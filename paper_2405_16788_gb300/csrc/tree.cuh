@@ -142,6 +142,12 @@ struct QueryCall {
 
 int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s);
 
+// Traversal timer (dipole_traversal_timer / dipole_traversal_elapsed): when
+// enabled, every query call records a CUDA event pair on its stream around
+// its traversal kernel launch, kept per query mode.
+void timer_enable(bool on);
+int timer_elapsed(int mode, float* total_ms, int64_t* launches);
+
 // Forward queries with all scratch in a static device array (no allocation);
 // q <= noalloc_max_queries().
 int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float beta, float* out,

@@ -38,7 +38,7 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom",
             "dipole_forward_grid", "dipole_adjoint_acc_size", "dipole_adjoint_stage1",
             "dipole_adjoint_stage2", "dipole_adjoint_queries", "dipole_query_packet_counts",
-            "dipole_device_allocations"]
+            "dipole_device_allocations", "dipole_traversal_timer", "dipole_traversal_elapsed"]
 
 
 class DipoleError(RuntimeError):
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_adjoint_stage2": [P, P, P, I32, P],
             "dipole_adjoint_queries": [P, P, I64, F, P, P, I32, P],
             "dipole_query_packet_counts": [P, P, I64, F, P, P, P],
+            "dipole_traversal_timer": [I32],
+            "dipole_traversal_elapsed": [I32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -136,6 +138,25 @@ def dipole_kernel_launches() -> int:
 def dipole_device_allocations() -> int:
     """Device allocations made by the library so far in this process."""
     return int(load_library().dipole_device_allocations())
+
+
+TIMER_MODES = {"forward": 0, "adjoint": 1, "counts": 2, "forward_grad": 3, "adjoint_grad": 4,
+               "adjoint_geom": 5, "query_grad": 6}
+
+
+def dipole_traversal_timer(enable: bool):
+    """Record CUDA events around every traversal kernel launch (or stop)."""
+    _check(load_library().dipole_traversal_timer(int(bool(enable))))
+
+
+def dipole_traversal_elapsed(mode: str):
+    """(total ms, launches) of the traversal kernels of `mode` recorded since
+    the last call; waits for them."""
+    ms = ctypes.c_float(0.0)
+    n = ctypes.c_int64(0)
+    _check(load_library().dipole_traversal_elapsed(TIMER_MODES[mode], ctypes.byref(ms),
+                                                   ctypes.byref(n)))
+    return float(ms.value), int(n.value)
 
 
 def _check(rc: int):
