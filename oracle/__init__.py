@@ -63,6 +63,9 @@ def _load():
         lib.orc_morton.argtypes = [_I64, _P, _P, _P]
         lib.orc_brute_forward.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P]
         lib.orc_brute_adjoint.argtypes = [_I64, _P, _P, _P, _P, _I, _I64, _P, _P, _P]
+        lib.orc_brute_forward_app.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _P, _I64, _P, _P]
+        lib.orc_brute_adjoint_app.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _I64, _P, _P, _P]
+        lib.orc_tree_set_geometry_channels.argtypes = [_P, _I]
         lib.orc_tree_build.restype = _P
         lib.orc_tree_build.argtypes = [_I64, _P, _P, _P, _P, _I, _I]
         lib.orc_tree_free.argtypes = [_P]
@@ -152,6 +155,37 @@ def brute_adjoint(points, normals, areas, eps, queries, g):
     out = np.zeros((n, C), np.float64)
     _load().orc_brute_adjoint(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C, nq, _ptr(q), _ptr(g),
                               _ptr(out))
+    return out
+
+
+def brute_forward_app(points, normals, areas, eps, mu, queries, geometry_channels):
+    """Plain O(NQ) sum with channels [geometry_channels, C) interpolated without
+    the foreshortening term (reading R12 of dipole_oracle.c): out [Q, C] float64."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    mu = _f32(mu)
+    if mu.ndim == 1:
+        mu = mu[:, None]
+    q = _f32(queries)
+    n, C, nq = p.shape[0], mu.shape[1], q.shape[0]
+    out = np.zeros((nq, C), np.float64)
+    _load().orc_brute_forward_app(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C,
+                                  int(geometry_channels), _ptr(mu), nq, _ptr(q), _ptr(out))
+    return out
+
+
+def brute_adjoint_app(points, normals, areas, eps, queries, g, geometry_channels):
+    """The transpose of brute_forward_app: dL/dmu [N, C] float64."""
+    p, nr, a = _f32(points), _f32(normals), _f32(areas)
+    e = None if eps is None else _f32(eps)
+    q = _f32(queries)
+    g = _f64(g)
+    if g.ndim == 1:
+        g = g[:, None]
+    n, nq, C = p.shape[0], q.shape[0], g.shape[1]
+    out = np.zeros((n, C), np.float64)
+    _load().orc_brute_adjoint_app(n, _ptr(p), _ptr(nr), _ptr(a), _ptr(e), C,
+                                  int(geometry_channels), nq, _ptr(q), _ptr(g), _ptr(out))
     return out
 
 
@@ -257,8 +291,10 @@ class Tree:
         _load().orc_tree_export(self._h, *[_ptr(o[k]) for k in keys])
         return o
 
-    def update(self, mu):
-        """Tree update of the node moments, eq. (farfield_dipole_features)."""
+    def update(self, mu, geometry_channels=None):
+        """Tree update of the node moments, eq. (farfield_dipole_features).  With
+        geometry_channels = G < C, channels [G, C) are interpolated without the
+        foreshortening term (reading R12)."""
         mu = _f32(mu)
         if mu.ndim == 1:
             mu = mu[:, None]
@@ -266,6 +302,15 @@ class Tree:
             raise ValueError("mu must have one row per point")
         self.C = mu.shape[1]
         _load().orc_tree_update(self._h, _ptr(mu), self.C)
+        self.G = self.C if geometry_channels is None else int(geometry_channels)
+        if not 0 <= self.G <= self.C:
+            raise ValueError("geometry_channels must be in [0, C]")
+        _load().orc_tree_set_geometry_channels(self._h, self.G)
+
+    def _dipole_only(self):
+        if getattr(self, "G", self.C) != self.C:
+            raise NotImplementedError("gradients in x, n and eps are stated for the dipole "
+                                      "kernel only (channels with the foreshortening term)")
 
     def forward(self, queries, beta, counters=False):
         """PrimalQuery for every query (Alg. 1): [Q, C] float64 (and [Q,3] counters)."""
@@ -282,6 +327,7 @@ class Tree:
         """Barnes-Hut spatial gradient of the dipole sum: [Q, C, 3] float64."""
         if self.C is None:
             raise RuntimeError("call update() first")
+        self._dipole_only()
         q = _f32(queries)
         out = np.zeros((q.shape[0], self.C, 3), np.float64)
         _load().orc_bh_forward_grad(self._h, q.shape[0], _ptr(q), float(beta), _ptr(out))
@@ -292,6 +338,7 @@ class Tree:
         be None), two-stage (Sec. 6.2, App. C) extended to the gradient (R9)."""
         if self.C is None:
             raise RuntimeError("call update() first")
+        self._dipole_only()
         q = _f32(queries)
         nq = q.shape[0]
         g64 = None if g is None else _f64(np.asarray(g).reshape(nq, self.C))
@@ -306,6 +353,7 @@ class Tree:
         eps (R10): (dmu [N, C], dn [N, 3], deps [N]) float64, input order."""
         if self.C is None:
             raise RuntimeError("call update() first")
+        self._dipole_only()
         q = _f32(queries)
         nq = q.shape[0]
         g64 = None if g is None else _f64(np.asarray(g).reshape(nq, self.C))

@@ -66,7 +66,17 @@
  *       of rho so that every formula above applies: a = 1/max(r, eps)^3,
  *       b = -3/r^5 outside the cutoff and 0 inside, da/deps = -3/eps^4 inside
  *       and 0 outside, db/deps = 0.  Selected by orc_set_kernel(1).
- *
+ *   R12 Appearance channels without the foreshortening term (Sec. 5.3,
+ *       radiance field details: the paper skips it for its appearance
+ *       attributes in eq. appearance_features and says no more).  The
+ *       foreshortening term is the cosine n.(p - x)/|p - x| of the kernel
+ *       A rho(r/eps) n.(p - x)/(4 pi r^3); without it a point contributes
+ *       A rho(r/eps)/(4 pi r^2) mu.  Channels [0, G) keep the term, channels
+ *       [G, C) skip it (G = C unless set).  A far node contributes, in the
+ *       order of eq. farfield, A~_t rho(d/eps~_t)/(4 pi d^2) m~_t^c with
+ *       m~_t^c = sum_{m in t} A_m mu_m^c / A~_t (the area-weighted mean
+ *       attribute, the counterpart of n~_t^c), and stage 2 of the adjoint
+ *       gives d mu_m^c = sum_{t in AS(m)} (A_m / A~_t) d m~_t^c.
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
  * the radius are specified operation by operation.
  */
@@ -193,6 +203,55 @@ static void point_grad(const double x[3], double px, double py, double pz, doubl
 
 /* out[j*C + c] = sum_m A_m P_eps_m(x_j, p_m) mu[m*C + c].
  * pts, nrm: [n,3]; area, eps: [n] (eps may be NULL: all zero); mu: [n,C]. */
+/* A rho(r/eps) / (4 pi r^2): the kernel without its foreshortening cosine
+ * (R12).  Returns 0 when x == p (R2). */
+static double point_weight_nf(const double x[3], double px, double py, double pz, double A,
+                              double eps) {
+    double dx = px - x[0], dy = py - x[1], dz = pz - x[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return 0.0;
+    return A * rho_r(sqrt(r2), eps) / (4.0 * ORC_PI * r2);
+}
+
+/* The plain definition with channels [G, C) without the foreshortening term
+ * (R12): out[j*C + c] = sum_m w_c(x_j, m) mu_m^c. */
+void orc_brute_forward_app(int64_t n, const float* pts, const float* nrm, const float* area,
+                           const float* eps, int C, int G, const float* mu, int64_t q,
+                           const float* qry, double* out) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < q; ++j) {
+        double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double* o = out + j * C;
+        for (int c = 0; c < C; ++c) o[c] = 0.0;
+        for (int64_t m = 0; m < n; ++m) {
+            double e = eps ? (double)eps[m] : 0.0;
+            double w = point_weight(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], nrm[3 * m],
+                                    nrm[3 * m + 1], nrm[3 * m + 2], area[m], e);
+            double wf = point_weight_nf(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], area[m], e);
+            for (int c = 0; c < C; ++c) o[c] += (c < G ? w : wf) * (double)mu[m * C + c];
+        }
+    }
+}
+
+/* Its transpose: grad[m*C + c] = sum_j g[j*C + c] w_c(x_j, m). */
+void orc_brute_adjoint_app(int64_t n, const float* pts, const float* nrm, const float* area,
+                           const float* eps, int C, int G, int64_t q, const float* qry,
+                           const double* g, double* grad) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < n; ++m) {
+        double* gm = grad + m * C;
+        for (int c = 0; c < C; ++c) gm[c] = 0.0;
+        double e = eps ? (double)eps[m] : 0.0;
+        for (int64_t j = 0; j < q; ++j) {
+            double x[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+            double w = point_weight(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], nrm[3 * m],
+                                    nrm[3 * m + 1], nrm[3 * m + 2], area[m], e);
+            double wf = point_weight_nf(x, pts[3 * m], pts[3 * m + 1], pts[3 * m + 2], area[m], e);
+            for (int c = 0; c < C; ++c) gm[c] += (c < G ? w : wf) * g[j * C + c];
+        }
+    }
+}
+
 void orc_brute_forward(int64_t n, const float* pts, const float* nrm, const float* area,
                        const float* eps, int C, const float* mu, int64_t q,
                        const float* qry, double* out) {
@@ -394,6 +453,8 @@ typedef struct orc_tree {
     int C;
     double* mu;       /* [n,C] sorted attributes */
     double* nt;       /* [nn,3C] n~_t^c, eq. (farfield_dipole_features) */
+    int G;            /* channels [0, G) with the foreshortening term, [G, C) without (R12) */
+    double* mt;       /* [nn,C] m~_t^c = sum A mu / A~ (R12) */
     double *s_area, *s_ap, *s_ae; /* [nn], [nn,3], [nn] double node sums (R7) */
 } orc_tree;
 
@@ -487,7 +548,7 @@ void orc_tree_free(orc_tree* T) {
     free(T->code); free(T->perm); free(T->p); free(T->nrm); free(T->A); free(T->eps);
     free(T->first); free(T->count); free(T->level); free(T->parent); free(T->skip);
     free(T->is_leaf); free(T->leaf_of); free(T->area); free(T->cen); free(T->epsn);
-    free(T->cen32); free(T->r32); free(T->mu); free(T->nt);
+    free(T->cen32); free(T->r32); free(T->mu); free(T->nt); free(T->mt);
     free(T->s_area); free(T->s_ap); free(T->s_ae);
     free(T);
 }
@@ -586,9 +647,12 @@ void orc_tree_update(orc_tree* T, const float* mu, int C) {
     int64_t n = T->n, nn = T->nn;
     free(T->mu);
     free(T->nt);
+    free(T->mt);
     T->C = C;
+    T->G = C;
     T->mu = (double*)malloc(sizeof(double) * n * C);
     T->nt = (double*)calloc((size_t)(nn * 3 * C), sizeof(double));
+    T->mt = (double*)calloc((size_t)(nn * C), sizeof(double));
     for (int64_t i = 0; i < n; ++i)
         for (int c = 0; c < C; ++c) T->mu[i * C + c] = mu[(int64_t)T->perm[i] * C + c];
 #pragma omp parallel for schedule(dynamic, 64)
@@ -604,8 +668,16 @@ void orc_tree_update(orc_tree* T, const float* mu, int C) {
             }
         }
         for (int k = 0; k < 3 * C; ++k) o[k] /= T->area[t];
+        /* R12: the area-weighted mean attribute */
+        double* mo = T->mt + t * C;
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m)
+            for (int c = 0; c < C; ++c) mo[c] += (double)T->A[m] * T->mu[m * C + c];
+        for (int c = 0; c < C; ++c) mo[c] /= T->area[t];
     }
 }
+
+/* Channels [G, C) skip the foreshortening term (R12); call after an update. */
+void orc_tree_set_geometry_channels(orc_tree* T, int G) { T->G = G < 0 ? 0 : G > T->C ? T->C : G; }
 
 /* ------------------------------------------------------------------------ */
 /* Barnes-Hut queries: Alg. 1                                                 */
@@ -636,6 +708,14 @@ static void far_vector(const orc_tree* T, int32_t t, const double x[3], double v
     v[0] = k * dx; v[1] = k * dy; v[2] = k * dz;
 }
 
+/* rho(|p~ - x| / eps~) / (4 pi |p~ - x|^2): the far-field factor of the
+ * channels without the foreshortening term (R12), without A~ and m~. */
+static double far_scalar(const orc_tree* T, int32_t t, const double x[3]) {
+    double dx = T->cen[3 * t] - x[0], dy = T->cen[3 * t + 1] - x[1], dz = T->cen[3 * t + 2] - x[2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    return rho_r(sqrt(d2), T->epsn[t]) / (4.0 * ORC_PI * d2);
+}
+
 typedef struct { int64_t tested, accepted, leafpts; } counters;
 
 /* PrimalQuery(x, node): returns all C channels at once (Sec. 6.3). */
@@ -648,8 +728,12 @@ static void primal_query(const orc_tree* T, const float xf[3], const double x[3]
         double v[3];
         far_vector(T, t, x, v);
         const double* nt = T->nt + (int64_t)t * 3 * C;
-        for (int c = 0; c < C; ++c)
+        for (int c = 0; c < T->G; ++c)
             out[c] += T->area[t] * (v[0] * nt[3 * c] + v[1] * nt[3 * c + 1] + v[2] * nt[3 * c + 2]);
+        if (T->G < C) { /* R12 */
+            double f = far_scalar(T, t, x);
+            for (int c = T->G; c < C; ++c) out[c] += T->area[t] * f * T->mt[(int64_t)t * C + c];
+        }
         k->accepted++;
         return;
     }
@@ -658,7 +742,9 @@ static void primal_query(const orc_tree* T, const float xf[3], const double x[3]
             double w = point_weight(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2],
                                     T->nrm[3 * m], T->nrm[3 * m + 1], T->nrm[3 * m + 2],
                                     T->A[m], T->eps[m]);
-            for (int c = 0; c < C; ++c) out[c] += w * T->mu[m * C + c];
+            double wf = point_weight_nf(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2], T->A[m],
+                                        T->eps[m]);
+            for (int c = 0; c < C; ++c) out[c] += (c < T->G ? w : wf) * T->mu[m * C + c];
         }
         k->leafpts += T->count[t];
         return;
@@ -694,12 +780,20 @@ static void adjoint_query(const orc_tree* T, const float xf[3], const double x[3
         double v[3];
         far_vector(T, t, x, v);
         double* o = dnt + (int64_t)t * 3 * C;
-        for (int c = 0; c < C; ++c)
+        for (int c = 0; c < T->G; ++c)
             for (int a = 0; a < 3; ++a) {
                 double inc = T->area[t] * v[a] * g[c];
 #pragma omp atomic
                 o[3 * c + a] += inc;
             }
+        if (T->G < C) { /* R12: d m~_t^c in the channel's first slot */
+            double f = far_scalar(T, t, x);
+            for (int c = T->G; c < C; ++c) {
+                double inc = T->area[t] * f * g[c];
+#pragma omp atomic
+                o[3 * c] += inc;
+            }
+        }
         return;
     }
     if (T->is_leaf[t]) { /* opened leaf: exact per-point derivative (R3) */
@@ -707,8 +801,10 @@ static void adjoint_query(const orc_tree* T, const float xf[3], const double x[3
             double w = point_weight(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2],
                                     T->nrm[3 * m], T->nrm[3 * m + 1], T->nrm[3 * m + 2],
                                     T->A[m], T->eps[m]);
+            double wf = point_weight_nf(x, T->p[3 * m], T->p[3 * m + 1], T->p[3 * m + 2], T->A[m],
+                                        T->eps[m]);
             for (int c = 0; c < C; ++c) {
-                double inc = w * g[c];
+                double inc = (c < T->G ? w : wf) * g[c];
 #pragma omp atomic
                 dmu[m * C + c] += inc;
             }
@@ -741,9 +837,10 @@ void orc_bh_adjoint(const orc_tree* T, int64_t q, const float* qry, float beta, 
         for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
             double f = (double)T->A[m] / T->area[t];
             const double* d = dnt + (int64_t)t * 3 * C;
-            for (int c = 0; c < C; ++c)
+            for (int c = 0; c < T->G; ++c)
                 gm[c] += f * (T->nrm[3 * m] * d[3 * c] + T->nrm[3 * m + 1] * d[3 * c + 1] +
                               T->nrm[3 * m + 2] * d[3 * c + 2]);
+            for (int c = T->G; c < C; ++c) gm[c] += f * d[3 * c]; /* R12 */
         }
     }
     free(dnt);
@@ -879,9 +976,10 @@ void orc_bh_adjoint_grad(const orc_tree* T, int64_t q, const float* qry, float b
         for (int32_t t = T->leaf_of[m]; t >= 0; t = T->parent[t]) {
             double f = (double)T->A[m] / T->area[t];
             const double* d = dnt + (int64_t)t * 3 * C;
-            for (int c = 0; c < C; ++c)
+            for (int c = 0; c < T->G; ++c)
                 gm[c] += f * (T->nrm[3 * m] * d[3 * c] + T->nrm[3 * m + 1] * d[3 * c + 1] +
                               T->nrm[3 * m + 2] * d[3 * c + 2]);
+            for (int c = T->G; c < C; ++c) gm[c] += f * d[3 * c]; /* R12 */
         }
     }
     free(dnt);
