@@ -130,6 +130,32 @@ int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t
                  void* stream);
 
 /*
+ * dipole_refit with appearance channels that skip the foreshortening term
+ * (Sec. 5.3, radiance field details: the paper interpolates its appearance
+ * attributes by eq. appearance_features without that term and says no more).
+ * Read here as: the term is the cosine n.(p - x)/|p - x| of the kernel, so a
+ * point contributes A_m rho(r/eps_m)/(4 pi r^2) mu_m^c and a far node
+ * rho(d/eps~_t)/(4 pi d^2) M_t^c with M_t^c = sum_{m in t} A_m mu_m^c (the
+ * zeroth-order far field of eq. farfield for this kernel); the adjoint's
+ * stage 2 gives dL/dmu_m^c = A_m sum_{t holding m} dM_t^c.
+ *
+ *   geometry_channels  G in [0, channels]: channels [0, G) use eq. dipole_sum
+ *                      (with the term), channels [G, channels) skip it;
+ *                      G = channels is dipole_refit
+ *
+ * Every query entry point evaluates each channel with its kernel, in one
+ * traversal.  The spatial, normal and radius gradients (dipole_forward_grad,
+ * dipole_adjoint_grad, dipole_adjoint_geom, dipole_adjoint_queries) are
+ * stated for channels with the term only and return DIPOLE_EINVAL on a tree
+ * refit with G < channels.  dipole_tree_export's moments hold M_t^c in the
+ * first slot of such a channel (0 in the other two).
+ * Errors: as dipole_refit; DIPOLE_EINVAL for G outside [0, channels] or, when
+ * G < channels, a tree built with the desingularized kernel.
+ */
+int dipole_refit_appearance(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,
+                            int32_t geometry_channels, void* stream);
+
+/*
  * Primal queries (Alg. 1, PrimalQuery; all channels in one traversal, Sec.
  * 5.3): out[j, c] = Barnes-Hut estimate of D^c(queries[j]).  A node t is far
  * when |x - p~_t| > beta r~_t (strict), evaluated in float as

@@ -208,7 +208,25 @@ int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t
         return dip_fail(DIPOLE_EINVAL, "dipole_refit: channels must be in [1, 64]");
     if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
         return dip_fail(DIPOLE_EINVAL, "dipole_refit: dtype must be DIPOLE_F32 or DIPOLE_BF16");
-    return dip::refit(tree, attrs, channels, dtype, as_stream(stream));
+    return dip::refit(tree, attrs, channels, dtype, channels, as_stream(stream));
+}
+
+int dipole_refit_appearance(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,
+                            int32_t geometry_channels, void* stream) {
+    if (!tree || !attrs)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: tree and attrs are required");
+    if (int rc_dev = check_device(tree, "dipole_refit_appearance")) return rc_dev;
+    if (channels < 1 || channels > dip::kMaxChannels)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: channels must be in [1, 64]");
+    if (geometry_channels < 0 || geometry_channels > channels)
+        return dip_fail(DIPOLE_EINVAL,
+                        "dipole_refit_appearance: geometry_channels must be in [0, channels]");
+    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: dtype must be DIPOLE_F32 or DIPOLE_BF16");
+    if (geometry_channels < channels && tree->kernel != DIPOLE_KERNEL_REGULARIZED)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: channels without the "
+                                       "foreshortening term need the regularized kernel");
+    return dip::refit(tree, attrs, channels, dtype, geometry_channels, as_stream(stream));
 }
 
 int dipole_forward(const dipole_tree* tree, const float* queries, int64_t q, float beta,
@@ -318,6 +336,9 @@ int dipole_adjoint_queries(const dipole_tree* tree, const float* queries, int64_
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: tree is NULL");
     if (int rc_dev = check_device(tree, "dipole_adjoint_queries")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_queries: call dipole_refit first");
+    if (tree->G < tree->C)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: the spatial, normal and radius gradients are "
+                                       "stated for channels with the foreshortening term only");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_queries: q must be in [0, 2^31)");
     if (q > 0 && (!queries || !grad_out || !grad_queries))
@@ -382,6 +403,9 @@ int dipole_forward_grad(const dipole_tree* tree, const float* queries, int64_t q
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: tree is NULL");
     if (int rc_dev = check_device(tree, "dipole_forward_grad")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_forward_grad: call dipole_refit first");
+    if (tree->G < tree->C)
+        return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: the spatial, normal and radius gradients are "
+                                       "stated for channels with the foreshortening term only");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_forward_grad: q must be in [0, 2^31)");
     if (q > 0 && (!queries || !grad_x))
@@ -404,6 +428,9 @@ int dipole_adjoint_grad(dipole_tree* tree, const float* queries, int64_t q, floa
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: tree is NULL");
     if (int rc_dev = check_device(tree, "dipole_adjoint_grad")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_grad: call dipole_refit first");
+    if (tree->G < tree->C)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: the spatial, normal and radius gradients are "
+                                       "stated for channels with the foreshortening term only");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: q must be in [0, 2^31)");
     if (!grad_attrs) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_grad: grad_attrs is required");
@@ -432,6 +459,9 @@ int dipole_adjoint_geom(dipole_tree* tree, const float* queries, int64_t q, floa
     if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: tree is NULL");
     if (int rc_dev = check_device(tree, "dipole_adjoint_geom")) return rc_dev;
     if (tree->C == 0) return dip_fail(DIPOLE_ESTATE, "dipole_adjoint_geom: call dipole_refit first");
+    if (tree->G < tree->C)
+        return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: the spatial, normal and radius gradients are "
+                                       "stated for channels with the foreshortening term only");
     if (q < 0 || q > (int64_t)INT32_MAX)
         return dip_fail(DIPOLE_EINVAL, "dipole_adjoint_geom: q must be in [0, 2^31)");
     if (!grad_attrs && !grad_normals && !grad_radii)

@@ -30,6 +30,7 @@ struct QueryArgs {
     float beta;
     int kernel;         // dipole_kernel of the tree
     int C;
+    int G;              // channels [0, G) with the foreshortening term, [G, C) without
     int Cp;
     const void* mu;
     const float* S;

@@ -135,11 +135,11 @@ template <int CP, typename AT>
 __global__ void __launch_bounds__(kLeafThreads) k_refit_leaves(
     int64_t n, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ count,
-    const AT* __restrict__ attrs, int C, AT* __restrict__ mu, float* __restrict__ S,
+    const AT* __restrict__ attrs, int C, int G, AT* __restrict__ mu, float* __restrict__ S,
     unsigned* __restrict__ cmax) {
     constexpr int SR = srow(CP);
     constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
-    constexpr int RW = CH + 3;           // staged row: CH attributes, then A n
+    constexpr int RW = CH + 4;           // staged row: CH attributes, then A n, A
     __shared__ float row[kLeafThreads * RW];
     __shared__ unsigned smax[3 * CP];
     for (int j = threadIdx.x; j < 3 * CP; j += blockDim.x) smax[j] = 0u;
@@ -165,18 +165,19 @@ __global__ void __launch_bounds__(kLeafThreads) k_refit_leaves(
             row[tid * RW + CH] = w.x;
             row[tid * RW + CH + 1] = w.y;
             row[tid * RW + CH + 2] = w.z;
+            row[tid * RW + CH + 3] = w.w;
             __syncthreads();
             if (head) {
                 float sacc[3 * CH];
 #pragma unroll
                 for (int j = 0; j < 3 * CH; ++j) sacc[j] = 0.0f;
                 for (int i = 0; i < k; ++i) {
-                    float v[CH], wx, wy, wz;
+                    float v[CH], wx, wy, wz, wa;
                     if (tid + i < kLeafThreads) {
                         const float* r = row + (tid + i) * RW;
 #pragma unroll
                         for (int c = 0; c < CH; ++c) v[c] = r[c];
-                        wx = r[CH]; wy = r[CH + 1]; wz = r[CH + 2];
+                        wx = r[CH]; wy = r[CH + 1]; wz = r[CH + 2]; wa = r[CH + 3];
                     } else {  // past the block's points
                         const int64_t mi = m + i;
                         const int64_t oi = perm[mi];
@@ -184,13 +185,17 @@ __global__ void __launch_bounds__(kLeafThreads) k_refit_leaves(
                         for (int c = 0; c < CH; ++c)
                             v[c] = c0 + c < C ? to_f<AT>(attrs[oi * C + c0 + c]) : 0.0f;
                         const float4 wi = pts[mi].w;
-                        wx = wi.x; wy = wi.y; wz = wi.z;
+                        wx = wi.x; wy = wi.y; wz = wi.z; wa = wi.w;
                     }
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
-                        sacc[3 * c] = fmaf(wx, v[c], sacc[3 * c]);
-                        sacc[3 * c + 1] = fmaf(wy, v[c], sacc[3 * c + 1]);
-                        sacc[3 * c + 2] = fmaf(wz, v[c], sacc[3 * c + 2]);
+                        if (c0 + c < G) {  // S^c = sum A n mu^c (eq. farfield_dipole_features)
+                            sacc[3 * c] = fmaf(wx, v[c], sacc[3 * c]);
+                            sacc[3 * c + 1] = fmaf(wy, v[c], sacc[3 * c + 1]);
+                            sacc[3 * c + 2] = fmaf(wz, v[c], sacc[3 * c + 2]);
+                        } else {  // no foreshortening term: M^c = sum A mu^c in the first slot
+                            sacc[3 * c] = fmaf(wa, v[c], sacc[3 * c]);
+                        }
                     }
                 }
 #pragma unroll
@@ -442,7 +447,7 @@ __global__ void __launch_bounds__(128) k_stage2(
     int64_t nn, const PointRec* __restrict__ pts, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ first, const int32_t* __restrict__ count,
     const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ parent,
-    const float* __restrict__ dS, const float* __restrict__ dmu, int C, int accumulate,
+    const float* __restrict__ dS, const float* __restrict__ dmu, int C, int G, int accumulate,
     float* __restrict__ grad) {
     constexpr int SR = srow(CP);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn;
@@ -469,7 +474,9 @@ __global__ void __launch_bounds__(128) k_stage2(
                     const int ch = c0 + c;
                     if (ch >= CP) break;
                     if (ch >= C) continue;
-                    float v = fmaf(w.x, D[3 * c], fmaf(w.y, D[3 * c + 1], w.z * D[3 * c + 2]));
+                    // channels without the foreshortening term: M^c = sum A mu^c
+                    float v = ch < G ? fmaf(w.x, D[3 * c], fmaf(w.y, D[3 * c + 1], w.z * D[3 * c + 2]))
+                                     : w.w * D[3 * c];
                     v += dmu[m * CP + ch];
                     float* dst = grad + o * C + ch;
                     *dst = accumulate ? *dst + v : v;
@@ -566,8 +573,8 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     const int64_t pblocks = (t->n + kLeafThreads - 1) / kLeafThreads, pcap = (int64_t)num_sms() * 8;
     note_launch();
     k_refit_leaves<CP, AT><<<(unsigned)(pblocks < pcap ? pblocks : pcap), kLeafThreads, 0, s>>>(
-        t->n, t->pts, t->perm, t->leaf_of, t->count, (const AT*)attrs, t->C, (AT*)t->mu, t->S,
-        t->fix_cmax);
+        t->n, t->pts, t->perm, t->leaf_of, t->count, (const AT*)attrs, t->C, t->G, (AT*)t->mu,
+        t->S, t->fix_cmax);
     note_launch();
     k_refit_tiles<CP><<<ntiles, kRefitThreads, 0, s>>>(t->nn, t->is_leaf, t->S, t->fix_cmax,
                                                        t->fix_kexp, t->fix_tsum, t->fix_done);
@@ -586,7 +593,7 @@ void launch_stage2(const dipole_tree* t, const float* dS, const float* dmu, floa
     int64_t blocks = (t->nn + 127) / 128;
     int64_t cap = (int64_t)num_sms() * 16;
     note_launch(); k_stage2<CP><<<(unsigned)(blocks < cap ? blocks : cap), 128, 0, s>>>(
-        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, dS, dmu, t->C,
+        t->nn, t->pts, t->perm, t->first, t->count, t->is_leaf, t->parent, dS, dmu, t->C, t->G,
         accumulate, grad);
 }
 
@@ -602,7 +609,7 @@ int padded_channels(int C) {
     return 64;
 }
 
-int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
+int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream_t s) {
     const int Cp = padded_channels(C);
     const int SR = srow(Cp);
     if (t->attr_Cp_alloc != Cp || t->attr_dtype_alloc != dtype) {
@@ -635,6 +642,7 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s) {
         t->attr_dtype_alloc = dtype;
     }
     t->C = C;
+    t->G = G;
     t->Cp = Cp;
     t->dtype = dtype;
 #define DIP_REFIT_CASE(K)                                                          \

@@ -31,9 +31,16 @@ namespace {
 // two (k_fwd_items) and its two parts add into the zeroed output (a sum of two
 // floats does not depend on their order); the adjoint with a plan cuts every
 // walk at the nodes the forward recorded (k_plan_items).
+//
+// KERN: 0 the regularized kernel, 1 the desingularized one, 2 the regularized
+// kernel with channels [a.G, C) interpolated without the foreshortening term
+// (a point adds A rho(r/eps)/(4 pi r^2) mu, a far node rho(d/eps~)/(4 pi d^2)
+// M with M = sum A mu in the first slot of the channel's moment row).
 template <int CP, typename AT, int MODE, int KERN, bool RANGED>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
 k_query(const QueryArgs a) {
+    constexpr bool NF = KERN == 2;       // some channels skip the foreshortening term
+    constexpr int KR = NF ? 0 : KERN;    // the radial factor's kernel
     constexpr int SR = srow(CP);
     constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
     constexpr unsigned FULL = 0xffffffffu;
@@ -84,10 +91,10 @@ k_query(const QueryArgs a) {
         }
 
         // Forward sums: plain float partial sums (part), folded every kFoldSteps
-        // warp steps into a Kahan-compensated sum (acc, cmp) for small channel
-        // counts; per-term Kahan for large ones (register budget).
-        constexpr bool kBlocked = CP <= 8;
-        constexpr unsigned kFoldSteps = 16;
+        // warp steps into a Kahan-compensated sum (acc, cmp) for up to 16
+        // channels; per-term Kahan for more (register budget).
+        constexpr bool kBlocked = CP <= 16;
+        constexpr unsigned kFoldSteps = 32;
         float acc[MODE == kForward ? CP : 1], cmp[MODE == kForward ? CP : 1];
         float part[MODE == kForward && kBlocked ? CP : 1];
         float g[MODE == kAdjoint ? CP : 1];
@@ -195,8 +202,11 @@ k_query(const QueryArgs a) {
             } else {
                 if (__any_sync(FULL, far)) {
                     // far field, eq. farfield: rho(d/eps~) S.(p~ - x) / d^3 (1/4pi applied at the end)
-                    float k = 0.f;
-                    if (far) k = radial_over_d3(d2, __int_as_float(meta.w), KERN);
+                    float k = 0.f, wf = 0.f;
+                    if (far) {
+                        k = radial_over_d3(d2, __int_as_float(meta.w), KR);
+                        if (NF) wf = k * (d2 * rsqrtf(d2));  // rho(d/eps~)/d^2
+                    }
                     const float vx = -k * dx, vy = -k * dy, vz = -k * dz;
                     if (MODE == kForward) {
                         const float* Sr = a.S + (size_t)n * SR;
@@ -210,32 +220,78 @@ k_query(const QueryArgs a) {
                             }
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
-                                const float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
-                                if (far) add_term(c0 + c, term);
+                                float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
+                                if (NF && c0 + c >= a.G) term = s[3 * c] * wf;
+                                // blocked sums: k = wf = 0 on lanes that did not take the
+                                // node, whose term is an exact zero
+                                if (kBlocked) part[c0 + c] += term;
+                                else if (far) add_term(c0 + c, term);
                             }
                         }
-                    } else if (MODE == kAdjoint) {
+                    } else if (MODE == kAdjoint && !NF) {
                         // eq. farfield_gradient: dS_t^c += rho (p~ - x)/d^3 g^c
                         float* dst = a.dS + (size_t)n * SR;
 #pragma unroll
                         for (int c0 = 0; c0 < CP; c0 += CH)
                             adjoint_far_reduce<CH>(vx, vy, vz, g + c0, dst + 3 * c0, ord[0], lane);
+                    } else if (MODE == kAdjoint) {
+                        // channels without the foreshortening term add rho/d^2 g^c to
+                        // the first slot of their row; the lanes' channel order
+                        // (ord) decides which vector each slot of v gets
+                        float* dst = a.dS + (size_t)n * SR;
+#pragma unroll
+                        for (int c0 = 0; c0 < CP; c0 += CH) {
+                            float v[3 * CH];
+#pragma unroll
+                            for (int i = 0; i < CH; ++i) {
+                                const bool geo = c0 + ord[i] < a.G;
+                                const float gi = g[c0 + i];
+                                v[3 * i] = (geo ? vx : wf) * gi;
+                                v[3 * i + 1] = geo ? vy * gi : 0.f;
+                                v[3 * i + 2] = geo ? vz * gi : 0.f;
+                            }
+                            adjoint_vec_reduce<CH>(v, dst + 3 * c0, ord[0], lane);
+                        }
                     }
                 }
 
-                // opened-leaf point term: the dipole kernel times A_m n_m . (p_m - x)
-                auto point_k = [&](const PointRec& pr) {
+                // opened-leaf point term: the dipole kernel times A_m n_m . (p_m - x);
+                // kn: without the foreshortening term, rho(r/eps) A_m / r^2
+                auto point_k2 = [&](const PointRec& pr, float& kn) {
                     float k = 0.f;
+                    kn = 0.f;
                     if (open_leaf) {
                         const float ex = pr.geo.x - x0, ey = pr.geo.y - x1, ez = pr.geo.z - x2;
                         const float r2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                        if (r2 > 0.f)
-                            k = radial_over_d3(r2, pr.geo.w, KERN) *
-                                fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
+                        if (r2 > 0.f) {
+                            const float kr = radial_over_d3(r2, pr.geo.w, KR);
+                            k = kr * fmaf(pr.w.x, ex, fmaf(pr.w.y, ey, pr.w.z * ez));
+                            if (NF) kn = kr * pr.w.w * (r2 * rsqrtf(r2));
+                        }
                     }
                     return k;
                 };
-                if (MODE == kAdjoint && __any_sync(FULL, open_leaf)) {
+                auto point_k = [&](const PointRec& pr) {
+                    float kn;
+                    return point_k2(pr, kn);
+                };
+                if (MODE == kAdjoint && NF && __any_sync(FULL, open_leaf)) {
+                    // opened leaf, one point at a time: each channel takes the
+                    // kernel of its kind
+                    const int f = meta.y, cnt = meta.z;
+                    for (int j = 0; j < cnt; ++j) {
+                        float kn;
+                        const float kd = point_k2(pts[f + j], kn);
+                        float* dst = a.dmu + (size_t)(f + j) * CP;
+#pragma unroll
+                        for (int c0 = 0; c0 < CP; c0 += CH) {
+                            float v[CH];
+#pragma unroll
+                            for (int i = 0; i < CH; ++i) v[i] = (c0 + ord[i] < a.G ? kd : kn) * g[c0 + i];
+                            adjoint_scalar_reduce<CH>(v, dst + c0, ord[0], lane);
+                        }
+                    }
+                } else if (MODE == kAdjoint && __any_sync(FULL, open_leaf)) {
                     // opened leaf, points in pairs (adjoint_point_pair_reduce)
                     const int f = meta.y, cnt = meta.z;
                     for (int j = 0; j < cnt; j += 2) {
@@ -252,7 +308,8 @@ k_query(const QueryArgs a) {
                     // opened leaf: exact sum over its points (eq. dipole_sum)
                     const int f = meta.y, cnt = meta.z;
                     for (int j = 0; j < cnt; ++j) {
-                        const float k = point_k(pts[f + j]);
+                        float kn;
+                        const float k = point_k2(pts[f + j], kn);
                         if (MODE == kForward) {
                             const AT* mrow = reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * CP;
 #pragma unroll
@@ -260,8 +317,11 @@ k_query(const QueryArgs a) {
                                 float m[CH];
                                 load_row<AT>(mrow + c0, m, CH);
 #pragma unroll
-                                for (int c = 0; c < CH; ++c)
-                                    if (open_leaf) add_term(c0 + c, k * m[c]);
+                                for (int c = 0; c < CH; ++c) {
+                                    const float v = (NF && c0 + c >= a.G ? kn : k) * m[c];
+                                    if (kBlocked) part[c0 + c] += v;  // k = kn = 0 off the leaf
+                                    else if (open_leaf) add_term(c0 + c, v);
+                                }
                             }
                         }
                     }
@@ -536,15 +596,19 @@ void launch_query_k(const QueryArgs& a, cudaStream_t s) {
 // branches cost the plain kernels registers.
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
+    // kernel 2: the regularized kernel with channels that skip the foreshortening term
+    const int kern = (MODE != kCount && a.G < a.C) ? 2 : a.kernel;
     if constexpr (MODE == kAdjoint || MODE == kForward) {
         if (a.items) {
-            if (a.kernel == 0) launch_query_k<CP, AT, MODE, 0, true>(a, s);
-            else launch_query_k<CP, AT, MODE, 1, true>(a, s);
+            if (kern == 0) launch_query_k<CP, AT, MODE, 0, true>(a, s);
+            else if (kern == 1) launch_query_k<CP, AT, MODE, 1, true>(a, s);
+            else launch_query_k<CP, AT, MODE, 2, true>(a, s);
             return;
         }
     }
-    if (MODE == kCount || a.kernel == 0) launch_query_k<CP, AT, MODE, 0, false>(a, s);
-    else launch_query_k<CP, AT, MODE, 1, false>(a, s);
+    if (MODE == kCount || kern == 0) launch_query_k<CP, AT, MODE, 0, false>(a, s);
+    else if (kern == 1) launch_query_k<CP, AT, MODE, 1, false>(a, s);
+    else if constexpr (MODE != kCount) launch_query_k<CP, AT, MODE, 2, false>(a, s);
 }
 
 template <int MODE>
@@ -697,6 +761,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.beta = beta;
     a.kernel = t->kernel;
     a.C = t->C;
+    a.G = t->G;
     a.Cp = t->Cp;
     a.mu = t->mu;
     a.S = t->S;
@@ -839,6 +904,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.beta = call.beta;
         a.kernel = t->kernel;
         a.C = t->C;
+        a.G = t->G;
         a.Cp = t->Cp;
         a.mu = t->mu;
         a.S = t->S;

@@ -47,6 +47,7 @@ struct dipole_tree {
 
     // attributes (set by refit)
     int C = 0;
+    int G = 0;                   // channels [0, G) with the foreshortening term, [G, C) without
     int Cp = 0;
     int dtype = 0;
     void* mu = nullptr;          // [n, Cp] float or bf16, Morton order
@@ -95,7 +96,9 @@ int import_tree(dipole_tree* t, const float* points, const float* normals, const
                 const int32_t* skip_h, const int32_t* is_leaf_h, cudaStream_t s);
 
 // Tree update of node moments (eq. farfield_dipole_features).
-int refit(dipole_tree* t, const void* attrs, int C, int dtype, cudaStream_t s);
+// Channels [G, C) skip the foreshortening term: their moment row holds
+// M^c = sum A mu^c in its first slot (0 in the other two).
+int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream_t s);
 
 // Query modes: the dipole sum (eq. dipole_sum with Alg. 1), its adjoint, the
 // traversal counters, the sum with its spatial gradient, the adjoint of both,

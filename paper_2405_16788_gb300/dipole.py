@@ -38,7 +38,8 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_forward_grad", "dipole_adjoint_grad", "dipole_adjoint_geom",
             "dipole_forward_grid", "dipole_adjoint_acc_size", "dipole_adjoint_stage1",
             "dipole_adjoint_stage2", "dipole_adjoint_queries", "dipole_query_packet_counts",
-            "dipole_device_allocations", "dipole_traversal_timer", "dipole_traversal_elapsed"]
+            "dipole_device_allocations", "dipole_traversal_timer", "dipole_traversal_elapsed",
+            "dipole_refit_appearance"]
 
 
 class DipoleError(RuntimeError):
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "dipole_adjoint_queries": [P, P, I64, F, P, P, I32, P],
             "dipole_query_packet_counts": [P, P, I64, F, P, P, P],
             "dipole_traversal_timer": [I32],
+            "dipole_refit_appearance": [P, P, I32, I32, I32, P],
             "dipole_traversal_elapsed": [I32, P, P],
         }
         for name, args in sig.items():
@@ -211,6 +213,19 @@ def dipole_refit(tree: int, attrs: torch.Tensor, stream=None):
     p = _dev(attrs, "attrs", dtype=None)
     _check(load_library().dipole_refit(ctypes.c_void_p(tree), p, int(attrs.shape[1]), dt,
                                        _stream(stream)))
+
+
+def dipole_refit_appearance(tree: int, attrs: torch.Tensor, geometry_channels: int, stream=None):
+    """Refit with channels [geometry_channels, C) interpolated without the
+    foreshortening term (the paper's appearance attributes)."""
+    if attrs.dim() == 1:
+        attrs = attrs[:, None]
+    dt = {torch.float32: DIPOLE_F32, torch.bfloat16: DIPOLE_BF16}.get(attrs.dtype)
+    if dt is None:
+        raise TypeError("attrs must be float32 or bfloat16")
+    p = _dev(attrs, "attrs", dtype=None)
+    _check(load_library().dipole_refit_appearance(ctypes.c_void_p(tree), p, int(attrs.shape[1]),
+                                                  dt, int(geometry_channels), _stream(stream)))
 
 
 def dipole_forward(tree: int, queries: torch.Tensor, beta: float, out: torch.Tensor,
@@ -508,13 +523,18 @@ class DipoleTree:
     def info(self) -> dict:
         return dipole_tree_info_get(self.handle)
 
-    def refit(self, attrs: torch.Tensor, stream=None):
+    def refit(self, attrs: torch.Tensor, stream=None, geometry_channels: int | None = None):
+        """Tree update (eq. farfield_dipole_features).  geometry_channels = G < C:
+        channels [G, C) skip the foreshortening term (appearance attributes)."""
         if attrs.dim() == 1:
             attrs = attrs[:, None]
         if attrs.shape[0] != self.n:
             raise ValueError("attrs must have one row per point")
         attrs = attrs.contiguous()
-        dipole_refit(self.handle, attrs, stream)
+        if geometry_channels is None:
+            dipole_refit(self.handle, attrs, stream)
+        else:
+            dipole_refit_appearance(self.handle, attrs, geometry_channels, stream)
         self.C = int(attrs.shape[1])
         self._attrs = attrs
 
