@@ -66,6 +66,7 @@ def _load():
         lib.orc_brute_forward_app.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _P, _I64, _P, _P]
         lib.orc_brute_adjoint_app.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _I64, _P, _P, _P]
         lib.orc_tree_set_geometry_channels.argtypes = [_P, _I]
+        lib.orc_bh_near_ties.argtypes = [_P, _I64, _P, _F, _P]
         lib.orc_tree_build.restype = _P
         lib.orc_tree_build.argtypes = [_I64, _P, _P, _P, _P, _I, _I]
         lib.orc_tree_free.argtypes = [_P]
@@ -322,6 +323,14 @@ class Tree:
         cnt = np.zeros((nq, 3), np.int64) if counters else None
         _load().orc_bh_forward(self._h, nq, _ptr(q), float(beta), _ptr(out), _ptr(cnt))
         return (out, cnt) if counters else out
+
+    def near_ties(self, queries, beta):
+        """Per query, the tested nodes whose double distance is within 1e-6 d of
+        beta r~ (the far test's near ties, a diagnostic of reading R6): int64 [Q]."""
+        q = _f32(queries)
+        out = np.zeros(q.shape[0], np.int64)
+        _load().orc_bh_near_ties(self._h, q.shape[0], _ptr(q), float(beta), _ptr(out))
+        return out
 
     def forward_grad(self, queries, beta):
         """Barnes-Hut spatial gradient of the dipole sum: [Q, C, 3] float64."""

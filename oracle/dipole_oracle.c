@@ -770,6 +770,32 @@ void orc_bh_forward(const orc_tree* T, int64_t q, const float* qry, float beta, 
     }
 }
 
+/* Near ties of the far test (R6): the walk of PrimalQuery, counting the
+ * tested nodes whose distance from the query is within 1e-6 d of beta r~
+ * in double, |d - beta r~| < 1e-6 d.  There the float decision could differ
+ * from a double one; the float decision itself is the one taken (R6), so a
+ * GPU taking the same float steps agrees with the oracle even there.  A
+ * diagnostic of how close a workload's decisions come to the boundary. */
+static int64_t near_ties_query(const orc_tree* T, const float xf[3], const double x[3], int32_t t,
+                               float beta) {
+    double dx = (double)T->cen32[3 * t] - x[0], dy = (double)T->cen32[3 * t + 1] - x[1],
+           dz = (double)T->cen32[3 * t + 2] - x[2];
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    int64_t k = fabs(d - (double)beta * (double)T->r32[t]) < 1e-6 * d ? 1 : 0;
+    if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta) || T->is_leaf[t]) return k;
+    for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c]) k += near_ties_query(T, xf, x, c, beta);
+    return k;
+}
+
+void orc_bh_near_ties(const orc_tree* T, int64_t q, const float* qry, float beta, int64_t* out) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < q; ++j) {
+        float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
+        double x[3] = {xf[0], xf[1], xf[2]};
+        out[j] = near_ties_query(T, xf, x, 0, beta);
+    }
+}
+
 /* AdjointQuery(dD, x, node): stage 1 of the two-stage scheme (Sec. 6.2).
  * dnt: [nn,3C] node gradients d n~_t; dmu: [n,C] sorted, for opened leaves. */
 static void adjoint_query(const orc_tree* T, const float xf[3], const double x[3],

@@ -249,3 +249,24 @@ def test_big_path_outside_queries_and_repeatability():
     ot.update(w.mu)
     ref = ot.forward(q, 2.0)
     assert np.all(normwise(y1, ref) <= TOL)
+
+
+def test_decisions_at_the_far_test_boundary():
+    """Queries placed on the boundary spheres |x - p~| = beta r~ of many nodes (in
+    float, some land exactly on it, where the strict test opens the node): the
+    GPU takes the oracle's decisions (per-query counts bit-exact) and its sums
+    match (1e-4); the oracle's near-tie diagnostic sees them."""
+    w = syn.workload("scene-200k", scale=0.05)
+    ot = oracle_tree(w.cloud)
+    ot.update(w.mu)
+    ex = ot.export()
+    rng = np.random.default_rng(17)
+    inner = np.flatnonzero(ex["is_leaf"] == 0)
+    t = rng.choice(inner, 3000)
+    u = rng.normal(size=(3000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    q = (ex["cen32"][t].astype(np.float64) + 2.0 * ex["r32"][t, None].astype(np.float64) * u).astype(np.float32)
+    assert ot.near_ties(q, 2.0).sum() >= 1000
+    y, ref, c, rc = _run(w.cloud, w.mu, q)
+    assert np.all(normwise(y, ref) <= TOL)
+    assert np.array_equal(c.astype(np.int64), rc)

@@ -149,7 +149,7 @@ def test_render_loss_gradient_matches_oracle_finite_differences():
                 args.append(sc.loss_from(Dp, Gp, Dsp, Gsp, idx, xs, wsh, dsh, target))
             fd[j, ch] = (args[0] - args[1]) / (2 * h)
     err = normwise(grad[pts], fd)
-    assert np.all(err <= 1e-2), err
+    assert np.all(err <= 1e-3), err  # the gradient tolerance (measured ~5e-6)
 
 
 @pytest.mark.parametrize("dtype", ["float32", "bfloat16"])

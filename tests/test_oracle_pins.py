@@ -371,3 +371,21 @@ def test_far_test_is_strict_and_scales_with_beta():
     # the offset is taken from the node centre, per axis
     assert not oracle.far_test([10.0, 20.0, 30.0], [7.0, 16.0, 30.0], 2.5, 2.0)
     assert oracle.far_test([10.0, 20.0, 30.0], [7.0, 16.0, 29.5], 2.5, 2.0)
+
+
+def test_near_tie_diagnostic_counts_boundary_queries():
+    """The oracle reports far tests within 1e-6 d of the boundary |x - p~| = beta r~
+    (reading R6's diagnostic): a query placed on a node's boundary sphere is
+    counted there; one placed at twice that distance is not counted at that node."""
+    p = np.array([[0.0, 0.0, 0.0], [0.6, 0.2, -0.1]], np.float32)
+    n = np.array([[0, 0, 1], [1, 0, 0]], np.float32)
+    A = np.array([0.3, 0.7], np.float32)
+    T = oracle.Tree(p, n, A, None, leaf_size=1)
+    T.update(np.ones((2, 1), np.float32))
+    ex = T.export()
+    c, r = ex["cen32"][0].astype(np.float64), float(ex["r32"][0])
+    u = np.array([0.36, 0.48, 0.8])
+    on = (c + 2.0 * r * (1 + 1e-9) * u).astype(np.float32)[None]
+    off = (c + 4.0 * r * u).astype(np.float32)[None]
+    assert T.near_ties(on, 2.0)[0] >= 1
+    assert T.near_ties(off, 2.0)[0] == 0
