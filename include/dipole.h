@@ -264,7 +264,7 @@ int dipole_adjoint_stage2(const dipole_tree* tree, const float* acc, float* grad
  *                                  order of the queries (a permutation of [0, q))
  *   plan_cost [8 * ceil(q / 32)]   uint32, written by dipole_forward_planned: 8 words per
  *                                  32-query packet: its traversal steps, the nodes its walk
- *                                  visited at steps 256, 512, 768 of its lower part, the node
+ *                                  visited at steps 128, 256, 384 of its lower part, the node
  *                                  where the walk was split in two, and the same three for its
  *                                  upper part (0 = none)
  * dipole_forward_planned = dipole_forward that also writes the plan.  (Every forward
@@ -275,7 +275,7 @@ int dipole_adjoint_stage2(const dipole_tree* tree, const float* acc, float* grad
  * dipole_adjoint_planned = dipole_adjoint that reads the plan of a forward on the
  *   same queries (the order of every training step: primal queries, then their
  *   adjoint, Sec. 6.2) instead of sorting them again; it cuts every packet's walk at
- *   the recorded nodes into preorder ranges of about 256 steps and runs the ranges
+ *   the recorded nodes into preorder ranges of about 128 steps and runs the ranges
  *   longest first.  Results do not depend on the plan: any increasing sequence of
  *   cuts partitions the walk; a plan from other queries only changes the balance.  It
  *   must come from a forward with the same q (plan_perm a permutation of [0, q)),

@@ -57,11 +57,11 @@ struct QueryArgs {
 
 // Query plan, kPlanWords words per 32-query packet: [0] the packet's warp
 // steps (all its items together); [1..3] the nodes its lower forward item
-// visited at its steps 256, 512, 768; [4] the node where the forward split
+// visited at its steps 128, 256, 384; [4] the node where the forward split
 // the walk; [5..7] the same as [1..3] for the upper item (0 = none).  Any
 // increasing subsequence of [1..7] inside (0, nn) partitions the walk, so a
 // stale or foreign plan changes only the balance of an adjoint, never a result.
-constexpr unsigned kCutSteps = 256u;
+constexpr unsigned kCutSteps = 128u;
 constexpr unsigned kPartCuts = 3u;
 constexpr unsigned kPlanWords = 8u;
 

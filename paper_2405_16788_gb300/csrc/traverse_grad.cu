@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                         kahan_add(acc[i], cmp[i], part[i]);
                         part[i] = 0.f;
                     }
-                    // plan record (first channel group): nodes of this part's steps 256, 512, 768
+                    // plan record (first channel group): nodes of this part's steps 128, 256, 384
                     if (RANGED && a.plan && c0 == 0 && lane == 0 && (gsteps & (kCutSteps - 1u)) == 0u &&
                         gsteps <= kCutSteps * kPartCuts)
                         a.plan[(size_t)pm * kPlanWords + 1u + 4u * half + gsteps / kCutSteps - 1u] = n;

@@ -293,7 +293,7 @@ def dipole_adjoint_queries(tree: int, queries: torch.Tensor, beta: float, grad_o
 class QueryPlan:
     """Caller-owned query plan: the Morton order of a query batch and a record
     of each 32-query packet's walk (its steps and the nodes where it passed
-    every 256th step), written by the forward (dipole_forward_planned,
+    every 128th step), written by the forward (dipole_forward_planned,
     dipole_forward_grad) and read by the adjoint on the same queries."""
 
     WORDS_PER_PACKET = 8
