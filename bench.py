@@ -865,7 +865,7 @@ def loop_row(torch, dev, steps):
 
 
 def dp_cp(C: int) -> int:
-    for k in (1, 2, 4, 8, 16, 32, 64):
+    for k in (1, 2, 4, 8, 16, 32, 36, 64):
         if C <= k:
             return k
     return 64

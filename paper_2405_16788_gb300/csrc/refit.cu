@@ -606,6 +606,7 @@ int padded_channels(int C) {
     if (C <= 8) return 8;
     if (C <= 16) return 16;
     if (C <= 32) return 32;
+    if (C <= 36) return 36;  // 32 appearance channels plus geometry, in chunks of 4
     return 64;
 }
 
@@ -657,6 +658,7 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream
         DIP_REFIT_CASE(8)
         DIP_REFIT_CASE(16)
         DIP_REFIT_CASE(32)
+        DIP_REFIT_CASE(36)
         DIP_REFIT_CASE(64)
         default:
             return dip_fail(-1, "dipole_refit: unsupported channel count");
@@ -679,6 +681,7 @@ int stage2(const dipole_tree* t, const float* dS, const float* dmu, float* grad,
         case 8: launch_stage2<8>(t, dS, dmu, grad, accumulate, s); break;
         case 16: launch_stage2<16>(t, dS, dmu, grad, accumulate, s); break;
         case 32: launch_stage2<32>(t, dS, dmu, grad, accumulate, s); break;
+        case 36: launch_stage2<36>(t, dS, dmu, grad, accumulate, s); break;
         case 64: launch_stage2<64>(t, dS, dmu, grad, accumulate, s); break;
         default: return dip_fail(-1, "dipole_adjoint: unsupported channel count");
     }
@@ -707,6 +710,7 @@ int stage2_geom(const dipole_tree* t, float* grad_n, float* grad_eps, int accumu
         DIP_S2G_CASE(8)
         DIP_S2G_CASE(16)
         DIP_S2G_CASE(32)
+        DIP_S2G_CASE(36)
         DIP_S2G_CASE(64)
         default:
             return dip_fail(-1, "stage2_geom: unsupported channel count");

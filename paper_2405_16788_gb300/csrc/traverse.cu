@@ -48,7 +48,8 @@ __device__ __forceinline__ void prefetch_l1(const void* p, int bytes, int lane) 
 // (a point adds A rho(r/eps)/(4 pi r^2) mu, a far node rho(d/eps~)/(4 pi d^2)
 // M with M = sum A mu in the first slot of the channel's moment row).
 template <int CP, typename AT, int MODE, int KERN, bool RANGED>
-__global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6 : 1)
+__global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6
+                                          : (MODE == kForward && CP <= 32) ? 3 : (MODE == kForward && CP <= 36) ? 2 : 1)
 k_query(const QueryArgs a) {
     constexpr bool NF = KERN == 2;       // some channels skip the foreshortening term
     constexpr int KR = NF ? 0 : KERN;    // the radial factor's kernel
@@ -102,16 +103,38 @@ k_query(const QueryArgs a) {
         }
 
         // Forward sums: plain float partial sums (part), folded every kFoldSteps
-        // warp steps into a Kahan-compensated sum (acc, cmp) for up to 16
-        // channels; per-term Kahan for more (register budget).
-        constexpr bool kBlocked = CP <= 16;
+        // warp steps into a Kahan-compensated sum (acc, cmp) for up to 36
+        // channels; per-term Kahan for more (register budget).  From 8 channels
+        // on the Kahan pairs live in shared memory (one column per thread, read
+        // and written only at a fold), which leaves the registers to the walk
+        // and keeps three blocks resident per SM.
+        constexpr bool kBlocked = CP <= 36;
         constexpr unsigned kFoldSteps = 32;
-        float acc[MODE == kForward ? CP : 1], cmp[MODE == kForward ? CP : 1];
+        constexpr bool kSmem = MODE == kForward && CP >= 8 && CP <= 36;
+        constexpr int kRegSums = (MODE == kForward && !kSmem) ? CP : 1;
+        __shared__ float sh_acc[kSmem ? CP : 1][kQThreads], sh_cmp[kSmem ? CP : 1][kQThreads];
+        float acc[kRegSums], cmp[kRegSums];
         float part[MODE == kForward && kBlocked ? CP : 1];
         float g[MODE == kAdjoint ? CP : 1];
+        auto kahan_into = [&](int c, float v) {  // channel c's Kahan sum += v
+            if (kSmem) kahan_add(sh_acc[kSmem ? c : 0][threadIdx.x], sh_cmp[kSmem ? c : 0][threadIdx.x], v);
+            else kahan_add(acc[kSmem ? 0 : c], cmp[kSmem ? 0 : c], v);
+        };
+        auto kahan_total = [&](int c) -> float {
+            return kSmem ? __fsub_rn(sh_acc[kSmem ? c : 0][threadIdx.x], sh_cmp[kSmem ? c : 0][threadIdx.x])
+                         : __fsub_rn(acc[kSmem ? 0 : c], cmp[kSmem ? 0 : c]);
+        };
         if (MODE == kForward) {
 #pragma unroll
-            for (int c = 0; c < CP; ++c) { acc[c] = 0.f; cmp[c] = 0.f; }
+            for (int c = 0; c < CP; ++c) {
+                if (kSmem) {
+                    sh_acc[kSmem ? c : 0][threadIdx.x] = 0.f;
+                    sh_cmp[kSmem ? c : 0][threadIdx.x] = 0.f;
+                } else {
+                    acc[kSmem ? 0 : c] = 0.f;
+                    cmp[kSmem ? 0 : c] = 0.f;
+                }
+            }
             if (kBlocked) {
 #pragma unroll
                 for (int c = 0; c < CP; ++c) part[c] = 0.f;
@@ -140,7 +163,7 @@ k_query(const QueryArgs a) {
         auto add_term = [&](int c, float v) {
             if (MODE == kForward) {
                 if (kBlocked) part[c] += v;
-                else kahan_add(acc[c], cmp[c], v);
+                else kahan_into(c, v);
             }
         };
         int n_tested = 0, n_far = 0, n_pts = 0;
@@ -350,7 +373,7 @@ k_query(const QueryArgs a) {
                     if (kBlocked) {
 #pragma unroll
                         for (int c = 0; c < CP; ++c) {
-                            kahan_add(acc[c], cmp[c], part[c]);
+                            kahan_into(c, part[c]);
                             part[c] = 0.f;
                         }
                     }
@@ -375,7 +398,7 @@ k_query(const QueryArgs a) {
         }
         if (MODE == kForward && kBlocked) {
 #pragma unroll
-            for (int c = 0; c < CP; ++c) kahan_add(acc[c], cmp[c], part[c]);
+            for (int c = 0; c < CP; ++c) kahan_into(c, part[c]);
         }
 
         if (RANGED && MODE == kForward && a.plan && lane == 0)
@@ -385,7 +408,7 @@ k_query(const QueryArgs a) {
 #pragma unroll
                 for (int c = 0; c < CP; ++c) {
                     if (c >= a.C) continue;
-                    const float v = __fsub_rn(acc[c], cmp[c]) * kInv4Pi;
+                    const float v = kahan_total(c) * kInv4Pi;
                     if (RANGED) atomicAdd(a.out + qo * a.C + c, v);  // the two parts of a packet
                     else a.out[qo * a.C + c] = v;
                 }
@@ -646,6 +669,7 @@ int dispatch(const dipole_tree* t, const QueryArgs& a, cudaStream_t s) {
         DIP_Q_CASE(8)
         DIP_Q_CASE(16)
         DIP_Q_CASE(32)
+        DIP_Q_CASE(36)
         DIP_Q_CASE(64)
         default:
             return dip_fail(-1, "unsupported channel count");

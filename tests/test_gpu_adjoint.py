@@ -34,7 +34,7 @@ def test_sphere_2k():
     assert np.all(normwise(ga, ref) <= TOL), normwise(ga, ref)
 
 
-@pytest.mark.parametrize("C,beta", [(4, 2.0), (1, 1.0), (3, 4.0), (16, 2.0), (33, 2.0)])
+@pytest.mark.parametrize("C,beta", [(4, 2.0), (1, 1.0), (3, 4.0), (16, 2.0), (33, 2.0), (40, 2.0)])
 def test_scene(C, beta):
     w = syn.workload("scene-200k", scale=0.1)
     mu = syn.attributes(w.cloud.n, C, seed=C)

@@ -44,7 +44,7 @@ def test_forward_grad_sphere_2k():
 
 
 @pytest.mark.parametrize("C,beta", [(1, 2.0), (2, 1.0), (3, 2.0), (4, 4.0), (5, 2.0), (8, 2.0),
-                                    (16, 0.5)])
+                                    (16, 0.5), (33, 2.0)])
 def test_forward_grad_channels_and_betas(C, beta):
     w = syn.workload("scene-200k", scale=0.05)
     mu = syn.attributes(w.cloud.n, C, seed=C)
