@@ -663,7 +663,8 @@ def config_rows(torch, dp, dev, stream):
         rows[name] = row
         del P_, N_, A_, E_, X_, MU_, out
 
-    # scene-3m-bf16: float32 and bf16 attribute storage on the same GPU
+    # scene-3m-bf16: float32 and bf16 attribute storage on the same GPU, and bf16
+    # attributes with bf16 node moments (DIPOLE_BF16_MOMENTS)
     w = syn.workload("scene-3m-bf16")
     c = w.cloud
     Q, C = len(w.queries), w.mu.shape[1]
@@ -678,8 +679,9 @@ def config_rows(torch, dp, dev, stream):
     res = {"points": c.n, "queries": Q, "channels": C, "build_ms": b_ms}
     idx = np.random.default_rng(4).choice(Q, 10000, replace=False)
     outs = {}
-    for dt, mu in (("f32", T(w.mu)), ("bf16", T(w.mu).to(torch.bfloat16))):
-        r_ms = timed(lambda: dp.dipole_refit(h, mu), reps=3)
+    for dt, mu, m16 in (("f32", T(w.mu), False), ("bf16", T(w.mu).to(torch.bfloat16), False),
+                        ("bf16_moments", T(w.mu).to(torch.bfloat16), True)):
+        r_ms = timed(lambda: dp.dipole_refit(h, mu, bf16_moments=m16), reps=3)
         dp.dipole_traversal_elapsed("forward")
         dp.dipole_traversal_elapsed("adjoint")
         dp.dipole_traversal_timer(True)
@@ -690,7 +692,7 @@ def config_rows(torch, dp, dev, stream):
                    "forward_kernel_ms": kernel_ms("forward"), "adjoint_kernel_ms": kernel_ms("adjoint"),
                    "refit_forward_adjoint_ms": r_ms + f_ms + a_ms,
                    "queries_per_s": Q / ((r_ms + f_ms + a_ms) * 1e-3)}
-        dp.dipole_refit(h, mu)
+        dp.dipole_refit(h, mu, bf16_moments=m16)
         dp.dipole_forward(h, X_, BETA, out)
         outs[dt] = out[torch.from_numpy(idx).to(dev)].cpu().numpy()
         # the adjoint with the upstream gradient on the sample only
@@ -707,6 +709,10 @@ def config_rows(torch, dp, dev, stream):
                            (b_ms + res["bf16"]["refit_forward_adjoint_ms"]),
         "forward_kernel": res["f32"]["forward_kernel_ms"] / res["bf16"]["forward_kernel_ms"],
         "adjoint_kernel": res["f32"]["adjoint_kernel_ms"] / res["bf16"]["adjoint_kernel_ms"]}
+    res["speedup_bf16_moments_vs_f32"] = {
+        "refit_forward_adjoint": res["f32"]["refit_forward_adjoint_ms"] /
+                                 res["bf16_moments"]["refit_forward_adjoint_ms"],
+        "forward_kernel": res["f32"]["forward_kernel_ms"] / res["bf16_moments"]["forward_kernel_ms"]}
     ot = oracle.Tree(c.points, c.normals, c.areas, c.eps, leaf_size=LEAF)
     g_s = syn.upstream_grad(Q, C, seed=404)[idx].astype(np.float64)
     ot.update(w.mu)
@@ -715,6 +721,8 @@ def config_rows(torch, dp, dev, stream):
     ot.update(_bf16_round(w.mu))
     ref_b = ot.forward(w.queries[idx], BETA)
     aref_b = ot.adjoint(w.queries[idx], BETA, g_s)
+    ot.update(_bf16_round(w.mu), bf16_moments=True)
+    ref_m = ot.forward(w.queries[idx], BETA)
     res["accuracy"] = {
         "queries": 10000,
         "f32_forward_normwise": _normwise(outs["f32"], ref_f).tolist(),
@@ -725,6 +733,11 @@ def config_rows(torch, dp, dev, stream):
         "bf16_adjoint_normwise_vs_bf16_attrs": _normwise(outs["bf16_adj"], aref_b).tolist(),
         "input_rounding_alone_normwise": _normwise(ref_b, ref_f).tolist(),
         "input_rounding_alone_rel_l2": _rel2(ref_b, ref_f).tolist(),
+        "bf16_moments_forward_normwise_vs_f32_attrs": _normwise(outs["bf16_moments"], ref_f).tolist(),
+        "bf16_moments_forward_rel_l2_vs_f32_attrs": _rel2(outs["bf16_moments"], ref_f).tolist(),
+        "bf16_moments_forward_normwise_vs_oracle_bf16_moments":
+            _normwise(outs["bf16_moments"], ref_m).tolist(),
+        "input_and_moment_rounding_alone_normwise": _normwise(ref_m, ref_f).tolist(),
         "gate": "3e-3 max-norm per channel vs the float32 attributes (met where the input "
                 "rounding alone is below it); 1e-4 vs the oracle on the bf16-rounded inputs"}
     rows["scene-3m-bf16"] = res

@@ -51,7 +51,12 @@ typedef enum {
     DIPOLE_ESTATE = -6       /* call out of order (e.g. forward before any refit) */
 } dipole_status;
 
-typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1 } dipole_dtype;
+/* Attribute storage.  DIPOLE_BF16_MOMENTS stores the attributes as bf16 like
+ * DIPOLE_BF16 and adds a bf16 copy of the node moments S_t^c, which the
+ * value forward (dipole_forward and its planned, grid and no-alloc forms)
+ * reads for far nodes; the gradient and adjoint queries keep the float
+ * moments.  Arithmetic is float in every case. */
+typedef enum { DIPOLE_F32 = 0, DIPOLE_BF16 = 1, DIPOLE_BF16_MOMENTS = 2 } dipole_dtype;
 
 /* Radial factor of the kernel.  REGULARIZED is the paper's method:
  * rho(r/eps)/r^3 with rho of eq. regularized_poisson (Sec. 4.1).
@@ -118,12 +123,15 @@ int dipole_build_tree(const float* points, const float* normals, const float* ar
  * iteration; Sec. 6.1, eq. farfield_dipole_features):
  *   S_t^c = A~_t n~_t^c = sum_{m in t} A_m n_m mu_m^c   (3 values per channel)
  *
- *   attrs     [n, channels] float (dtype DIPOLE_F32) or bfloat16 (DIPOLE_BF16)
+ *   attrs     [n, channels] float (dtype DIPOLE_F32) or bfloat16 (DIPOLE_BF16,
+ *             DIPOLE_BF16_MOMENTS)
  *   channels  in [1, 64]
  *
  * The attributes are copied into Morton order in the given dtype (bf16
- * storage halves their bytes; arithmetic is float).  Node sums are float for
- * small nodes and double for nodes of 2^15 or more points.
+ * storage halves their bytes; arithmetic is float).  A leaf's moments are
+ * float sums over its points; a larger node's are exact sums of its leaves'
+ * (64-bit fixed point) rounded once to float.  DIPOLE_BF16_MOMENTS rounds
+ * those floats once more, to bf16 (nearest even), for the value forward.
  * Errors: DIPOLE_EINVAL for a null pointer or a bad channel count/dtype.
  */
 int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t dtype,

@@ -74,6 +74,9 @@ def _load():
         lib.orc_tree_num_nodes.argtypes = [_P]
         lib.orc_tree_export.argtypes = [_P] * 15
         lib.orc_tree_update.argtypes = [_P, _P, _I]
+        lib.orc_round_bf16_n.argtypes = [_I64, _P, _P]
+        lib.orc_tree_round_moments_bf16.argtypes = [_P]
+        lib.orc_bh_forward_bf16.argtypes = [_P, _I64, _P, _F, _P, _P, _P]
         lib.orc_bh_forward.argtypes = [_P, _I64, _P, _F, _P, _P]
         lib.orc_bh_adjoint.argtypes = [_P, _I64, _P, _F, _P, _P]
         lib.orc_brute_forward_grad.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I64, _P, _P]
@@ -127,6 +130,14 @@ def morton(points):
     codes = np.zeros(n, np.uint32)
     _load().orc_morton(n, _ptr(p), _ptr(lo_ext), _ptr(codes))
     return lo_ext[:3].copy(), float(lo_ext[3]), codes
+
+
+def round_bf16(x):
+    """x rounded to float and then to bfloat16, nearest even (reading R13), as float64."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(x)
+    _load().orc_round_bf16_n(x.size, _ptr(x), _ptr(out))
+    return out
 
 
 def brute_forward(points, normals, areas, eps, mu, queries):
@@ -292,10 +303,11 @@ class Tree:
         _load().orc_tree_export(self._h, *[_ptr(o[k]) for k in keys])
         return o
 
-    def update(self, mu, geometry_channels=None):
+    def update(self, mu, geometry_channels=None, bf16_moments=False):
         """Tree update of the node moments, eq. (farfield_dipole_features).  With
         geometry_channels = G < C, channels [G, C) are interpolated without the
-        foreshortening term (reading R12)."""
+        foreshortening term (reading R12).  bf16_moments: the far field of
+        forward() uses the node sums rounded to float, then to bf16 (reading R13)."""
         mu = _f32(mu)
         if mu.ndim == 1:
             mu = mu[:, None]
@@ -307,6 +319,9 @@ class Tree:
         if not 0 <= self.G <= self.C:
             raise ValueError("geometry_channels must be in [0, C]")
         _load().orc_tree_set_geometry_channels(self._h, self.G)
+        self.bf16_moments = bool(bf16_moments)
+        if bf16_moments:
+            _load().orc_tree_round_moments_bf16(self._h)
 
     def _dipole_only(self):
         if getattr(self, "G", self.C) != self.C:
@@ -323,6 +338,20 @@ class Tree:
         cnt = np.zeros((nq, 3), np.int64) if counters else None
         _load().orc_bh_forward(self._h, nq, _ptr(q), float(beta), _ptr(out), _ptr(cnt))
         return (out, cnt) if counters else out
+
+    def forward_bf16_allowance(self, queries, beta):
+        """With bf16 moments (reading R13): the forward [Q, C] and, per query and
+        channel, the bound on what roundings on the edge of a bf16 boundary can
+        change (0 where no far node's sum is that close to one)."""
+        if not getattr(self, "bf16_moments", False):
+            raise RuntimeError("update(..., bf16_moments=True) first")
+        q = _f32(queries)
+        nq = q.shape[0]
+        out = np.zeros((nq, self.C), np.float64)
+        allow = np.zeros((nq, self.C), np.float64)
+        _load().orc_bh_forward_bf16(self._h, nq, _ptr(q), float(beta), _ptr(out), None,
+                                    _ptr(allow))
+        return out, allow
 
     def near_ties(self, queries, beta):
         """Per query, the tested nodes whose double distance is within 1e-6 d of

@@ -77,6 +77,19 @@
  *       m~_t^c = sum_{m in t} A_m mu_m^c / A~_t (the area-weighted mean
  *       attribute, the counterpart of n~_t^c), and stage 2 of the adjoint
  *       gives d mu_m^c = sum_{t in AS(m)} (A_m / A~_t) d m~_t^c.
+ *   R13 bf16 node moments (an option of the storage, not in the paper): the
+ *       far field of PrimalQuery uses the node sums A~_t n~_t^c (and A~_t m~_t^c
+ *       for R12 channels) rounded to float and then to bfloat16, each rounding
+ *       to nearest with ties to even; every other query keeps the double
+ *       moments.  Set by orc_tree_round_moments_bf16 after an update.  Where
+ *       a node sum lies so close to a rounding boundary of bf16 that an
+ *       implementation summing the same values in float (every product and
+ *       partial sum rounded) could round it the other way, both results are
+ *       correct: such a sum S is one whose interval S -+ delta, delta =
+ *       2^-19 sum |A n mu| + 2^-22 |S| over the node's points, holds a
+ *       boundary, and the forward reports per query and channel the largest
+ *       change such choices can make, sum |v_k| (round(S+delta) - round(S-delta))
+ *       over the far nodes' moments (orc_bh_forward_bf16).
  * Compile with -ffp-contract=off: the Morton quantisation, the far test and
  * the radius are specified operation by operation.
  */
@@ -455,6 +468,10 @@ typedef struct orc_tree {
     double* nt;       /* [nn,3C] n~_t^c, eq. (farfield_dipole_features) */
     int G;            /* channels [0, G) with the foreshortening term, [G, C) without (R12) */
     double* mt;       /* [nn,C] m~_t^c = sum A mu / A~ (R12) */
+    double* s16;      /* [nn,3C] A~ n~ rounded to bf16 (R13), or NULL */
+    double* m16;      /* [nn,C] A~ m~ rounded to bf16 (R13), or NULL */
+    double* a16;      /* [nn,3C] width of s16's rounding ambiguity (R13), often 0 */
+    double* am16;     /* [nn,C] the same for m16 */
     double *s_area, *s_ap, *s_ae; /* [nn], [nn,3], [nn] double node sums (R7) */
 } orc_tree;
 
@@ -549,6 +566,7 @@ void orc_tree_free(orc_tree* T) {
     free(T->first); free(T->count); free(T->level); free(T->parent); free(T->skip);
     free(T->is_leaf); free(T->leaf_of); free(T->area); free(T->cen); free(T->epsn);
     free(T->cen32); free(T->r32); free(T->mu); free(T->nt); free(T->mt);
+    free(T->s16); free(T->m16); free(T->a16); free(T->am16);
     free(T->s_area); free(T->s_ap); free(T->s_ae);
     free(T);
 }
@@ -648,6 +666,11 @@ void orc_tree_update(orc_tree* T, const float* mu, int C) {
     free(T->mu);
     free(T->nt);
     free(T->mt);
+    free(T->s16);
+    free(T->m16);
+    free(T->a16);
+    free(T->am16);
+    T->s16 = T->m16 = T->a16 = T->am16 = NULL;
     T->C = C;
     T->G = C;
     T->mu = (double*)malloc(sizeof(double) * n * C);
@@ -673,6 +696,70 @@ void orc_tree_update(orc_tree* T, const float* mu, int C) {
         for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m)
             for (int c = 0; c < C; ++c) mo[c] += (double)T->A[m] * T->mu[m * C + c];
         for (int c = 0; c < C; ++c) mo[c] /= T->area[t];
+    }
+}
+
+/* x rounded to float, then to bfloat16 (the upper 16 bits of the float's
+ * encoding), each to nearest with ties to even (R13).  Infinities and NaNs
+ * pass through. */
+double orc_round_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        /* add just under half of the dropped part's unit, plus its last kept
+         * bit: a tie rounds up only when the kept part is odd */
+        u += 0x7fffu + ((u >> 16) & 1u);
+        u &= 0xffff0000u;
+    }
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+void orc_round_bf16_n(int64_t n, const double* x, double* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_round_bf16(x[i]);
+}
+
+/* R13: the bf16 node moments used by PrimalQuery's far field; call after an
+ * update (the next update drops them). */
+static double ambiguity_bf16(double S, double abs_sum) {
+    const double delta = ldexp(abs_sum, -19) + ldexp(fabs(S), -22);
+    return orc_round_bf16(S + delta) - orc_round_bf16(S - delta);
+}
+
+void orc_tree_round_moments_bf16(orc_tree* T) {
+    int64_t nn = T->nn;
+    int C = T->C;
+    free(T->s16);
+    free(T->m16);
+    free(T->a16);
+    free(T->am16);
+    T->s16 = (double*)malloc(sizeof(double) * nn * 3 * C);
+    T->m16 = (double*)malloc(sizeof(double) * nn * C);
+    T->a16 = (double*)malloc(sizeof(double) * nn * 3 * C);
+    T->am16 = (double*)malloc(sizeof(double) * nn * C);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < nn; ++t) {
+        double* ab = (double*)calloc((size_t)(4 * C), sizeof(double)); /* sums of |terms| */
+        for (int64_t m = T->first[t]; m < (int64_t)T->first[t] + T->count[t]; ++m)
+            for (int c = 0; c < C; ++c) {
+                double v = fabs((double)T->A[m] * T->mu[m * C + c]);
+                ab[3 * c] += v * fabs((double)T->nrm[3 * m]);
+                ab[3 * c + 1] += v * fabs((double)T->nrm[3 * m + 1]);
+                ab[3 * c + 2] += v * fabs((double)T->nrm[3 * m + 2]);
+                ab[3 * C + c] += v;
+            }
+        for (int k = 0; k < 3 * C; ++k) {
+            double S = T->area[t] * T->nt[t * 3 * C + k];
+            T->s16[t * 3 * C + k] = orc_round_bf16(S);
+            T->a16[t * 3 * C + k] = ambiguity_bf16(S, ab[k]);
+        }
+        for (int c = 0; c < C; ++c) {
+            double S = T->area[t] * T->mt[t * C + c];
+            T->m16[t * C + c] = orc_round_bf16(S);
+            T->am16[t * C + c] = ambiguity_bf16(S, ab[3 * C + c]);
+        }
+        free(ab);
     }
 }
 
@@ -720,13 +807,32 @@ typedef struct { int64_t tested, accepted, leafpts; } counters;
 
 /* PrimalQuery(x, node): returns all C channels at once (Sec. 6.3). */
 static void primal_query(const orc_tree* T, const float xf[3], const double x[3], int32_t t,
-                         float beta, double* out, counters* k) {
+                         float beta, double* out, counters* k, double* allow) {
     int C = T->C;
     k->tested++;
     if (far_test(xf, T->cen32 + 3 * t, T->r32[t], beta)) {
         /* GetContribution: A~ rho (p~ - x)/|p~ - x|^3 . n~ / (4 pi) */
         double v[3];
         far_vector(T, t, x, v);
+        if (T->s16) { /* R13: the bf16 sums A~ n~ and A~ m~ */
+            const double* s = T->s16 + (int64_t)t * 3 * C;
+            const double* a = T->a16 + (int64_t)t * 3 * C;
+            for (int c = 0; c < T->G; ++c) {
+                out[c] += v[0] * s[3 * c] + v[1] * s[3 * c + 1] + v[2] * s[3 * c + 2];
+                if (allow)
+                    allow[c] += fabs(v[0]) * a[3 * c] + fabs(v[1]) * a[3 * c + 1] +
+                                fabs(v[2]) * a[3 * c + 2];
+            }
+            if (T->G < C) {
+                double f = far_scalar(T, t, x);
+                for (int c = T->G; c < C; ++c) {
+                    out[c] += f * T->m16[(int64_t)t * C + c];
+                    if (allow) allow[c] += fabs(f) * T->am16[(int64_t)t * C + c];
+                }
+            }
+            k->accepted++;
+            return;
+        }
         const double* nt = T->nt + (int64_t)t * 3 * C;
         for (int c = 0; c < T->G; ++c)
             out[c] += T->area[t] * (v[0] * nt[3 * c] + v[1] * nt[3 * c + 1] + v[2] * nt[3 * c + 2]);
@@ -750,24 +856,34 @@ static void primal_query(const orc_tree* T, const float xf[3], const double x[3]
         return;
     }
     for (int32_t c = t + 1; c < T->skip[t]; c = T->skip[c])
-        primal_query(T, xf, x, c, beta, out, k);
+        primal_query(T, xf, x, c, beta, out, k, allow);
 }
 
 /* out[j*C + c] = Barnes-Hut dipole sum at qry[j]; cnt (may be NULL) receives
  * per query {nodes tested, nodes accepted, leaf points summed}. */
-void orc_bh_forward(const orc_tree* T, int64_t q, const float* qry, float beta, double* out,
-                    int64_t* cnt) {
+/* As orc_bh_forward; with bf16 moments (R13), allow [q, C] (may be NULL)
+ * receives the bound on the change that the ambiguous roundings can make. */
+void orc_bh_forward_bf16(const orc_tree* T, int64_t q, const float* qry, float beta, double* out,
+                         int64_t* cnt, double* allow) {
     int C = T->C;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t j = 0; j < q; ++j) {
         float xf[3] = {qry[3 * j], qry[3 * j + 1], qry[3 * j + 2]};
         double x[3] = {xf[0], xf[1], xf[2]};
         double* o = out + j * C;
+        double* al = allow ? allow + j * C : NULL;
         for (int c = 0; c < C; ++c) o[c] = 0.0;
+        if (al)
+            for (int c = 0; c < C; ++c) al[c] = 0.0;
         counters k = {0, 0, 0};
-        primal_query(T, xf, x, 0, beta, o, &k);
+        primal_query(T, xf, x, 0, beta, o, &k, al);
         if (cnt) { cnt[3 * j] = k.tested; cnt[3 * j + 1] = k.accepted; cnt[3 * j + 2] = k.leafpts; }
     }
+}
+
+void orc_bh_forward(const orc_tree* T, int64_t q, const float* qry, float beta, double* out,
+                    int64_t* cnt) {
+    orc_bh_forward_bf16(T, q, qry, beta, out, cnt, NULL);
 }
 
 /* Near ties of the far test (R6): the walk of PrimalQuery, counting the

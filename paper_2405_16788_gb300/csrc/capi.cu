@@ -206,8 +206,9 @@ int dipole_refit(dipole_tree* tree, const void* attrs, int32_t channels, int32_t
     if (int rc_dev = check_device(tree, "dipole_refit")) return rc_dev;
     if (channels < 1 || channels > dip::kMaxChannels)
         return dip_fail(DIPOLE_EINVAL, "dipole_refit: channels must be in [1, 64]");
-    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
-        return dip_fail(DIPOLE_EINVAL, "dipole_refit: dtype must be DIPOLE_F32 or DIPOLE_BF16");
+    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16 && dtype != DIPOLE_BF16_MOMENTS)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit: dtype must be DIPOLE_F32, DIPOLE_BF16 or "
+                                       "DIPOLE_BF16_MOMENTS");
     return dip::refit(tree, attrs, channels, dtype, channels, as_stream(stream));
 }
 
@@ -221,8 +222,9 @@ int dipole_refit_appearance(dipole_tree* tree, const void* attrs, int32_t channe
     if (geometry_channels < 0 || geometry_channels > channels)
         return dip_fail(DIPOLE_EINVAL,
                         "dipole_refit_appearance: geometry_channels must be in [0, channels]");
-    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16)
-        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: dtype must be DIPOLE_F32 or DIPOLE_BF16");
+    if (dtype != DIPOLE_F32 && dtype != DIPOLE_BF16 && dtype != DIPOLE_BF16_MOMENTS)
+        return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: dtype must be DIPOLE_F32, "
+                                       "DIPOLE_BF16 or DIPOLE_BF16_MOMENTS");
     if (geometry_channels < channels && tree->kernel != DIPOLE_KERNEL_REGULARIZED)
         return dip_fail(DIPOLE_EINVAL, "dipole_refit_appearance: channels without the "
                                        "foreshortening term need the regularized kernel");
@@ -574,7 +576,7 @@ int dipole_tree_info_get(const dipole_tree* tree, dipole_tree_info* info) {
     info->n_points = tree->n;
     info->n_nodes = tree->nn;
     info->channels = tree->C;
-    info->dtype = tree->dtype;
+    info->dtype = tree->S16 ? DIPOLE_BF16_MOMENTS : tree->dtype;
     info->leaf_size = tree->leaf_size;
     info->max_depth = tree->max_depth;
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = tree->bbox_host[a];

@@ -8,6 +8,9 @@ namespace dip {
 
 // Floats per node moment row: 3 per channel, padded to whole float4s.
 __host__ __device__ constexpr int srow(int cp) { return (3 * cp + 3) & ~3; }
+// bf16 values per row of the bf16 moment copy: 3 per channel, padded to whole
+// 16-byte vectors.
+__host__ __device__ constexpr int srow16(int cp) { return (3 * cp + 7) & ~7; }
 
 // rho(t) = erf(t) - (2t/sqrt(pi)) exp(-t^2)  (Sec. 4.1, eq. regularized_poisson).
 // Above kTCut, 1 - rho < 1e-8 and rho rounds to 1 in float.  Below kTSeries

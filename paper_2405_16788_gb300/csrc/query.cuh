@@ -34,6 +34,7 @@ struct QueryArgs {
     int Cp;
     const void* mu;
     const float* S;
+    const uint16_t* S16;  // S rounded to bf16, [nn, srow16(Cp)] (bf16 attributes), or NULL
     float* out;         // D [q, C]
     float* gout;        // grad D [q, C, 3]
     const float* g;     // dL/dD [q, C]

@@ -439,6 +439,32 @@ __global__ void __launch_bounds__(128) k_refit_internal(
     }
 }
 
+// The bf16 copy of the moments (DIPOLE_BF16_MOMENTS): every value rounded to
+// nearest even, padding columns 0.  Four values per thread, so that a warp
+// reads and writes consecutive 16- and 8-byte pieces of the rows.
+template <int CP>
+__global__ void __launch_bounds__(256) k_moments_bf16(int64_t nn, const float* __restrict__ S,
+                                                      uint16_t* __restrict__ S16) {
+    constexpr int SR = srow(CP), SR16 = srow16(CP), NC = 3 * CP, QR = SR16 / 4;
+    const int64_t total = nn * QR;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / QR;
+        const int j = 4 * (int)(i - t * QR);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < SR) v = __ldg(reinterpret_cast<const float4*>(S + t * SR + j));
+        const float f[4] = {v.x, v.y, v.z, v.w};
+        unsigned short h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            h[k] = j + k < NC ? __bfloat16_as_ushort(__float2bfloat16_rn(f[k])) : (unsigned short)0;
+        uint2 out;
+        out.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
+        out.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
+        *reinterpret_cast<uint2*>(S16 + t * SR16 + j) = out;
+    }
+}
+
 // Stage 2 (eq. farfield_features_gradient): for each leaf, D^c = sum of dS^c
 // over the leaf and its ancestors; each point of the leaf gets
 // (A_m n_m) . D^c plus its opened-leaf term, written in the caller's order.
@@ -585,6 +611,13 @@ void launch_refit(dipole_tree* t, const void* attrs, cudaStream_t s) {
     note_launch();
     k_refit_internal<CP><<<grid, 128, 0, s>>>(t->nn, ldP, t->is_leaf, t->skip, t->fix_kexp,
                                               t->fix_P, t->S);
+    if (t->S16) {
+        const int64_t total = t->nn * (srow16(CP) / 4);
+        const int64_t mblocks = (total + 255) / 256, mcap = (int64_t)num_sms() * 8;
+        note_launch();
+        k_moments_bf16<CP><<<(unsigned)(mblocks < mcap ? mblocks : mcap), 256, 0, s>>>(t->nn, t->S,
+                                                                                     t->S16);
+    }
 }
 
 template <int CP>
@@ -613,6 +646,8 @@ int padded_channels(int C) {
 int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream_t s) {
     const int Cp = padded_channels(C);
     const int SR = srow(Cp);
+    const bool m16 = dtype == 2;  // bf16 attributes and a bf16 copy of the moments
+    const int adt = m16 ? 1 : dtype;
     if (t->attr_Cp_alloc != Cp || t->attr_dtype_alloc != dtype) {
         // (re)allocate the attribute state in one block; the previous one is freed in stream order
         if (t->attr_block) cudaFreeAsync(t->attr_block, s);
@@ -621,9 +656,11 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream
         const int64_t ntiles = (t->nn + kRefitTile - 1) / kRefitTile;
         auto take = [&](Carve& c) {
             unsigned char* mu = nullptr;
-            c.take(&mu, (dtype == 1 ? 2 : 4) * t->n * Cp);
+            c.take(&mu, (adt == 1 ? 2 : 4) * t->n * Cp);
             t->mu = mu;
             c.take(&t->S, t->nn * SR);
+            if (m16) c.take(&t->S16, t->nn * srow16(Cp));
+            else t->S16 = nullptr;
             c.take(&t->dS, t->nn * SR);
             c.take(&t->dmu, t->n * Cp);
             c.take(&t->fix_P, fix_ld(t->nn) * NC);
@@ -645,10 +682,10 @@ int refit(dipole_tree* t, const void* attrs, int C, int dtype, int G, cudaStream
     t->C = C;
     t->G = G;
     t->Cp = Cp;
-    t->dtype = dtype;
+    t->dtype = adt;
 #define DIP_REFIT_CASE(K)                                                          \
     case K:                                                                        \
-        if (dtype == 1) launch_refit<K, __nv_bfloat16>(t, attrs, s);               \
+        if (adt == 1) launch_refit<K, __nv_bfloat16>(t, attrs, s);                 \
         else launch_refit<K, float>(t, attrs, s);                                  \
         break;
     switch (Cp) {

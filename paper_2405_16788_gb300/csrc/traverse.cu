@@ -16,6 +16,7 @@
 // same step, so their contributions to dS_t are summed inside the warp before
 // one set of atomics; the same holds for the points of an opened leaf.
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -47,13 +48,24 @@ __device__ __forceinline__ void prefetch_l1(const void* p, int bytes, int lane) 
 // kernel with channels [a.G, C) interpolated without the foreshortening term
 // (a point adds A rho(r/eps)/(4 pi r^2) mu, a far node rho(d/eps~)/(4 pi d^2)
 // M with M = sum A mu in the first slot of the channel's moment row).
-template <int CP, typename AT, int MODE, int KERN, bool RANGED>
+// Value v (0..23) of a group of 24 bf16 values held in three 16-byte vectors,
+// as a float (v is a compile-time index after unrolling).
+__device__ __forceinline__ float bf16_in_group(const uint4* g, int v) {
+    const uint4 q = g[v >> 3];
+    const int w = (v >> 1) & 3;
+    const unsigned u = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+    return __uint_as_float((v & 1) ? (u & 0xffff0000u) : (u << 16));
+}
+
+template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6
                                           : (MODE == kForward && CP <= 32) ? 3 : (MODE == kForward && CP <= 36) ? 2 : 1)
 k_query(const QueryArgs a) {
     constexpr bool NF = KERN == 2;       // some channels skip the foreshortening term
     constexpr int KR = NF ? 0 : KERN;    // the radial factor's kernel
     constexpr int SR = srow(CP);
+    constexpr int SR16 = srow16(CP);
+    constexpr bool kS16 = MODE == kForward && M16;  // far-node moments from the bf16 copy
     constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -188,6 +200,15 @@ k_query(const QueryArgs a) {
             }
         }
         unsigned steps = 0;
+        // bf16 moments (bf16 attributes, forward): a row is read in groups of up
+        // to 8 channels, 24 bf16 values in three 16-byte loads
+        auto load_group16 = [&](unsigned node, int c0, uint4* gp) {
+            const uint4* p = reinterpret_cast<const uint4*>(a.S16 + (size_t)node * SR16 + 3 * c0);
+            const int nv = 3 * ((CP - c0) < 8 ? (CP - c0) : 8);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (8 * j < nv) gp[j] = __ldg(p + j);
+        };
         // one warp step of the walk; false once the walk is over
         auto walk_step = [&](const bool fold_here) -> bool {
             const unsigned n = __reduce_min_sync(FULL, next);
@@ -204,8 +225,11 @@ k_query(const QueryArgs a) {
             // forward: the node's first moment chunk is loaded before the far test
             // so that its latency overlaps the test (most visited nodes are far
             // for some lane)
-            float4 s_first[MODE == kForward ? (3 * CH + 3) / 4 : 1];
-            if (MODE == kForward) {
+            float4 s_first[MODE == kForward && !kS16 ? (3 * CH + 3) / 4 : 1];
+            uint4 grp[kS16 ? 3 : 1];  // bf16 moments: the row's current group of 8 channels
+            if (MODE == kForward && kS16) {
+                load_group16(n, 0, grp);
+            } else if (MODE == kForward) {
                 const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR);
 #pragma unroll
                 for (int j = 0; j < (3 * CH + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
@@ -247,10 +271,16 @@ k_query(const QueryArgs a) {
 #pragma unroll
                         for (int c0 = 0; c0 < CP; c0 += CH) {
                             float s[3 * CH + 3];
+                            if (kS16) {
+                                if (c0 > 0 && c0 % 8 == 0) load_group16(n, c0, grp);
 #pragma unroll
-                            for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
-                                const float4 q4 = c0 == 0 ? s_first[j] : __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
-                                s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
+                                for (int j = 0; j < 3 * CH; ++j) s[j] = bf16_in_group(grp, 3 * (c0 % 8) + j);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < (3 * CH + 3) / 4; ++j) {
+                                    const float4 q4 = c0 == 0 ? s_first[j] : __ldg(reinterpret_cast<const float4*>(Sr + 3 * c0) + j);
+                                    s[4 * j] = q4.x; s[4 * j + 1] = q4.y; s[4 * j + 2] = q4.z; s[4 * j + 3] = q4.w;
+                                }
                             }
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
@@ -624,15 +654,27 @@ void order_place(const uint32_t* ibucket, int64_t ni, uint32_t* ostate, uint32_t
 // Packets below this count are too few for the queue's tail to matter.
 constexpr int64_t kOrderMinPackets = 2048;
 
-template <int CP, typename AT, int MODE, int KERN, bool RANGED>
-void launch_query_k(const QueryArgs& a, cudaStream_t s) {
+template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16>
+void launch_query_m(const QueryArgs& a, cudaStream_t s) {
     static int per_sm = 0;
-    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN, RANGED>, a.nq, per_sm);
-    note_launch(); k_query<CP, AT, MODE, KERN, RANGED><<<grid, kQThreads, 0, s>>>(a);
+    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN, RANGED, M16>, a.nq, per_sm);
+    note_launch(); k_query<CP, AT, MODE, KERN, RANGED, M16><<<grid, kQThreads, 0, s>>>(a);
 }
 
-// The kernel choice and ranged items are template parameters: runtime
-// branches cost the plain kernels registers.
+// bf16 node moments (a.S16) only in the forward with bf16 attributes
+template <int CP, typename AT, int MODE, int KERN, bool RANGED>
+void launch_query_k(const QueryArgs& a, cudaStream_t s) {
+    if constexpr (MODE == kForward && std::is_same<AT, __nv_bfloat16>::value) {
+        if (a.S16) {
+            launch_query_m<CP, AT, MODE, KERN, RANGED, true>(a, s);
+            return;
+        }
+    }
+    launch_query_m<CP, AT, MODE, KERN, RANGED, false>(a, s);
+}
+
+// The kernel choice, ranged items and the moment type are template
+// parameters: runtime branches cost the plain kernels registers.
 template <int CP, typename AT, int MODE>
 void launch_query(const QueryArgs& a, cudaStream_t s) {
     // kernel 2: the regularized kernel with channels that skip the foreshortening term
@@ -805,6 +847,7 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.Cp = t->Cp;
     a.mu = t->mu;
     a.S = t->S;
+    a.S16 = t->S16;
     a.out = out;
     a.gout = nullptr;
     a.g = nullptr;
@@ -948,6 +991,7 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.Cp = t->Cp;
         a.mu = t->mu;
         a.S = t->S;
+        a.S16 = t->S16;
         a.out = call.out;
         a.gout = call.gout;
         a.g = call.g;

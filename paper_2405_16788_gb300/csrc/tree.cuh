@@ -49,9 +49,10 @@ struct dipole_tree {
     int C = 0;
     int G = 0;                   // channels [0, G) with the foreshortening term, [G, C) without
     int Cp = 0;
-    int dtype = 0;
+    int dtype = 0;               // attribute storage: 0 float, 1 bf16
     void* mu = nullptr;          // [n, Cp] float or bf16, Morton order
     float* S = nullptr;          // [nn, 3 Cp]
+    uint16_t* S16 = nullptr;     // [nn, srow16(Cp)] S rounded to bf16 (DIPOLE_BF16_MOMENTS), or NULL
     // refit scratch: fixed-point prefix of the leaf moments over preorder
     long long* fix_P = nullptr;     // [3 Cp, nn + 1 rounded up to 4], column-major
     long long* fix_tsum = nullptr;  // [tiles, 3 Cp] tile sums, then tile offsets

@@ -29,6 +29,7 @@ DIPOLE_ETRAVERSAL = -5
 DIPOLE_ESTATE = -6
 DIPOLE_F32 = 0
 DIPOLE_BF16 = 1
+DIPOLE_BF16_MOMENTS = 2
 
 EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoint",
             "dipole_query_counts", "dipole_sync_status", "dipole_tree_info_get",
@@ -204,25 +205,35 @@ def dipole_build_tree(points, normals, areas, radii=None, leaf_size=8, max_depth
     return h.value
 
 
-def dipole_refit(tree: int, attrs: torch.Tensor, stream=None):
-    if attrs.dim() == 1:
-        attrs = attrs[:, None]
+def _attr_dtype(attrs: torch.Tensor, bf16_moments: bool) -> int:
     dt = {torch.float32: DIPOLE_F32, torch.bfloat16: DIPOLE_BF16}.get(attrs.dtype)
     if dt is None:
         raise TypeError("attrs must be float32 or bfloat16")
+    if bf16_moments:
+        if dt != DIPOLE_BF16:
+            raise TypeError("bf16_moments needs bfloat16 attrs")
+        dt = DIPOLE_BF16_MOMENTS
+    return dt
+
+
+def dipole_refit(tree: int, attrs: torch.Tensor, stream=None, bf16_moments: bool = False):
+    """Tree update; bf16_moments (bfloat16 attrs only): the value forward reads
+    a bf16 copy of the node moments (DIPOLE_BF16_MOMENTS)."""
+    if attrs.dim() == 1:
+        attrs = attrs[:, None]
+    dt = _attr_dtype(attrs, bf16_moments)
     p = _dev(attrs, "attrs", dtype=None)
     _check(load_library().dipole_refit(ctypes.c_void_p(tree), p, int(attrs.shape[1]), dt,
                                        _stream(stream)))
 
 
-def dipole_refit_appearance(tree: int, attrs: torch.Tensor, geometry_channels: int, stream=None):
+def dipole_refit_appearance(tree: int, attrs: torch.Tensor, geometry_channels: int, stream=None,
+                            bf16_moments: bool = False):
     """Refit with channels [geometry_channels, C) interpolated without the
     foreshortening term (the paper's appearance attributes)."""
     if attrs.dim() == 1:
         attrs = attrs[:, None]
-    dt = {torch.float32: DIPOLE_F32, torch.bfloat16: DIPOLE_BF16}.get(attrs.dtype)
-    if dt is None:
-        raise TypeError("attrs must be float32 or bfloat16")
+    dt = _attr_dtype(attrs, bf16_moments)
     p = _dev(attrs, "attrs", dtype=None)
     _check(load_library().dipole_refit_appearance(ctypes.c_void_p(tree), p, int(attrs.shape[1]),
                                                   dt, int(geometry_channels), _stream(stream)))
@@ -523,18 +534,20 @@ class DipoleTree:
     def info(self) -> dict:
         return dipole_tree_info_get(self.handle)
 
-    def refit(self, attrs: torch.Tensor, stream=None, geometry_channels: int | None = None):
+    def refit(self, attrs: torch.Tensor, stream=None, geometry_channels: int | None = None,
+              bf16_moments: bool = False):
         """Tree update (eq. farfield_dipole_features).  geometry_channels = G < C:
-        channels [G, C) skip the foreshortening term (appearance attributes)."""
+        channels [G, C) skip the foreshortening term (appearance attributes).
+        bf16_moments (bfloat16 attrs): the value forward reads bf16 node moments."""
         if attrs.dim() == 1:
             attrs = attrs[:, None]
         if attrs.shape[0] != self.n:
             raise ValueError("attrs must have one row per point")
         attrs = attrs.contiguous()
         if geometry_channels is None:
-            dipole_refit(self.handle, attrs, stream)
+            dipole_refit(self.handle, attrs, stream, bf16_moments)
         else:
-            dipole_refit_appearance(self.handle, attrs, geometry_channels, stream)
+            dipole_refit_appearance(self.handle, attrs, geometry_channels, stream, bf16_moments)
         self.C = int(attrs.shape[1])
         self._attrs = attrs
 

@@ -36,6 +36,17 @@ def normwise(y, ref):
     return np.max(np.abs(y - ref), axis=0) / den
 
 
+def excess_over_allowance(y, ref, allow):
+    """Per channel: the largest max_q (|y - ref| - allow) / max_q |ref|, the
+    norm-wise error once each element may differ by its allowance (the bf16
+    roundings that both implementations may take either way)."""
+    y = np.asarray(y, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.max(np.abs(ref), axis=0)
+    den = np.where(den > 0, den, 1.0)
+    return np.max(np.abs(y - ref) - allow, axis=0) / den
+
+
 def bf16_round(a):
     """Round float32 to bfloat16 (nearest even) and back, in numpy."""
     a = np.ascontiguousarray(a, np.float32)

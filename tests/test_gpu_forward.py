@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2405_16788_gb300 import synthetic as syn
-from _helpers import bf16_round, gpu_tree, normwise, oracle_tree, to_dev
+from _helpers import bf16_round, excess_over_allowance, gpu_tree, normwise, oracle_tree, to_dev
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -167,6 +167,42 @@ def test_bf16_attributes():
     ot.update(mu)
     ref = ot.forward(q, 2.0)
     _bf16_gate(normwise(y, ref), normwise(ref_b, ref))
+
+
+@pytest.mark.parametrize("C,G", [(1, 1), (2, 2), (4, 4), (16, 16), (33, 33), (6, 2), (33, 1)])
+def test_bf16_moments(C, G):
+    """DIPOLE_BF16_MOMENTS: the value forward reads the node moments rounded to
+    bf16.  Against the oracle with the same rounding (reading R13) on the same
+    bf16-rounded attributes: 1e-4 per channel, plain and planned (ranged)
+    walks, decisions unchanged; an element may differ in addition by the
+    oracle's allowance for sums on the edge of a bf16 rounding boundary (the
+    GPU sums a leaf in float, the oracle in double); against the float32 attributes and double
+    moments the 3e-3 gate of the bf16 path, as in test_bf16_attributes."""
+    import torch
+    from paper_2405_16788_gb300 import dipole
+    w = syn.workload("scene-200k", scale=0.1)
+    mu = syn.attributes(w.cloud.n, C, seed=30 + C)
+    gt = gpu_tree(w.cloud)
+    gt.refit(to_dev(mu).to(torch.bfloat16), bf16_moments=True,
+             geometry_channels=None if G == C else G)
+    assert dipole.dipole_tree_info_get(gt.handle)["dtype"] == dipole.DIPOLE_BF16_MOMENTS
+    q = w.queries[:20000]
+    X = to_dev(q)
+    y = gt.forward(X, 2.0).cpu().numpy()
+    plan = dipole.QueryPlan(len(q), X.device)
+    yp = gt.forward(X, 2.0, plan=plan).cpu().numpy()
+    cnt = gt.query_counts(X, 2.0).cpu().numpy()
+    gt.sync_status()
+    ot = oracle_tree(w.cloud)
+    ot.update(bf16_round(mu), geometry_channels=G, bf16_moments=True)
+    ref_m, allow = ot.forward_bf16_allowance(q, 2.0)
+    _, rc = ot.forward(q, 2.0, counters=True)
+    assert np.all(excess_over_allowance(y, ref_m, allow) <= TOL)
+    assert np.all(excess_over_allowance(yp, ref_m, allow) <= TOL)
+    assert np.array_equal(cnt.astype(np.int64), rc)
+    ot.update(mu, geometry_channels=G)
+    ref = ot.forward(q, 2.0)
+    _bf16_gate(normwise(y, ref), normwise(ref_m, ref))
 
 
 def _bf16_gate(err, quant, gate=3e-3):
