@@ -48,7 +48,10 @@ typedef enum {
     DIPOLE_ECUDA = -3,       /* a CUDA call failed; see dipole_last_error() */
     DIPOLE_ENONFINITE = -4,  /* a non-finite input was found */
     DIPOLE_ETRAVERSAL = -5,  /* a traversal exceeded its step bound (corrupt tree) */
-    DIPOLE_ESTATE = -6       /* call out of order (e.g. forward before any refit) */
+    DIPOLE_ESTATE = -6,      /* call out of order (e.g. forward before any refit) */
+    DIPOLE_EBOUNDS = -7      /* checked build only (compiled with -DDIPOLE_CHECKED): a
+                                traversal met an index outside its array and skipped the
+                                access; the outputs of that call are incomplete */
 } dipole_status;
 
 /* Attribute storage.  DIPOLE_BF16_MOMENTS stores the attributes as bf16 like
@@ -507,6 +510,14 @@ uint64_t dipole_kernel_launches(void);
  * (or a test) check that a call allocates nothing.  The paper has no
  * counterpart. */
 uint64_t dipole_device_allocations(void);
+
+/*
+ * 1 in the checked build of the library (compiled with -DDIPOLE_CHECKED: the
+ * traversals test every index they read from an array before using it and
+ * report DIPOLE_EBOUNDS), 0 in the normal build.  A testing aid with no
+ * counterpart in the paper.
+ */
+int dipole_checked_build(void);
 
 /* Query modes of the traversal timer below. */
 typedef enum {

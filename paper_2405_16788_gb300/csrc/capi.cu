@@ -53,6 +53,7 @@ int check_device(const dipole_tree* t, const char* fn) {
 }
 
 int status_to_code(int st) {
+    if (st & dip::kStatusBounds) return DIPOLE_EBOUNDS;
     if (st & dip::kStatusTraversal) return DIPOLE_ETRAVERSAL;
     if (st & dip::kStatusNonFinite) return DIPOLE_ENONFINITE;
     return DIPOLE_OK;
@@ -86,6 +87,8 @@ const char* dipole_last_error(void) { return g_last_error.c_str(); }
 uint64_t dipole_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 uint64_t dipole_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
+
+int dipole_checked_build(void) { return dip::kChecked ? 1 : 0; }
 
 int dipole_traversal_timer(int32_t enable) {
     if (enable != 0 && enable != 1)
@@ -565,6 +568,8 @@ int dipole_sync_status(dipole_tree* tree, void* stream) {
     DIP_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
     DIP_CUDA_TRY(cudaGetLastError());
     int code = status_to_code(st);
+    if (code == DIPOLE_EBOUNDS)
+        return dip_fail(code, "an index outside its array was caught and skipped (checked build)");
     if (code == DIPOLE_ETRAVERSAL)
         return dip_fail(code, "a traversal exceeded its step bound (corrupt tree)");
     if (code == DIPOLE_ENONFINITE) return dip_fail(code, "a non-finite query point was seen");

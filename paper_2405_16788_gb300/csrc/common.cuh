@@ -24,6 +24,26 @@ constexpr int kStatusTraversal = 1;
 constexpr int kStatusNonFinite = 2;
 constexpr int kStatusBadArea = 4;
 constexpr int kStatusBadRadius = 8;
+constexpr int kStatusBounds = 16;
+
+// The checked build (nvcc -DDIPOLE_CHECKED, a separate library) tests the
+// indexes that the traversals read from arrays (work items and their order,
+// the query permutation, parents, a leaf's point range) before using them: one
+// outside its array sets kStatusBounds and the access is skipped, so the call
+// returns DIPOLE_EBOUNDS instead of reading or writing out of bounds.  In the
+// normal build the tests compile to nothing.
+#ifdef DIPOLE_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool in_bounds(bool ok, int* status) {
+    if (kChecked && !ok) {
+        atomicOr(status, kStatusBounds);
+        return false;
+    }
+    return true;
+}
 
 // One octree node, 32 bytes = one L2 sector, read by every visiting warp.
 //   geo  = {p~.x, p~.y, p~.z, r~}            (Sec. 6.1, eq. farfield_dipole)

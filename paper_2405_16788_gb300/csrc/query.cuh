@@ -48,6 +48,8 @@ struct QueryArgs {
     int32_t* counts;
     int32_t* ucounts;   // [packets, 4] warp steps, far steps, opened-leaf point loads, lanes (kCount)
     unsigned long long* work;
+    int64_t npts;            // points of the tree (leaf point ranges lie in [0, npts))
+    int64_t n_slots;         // entries of items (ranged work)
     const uint32_t* porder;  // packet (or item) order, or NULL for sorted order
     GridSpec grid;           // dense-grid queries instead of q / qperm
     uint32_t* plan;          // query plan being written (forward): kPlanWords per packet

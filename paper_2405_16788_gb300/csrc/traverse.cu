@@ -82,14 +82,18 @@ k_query(const QueryArgs a) {
         unsigned half = 0u;  // forward item: 0 lower, 1 upper part of the walk
         if (RANGED) {
             if (pk >= *a.n_items) break;
-            const uint4 it = a.items[a.porder ? a.porder[pk] : pk];
+            const uint64_t slot = a.porder ? a.porder[pk] : pk;
+            if (!in_bounds(slot < (uint64_t)a.n_slots, a.status)) continue;
+            const uint4 it = a.items[slot];
             pm = (int64_t)it.x;
             lo = it.y;
             hi = it.z;
             half = it.w;
+            if (!in_bounds(lo <= hi && hi <= nn && pm * 32 < a.nq, a.status)) continue;
         } else {
             if ((int64_t)pk * 32 >= a.nq) break;
             pm = (int64_t)(a.porder ? a.porder[pk] : pk);  // packet index in sorted order
+            if (!in_bounds(pm * 32 < a.nq, a.status)) continue;
         }
         bool valid;
         int64_t qo;
@@ -111,6 +115,10 @@ k_query(const QueryArgs a) {
             const int64_t qi = pm * 32 + lane;
             valid = qi < a.nq;
             qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+            if (valid && !in_bounds(qo >= 0 && qo < a.nq, a.status)) {
+                valid = false;
+                qo = 0;
+            }
             if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
         }
 
@@ -188,6 +196,7 @@ k_query(const QueryArgs a) {
             const unsigned start = next;
             int32_t u = a.parent[lo];
             for (int up = 0; up <= kMaxLevel + 1 && u >= 0; ++up) {
+                if (!in_bounds(u < (int32_t)nn, a.status)) break;
                 const float4 geo = __ldg(&nodes[u].geo);
                 const int4 meta = __ldg(&nodes[u].meta);
                 const float dx = __fsub_rn(x0, geo.x);
@@ -342,7 +351,9 @@ k_query(const QueryArgs a) {
                 if (MODE == kAdjoint && NF && __any_sync(FULL, open_leaf)) {
                     // opened leaf, one point at a time: each channel takes the
                     // kernel of its kind
-                    const int f = meta.y, cnt = meta.z;
+                    const int f = meta.y;
+                    const int cnt =
+                        in_bounds(f >= 0 && meta.z >= 0 && (int64_t)f + meta.z <= a.npts, a.status) ? meta.z : 0;
                     for (int j = 0; j < cnt; ++j) {
                         float kn;
                         const float kd = point_k2(pts[f + j], kn);
@@ -357,7 +368,9 @@ k_query(const QueryArgs a) {
                     }
                 } else if (MODE == kAdjoint && __any_sync(FULL, open_leaf)) {
                     // opened leaf, points in pairs (adjoint_point_pair_reduce)
-                    const int f = meta.y, cnt = meta.z;
+                    const int f = meta.y;
+                    const int cnt =
+                        in_bounds(f >= 0 && meta.z >= 0 && (int64_t)f + meta.z <= a.npts, a.status) ? meta.z : 0;
                     for (int j = 0; j < cnt; j += 2) {
                         const bool two = j + 1 < cnt;
                         const float ka = point_k(pts[f + j]);
@@ -370,7 +383,9 @@ k_query(const QueryArgs a) {
                     }
                 } else if (MODE != kAdjoint && __any_sync(FULL, open_leaf)) {
                     // opened leaf: exact sum over its points (eq. dipole_sum)
-                    const int f = meta.y, cnt = meta.z;
+                    const int f = meta.y;
+                    const int cnt =
+                        in_bounds(f >= 0 && meta.z >= 0 && (int64_t)f + meta.z <= a.npts, a.status) ? meta.z : 0;
                     if (MODE == kForward) {
                         prefetch_l1(pts + f, cnt * (int)sizeof(PointRec), lane);
                         prefetch_l1(reinterpret_cast<const AT*>(a.mu) + (size_t)f * CP,
@@ -861,6 +876,8 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.counts = nullptr;
     a.ucounts = nullptr;
     a.work = work;
+    a.npts = t->n;
+    a.n_slots = 0;
     a.porder = nullptr;  // packets in sorted order
     a.plan = nullptr;
     a.items = nullptr;
@@ -1005,6 +1022,8 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.counts = call.counts;
         a.ucounts = call.ucounts;
         a.work = work;
+        a.npts = t->n;
+        a.n_slots = ni;
         a.porder = porder;
         a.plan = plan_w;
         a.items = items;

@@ -184,18 +184,26 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
         unsigned lo = 0u, hi = nn, half = 0u;
         if (RANGED) {
             if (pk >= *a.n_items) break;
-            const uint4 it = a.items[a.porder ? a.porder[pk] : pk];
+            const uint64_t slot = a.porder ? a.porder[pk] : pk;
+            if (!in_bounds(slot < (uint64_t)a.n_slots, a.status)) continue;
+            const uint4 it = a.items[slot];
             pm = (int64_t)it.x;
             lo = it.y;
             hi = it.z;
             half = it.w;
+            if (!in_bounds(lo <= hi && hi <= nn && pm * 32 < a.nq, a.status)) continue;
         } else {
             if ((int64_t)pk * 32 >= a.nq) break;
             pm = (int64_t)(a.porder ? a.porder[pk] : pk);
+            if (!in_bounds(pm * 32 < a.nq, a.status)) continue;
         }
         const int64_t qi = pm * 32 + lane;
-        const bool valid = qi < a.nq;
-        const int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+        bool valid = qi < a.nq;
+        int64_t qo = valid ? (a.qperm ? (int64_t)a.qperm[qi] : qi) : 0;
+        if (valid && !in_bounds(qo >= 0 && qo < a.nq, a.status)) {
+            valid = false;
+            qo = 0;
+        }
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
         if (valid) { x0 = a.q[3 * qo]; x1 = a.q[3 * qo + 1]; x2 = a.q[3 * qo + 2]; }
         int ord[CG];
@@ -258,6 +266,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                 const unsigned start = next;
                 int32_t u = a.parent[lo];
                 for (int up = 0; up <= kMaxLevel + 1 && u >= 0; ++up) {
+                    if (!in_bounds(u < (int32_t)nn, a.status)) break;
                     const float4 geo = __ldg(&nodes[u].geo);
                     const int4 meta = __ldg(&nodes[u].meta);
                     const float dx = __fsub_rn(x0, geo.x);
@@ -367,7 +376,9 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
 
                 if (__any_sync(FULL, open_leaf)) {
                     // opened leaf: exact terms of its points (eq. dipole_sum)
-                    const int f = meta.y, cnt = meta.z;
+                    const int f = meta.y;
+                    const int cnt =
+                        in_bounds(f >= 0 && meta.z >= 0 && (int64_t)f + meta.z <= a.npts, a.status) ? meta.z : 0;
                     for (int j = 0; j < cnt; ++j) {
                         const PointRec pr = pts[f + j];
                         float fa = 0.f, fb = 0.f, wu = 0.f, pae = 0.f, pbe = 0.f;

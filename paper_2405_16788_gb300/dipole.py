@@ -18,7 +18,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdipole.so")
+# DIPOLE_LIBRARY selects another build of the library (the checked build,
+# libdipole_checked.so); by default the one next to this file.
+LIB_PATH = os.environ.get("DIPOLE_LIBRARY") or os.path.join(_HERE, "libdipole.so")
 
 DIPOLE_OK = 0
 DIPOLE_EINVAL = -1
@@ -27,6 +29,7 @@ DIPOLE_ECUDA = -3
 DIPOLE_ENONFINITE = -4
 DIPOLE_ETRAVERSAL = -5
 DIPOLE_ESTATE = -6
+DIPOLE_EBOUNDS = -7
 DIPOLE_F32 = 0
 DIPOLE_BF16 = 1
 DIPOLE_BF16_MOMENTS = 2
@@ -40,7 +43,7 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_forward_grid", "dipole_adjoint_acc_size", "dipole_adjoint_stage1",
             "dipole_adjoint_stage2", "dipole_adjoint_queries", "dipole_query_packet_counts",
             "dipole_device_allocations", "dipole_traversal_timer", "dipole_traversal_elapsed",
-            "dipole_refit_appearance"]
+            "dipole_refit_appearance", "dipole_checked_build"]
 
 
 class DipoleError(RuntimeError):
@@ -125,6 +128,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.dipole_kernel_launches.restype = ctypes.c_uint64
         lib.dipole_device_allocations.argtypes = []
         lib.dipole_device_allocations.restype = ctypes.c_uint64
+        lib.dipole_checked_build.argtypes = []
+        lib.dipole_checked_build.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -141,6 +146,11 @@ def dipole_kernel_launches() -> int:
 def dipole_device_allocations() -> int:
     """Device allocations made by the library so far in this process."""
     return int(load_library().dipole_device_allocations())
+
+
+def dipole_checked_build() -> bool:
+    """True when the loaded library is the checked build (DIPOLE_CHECKED)."""
+    return bool(load_library().dipole_checked_build())
 
 
 TIMER_MODES = {"forward": 0, "adjoint": 1, "counts": 2, "forward_grad": 3, "adjoint_grad": 4,
