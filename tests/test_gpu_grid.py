@@ -1,7 +1,7 @@
 """Dense-grid primal queries (the evaluation grid that the paper meshes with
 marching cubes, Sec. 7): the kernel generates the grid points itself; results
 equal dipole_forward on the same points up to the rounding of the partial
-sums (which are folded every 16 steps of the warp, so they depend on a query's
+sums (which are folded every 32 steps of the warp, so they depend on a query's
 warp neighbours), with the same traversal, and the oracle within 1e-4."""
 import numpy as np
 import pytest
