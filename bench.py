@@ -563,7 +563,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_configs:
         del flush
         torch.cuda.empty_cache()
-        configs = config_rows(torch, dp, dev, stream)
+        configs = config_rows(torch, dp, dev, stream, clocks)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -597,12 +597,14 @@ def _bf16_round(a):
     return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32).reshape(a.shape)
 
 
-def config_rows(torch, dp, dev, stream):
+def config_rows(torch, dp, dev, stream, clocks=None):
     """The workloads besides the headline one (sphere-2k and scene-200k
     forward only, scene-3m-bf16 forward + adjoint in bf16 and in float32),
     each timed with CUDA events (median of 5, a 512 MB L2 flush before each)
     and checked against the oracle's FP64 Barnes-Hut on a query sample (all
-    queries for sphere-2k, where the plain O(NQ) sum is also given)."""
+    queries for sphere-2k, where the plain O(NQ) sum is also given).  The
+    scene-3m-bf16 row carries the roofline block of its float32 traversals
+    (working set beyond the L2: the HBM bound)."""
     import oracle
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -701,6 +703,20 @@ def config_rows(torch, dp, dev, stream):
         dp.dipole_adjoint(h, X_, BETA, gs, grad, False)
         outs[dt + "_adj"] = grad.cpu().numpy()
         del mu
+    # roofline of the float32 traversals: per-query and per-packet counts of this tree
+    dp.dipole_refit(h, T(w.mu))
+    npk = (Q + 31) // 32
+    cnt = torch.empty((Q, 3), dtype=torch.int32, device=dev)
+    pcnt = torch.empty((npk, 4), dtype=torch.int32, device=dev)
+    dp.dipole_query_packet_counts(h, X_, BETA, pcnt, counts=cnt)
+    sums = cnt.to(torch.int64).sum(0).tolist()
+    usums = pcnt.to(torch.int64).sum(0).tolist()
+    nodes = dp.dipole_tree_info_get(h)["n_nodes"]
+    del cnt, pcnt
+    res["roofline"] = roofline_block(
+        torch, dev, dp, C, Q, c.n, nodes, sums, usums,
+        {"forward": res["f32"]["forward_kernel_ms"], "adjoint": res["f32"]["adjoint_kernel_ms"]},
+        clocks, 0)
     dp.dipole_sync_status(h)
     dp.dipole_tree_destroy(h)
     res["speedup_bf16_vs_f32"] = {

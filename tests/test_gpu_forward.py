@@ -41,7 +41,7 @@ def test_scene_betas(beta):
     assert np.array_equal(c.astype(np.int64), rc)
 
 
-@pytest.mark.parametrize("C", [1, 2, 3, 5, 8, 16, 20, 33, 36, 40])
+@pytest.mark.parametrize("C", [1, 2, 3, 5, 8, 16, 20, 33, 36, 40, 64])
 def test_channel_counts(C):
     w = syn.workload("scene-200k", scale=0.05)
     mu = syn.attributes(w.cloud.n, C, seed=C)
