@@ -160,14 +160,16 @@ __device__ __forceinline__ void desing_factors(float d2, float inv_eps, float& a
 // traversal (two per packet in the forward, the plan's cuts in the adjoints);
 // the same range holds for every channel group, whose walks are identical.
 template <int CG, typename AT, int MODE, bool RANGED>
-__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kForwardGradDot || MODE == kAdjointGeom) ? 3 : 2)
+__global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kForwardGradDot ||
+                                               MODE == kAdjointGrad) ? 4
+                                              : (MODE == kAdjointGeom) ? 3 : 2)
     k_query_grad(const QueryArgs a) {
     static_assert(CG == 1 || CG == 2 || CG == 4, "channel group");
     constexpr bool FWD = MODE == kForwardGrad || MODE == kForwardGradDot;
     constexpr bool DOT = MODE == kForwardGradDot;  // only sum_c g^c grad D^c
     constexpr bool GEOM = MODE == kAdjointGeom;  // also the normal and radius gradients
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr unsigned kFoldSteps = 16;
+    constexpr unsigned kFoldSteps = 32;
     constexpr int NV = FWD ? 4 * CG : 1;  // D and grad D per channel: [4c] D, [4c+1+k] d/dx_k
     const int lane = threadIdx.x & 31;
     const NodeRec* __restrict__ nodes = a.nodes;
@@ -214,11 +216,26 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
         for (int k = 0; k < (DOT ? 3 : 1); ++k) gq[k] = 0.f;
 
         for (int c0 = 0; c0 < Cp; c0 += CG) {
-            // forward: blocked Kahan sums (plain partial sums folded every
-            // kFoldSteps warp steps into compensated ones)
-            float acc[NV], cmp[NV], part[NV];
+            // forward: blocked Kahan sums, plain partial sums (registers) folded
+            // every kFoldSteps warp steps into compensated ones (shared memory,
+            // one column per thread, touched only at a fold: 32 KB per block at
+            // CG = 4, which leaves the registers to the walk and four blocks per SM)
+            __shared__ float sh_acc[FWD ? NV : 1][kQThreads], sh_cmp[FWD ? NV : 1][kQThreads];
+            float part[NV];
 #pragma unroll
-            for (int i = 0; i < NV; ++i) { acc[i] = 0.f; cmp[i] = 0.f; part[i] = 0.f; }
+            for (int i = 0; i < NV; ++i) {
+                part[i] = 0.f;
+                if (FWD) {
+                    sh_acc[FWD ? i : 0][threadIdx.x] = 0.f;
+                    sh_cmp[FWD ? i : 0][threadIdx.x] = 0.f;
+                }
+            }
+            auto kahan_into = [&](int i, float v) {
+                kahan_add(sh_acc[FWD ? i : 0][threadIdx.x], sh_cmp[FWD ? i : 0][threadIdx.x], v);
+            };
+            auto total = [&](int i) -> float {
+                return __fsub_rn(sh_acc[FWD ? i : 0][threadIdx.x], sh_cmp[FWD ? i : 0][threadIdx.x]);
+            };
             // adjoint: upstream values and gradients of this group, scaled by
             // 1/(4 pi), in lane_channel_order
             float gl[FWD ? 1 : CG], Gl[FWD ? 1 : 3 * CG];
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                     }
 #pragma unroll
                     for (int i = 0; i < NV; ++i) {
-                        kahan_add(acc[i], cmp[i], part[i]);
+                        kahan_into(i, part[i]);
                         part[i] = 0.f;
                     }
                     // plan record (first channel group): nodes of this part's steps 128, 256, 384
@@ -475,7 +492,7 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
             steps += gsteps;
             if (FWD) {
 #pragma unroll
-                for (int i = 0; i < NV; ++i) kahan_add(acc[i], cmp[i], part[i]);
+                for (int i = 0; i < NV; ++i) kahan_into(i, part[i]);
                 if (valid) {
 #pragma unroll
                     for (int c = 0; c < CG; ++c) {
@@ -485,18 +502,18 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                             const float gc = a.g[o];
 #pragma unroll
                             for (int k = 0; k < 3; ++k)
-                                gq[k] = fmaf(gc, __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi, gq[k]);
+                                gq[k] = fmaf(gc, total(4 * c + 1 + k) * kInv4Pi, gq[k]);
                             continue;
                         }
                         // ranged: the two parts of a packet add into the zeroed outputs
-                        const float d = __fsub_rn(acc[4 * c], cmp[4 * c]) * kInv4Pi;
+                        const float d = total(4 * c) * kInv4Pi;
                         if (a.out) {
                             if (RANGED) atomicAdd(a.out + o, d);
                             else a.out[o] = d;
                         }
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            const float v = __fsub_rn(acc[4 * c + 1 + k], cmp[4 * c + 1 + k]) * kInv4Pi;
+                            const float v = total(4 * c + 1 + k) * kInv4Pi;
                             if (RANGED) atomicAdd(a.gout + 3 * o + k, v);
                             else a.gout[3 * o + k] = v;
                         }
