@@ -65,6 +65,18 @@ __device__ __forceinline__ float radial_over_d3(float d2, float inv_eps, int ker
     return kernel == 0 ? rho_over_d3(d2, inv_eps) : desing_over_d3(d2, inv_eps);
 }
 
+// Bring the bytes [p, p + bytes) into L1 ahead of their loads: lane i
+// prefetches the i-th 128-byte line of the range (bytes <= 32 lines), one
+// instruction for the warp.  The forward reads an opened leaf's point records
+// and attribute rows one point after another; prefetched, they come from L1
+// (value forward -2%, gradient forward -3%; the attribute adjoint, with its
+// heavier L1 traffic, lost 5%).
+__device__ __forceinline__ void prefetch_l1(const void* p, int bytes, int lane) {
+    const uintptr_t b = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t line = (b & ~uintptr_t(127)) + 128u * (uintptr_t)lane;
+    if (line < b + (uintptr_t)bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
+}
+
 // Kahan-compensated add: s + (c) tracks the sum, c holds the lost low part
 // with the sign convention sum = s - c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {

@@ -25,17 +25,6 @@
 namespace dip {
 namespace {
 
-// Bring the bytes [p, p + bytes) into L1 ahead of their loads: lane i
-// prefetches the i-th 128-byte line of the range (bytes <= 32 lines), one
-// instruction for the warp.  The forward reads an opened leaf's point records
-// and attribute rows one point after another; prefetched, they come from L1
-// (forward kernel -2%; the adjoint, with its heavier L1 traffic, lost 5%).
-__device__ __forceinline__ void prefetch_l1(const void* p, int bytes, int lane) {
-    const uintptr_t b = reinterpret_cast<uintptr_t>(p);
-    const uintptr_t line = (b & ~uintptr_t(127)) + 128u * (uintptr_t)lane;
-    if (line < b + (uintptr_t)bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
-}
-
 // RANGED: each work item is a preorder range [lo, hi) of one packet's walk; a
 // lane enters it in the state its depth-first walk has at lo (decided by lo's
 // ancestors alone) and stops at hi, so the items of a packet together visit

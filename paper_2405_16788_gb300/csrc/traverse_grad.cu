@@ -341,17 +341,17 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                             s[4 * j] = s_first[j].x; s[4 * j + 1] = s_first[j].y;
                             s[4 * j + 2] = s_first[j].z; s[4 * j + 3] = s_first[j].w;
                         }
-                        if (far) {
+                        // no per-lane predicate: a lane that did not take the node
+                        // has fa = fb = 0 and adds exact zeros
 #pragma unroll
-                            for (int c = 0; c < CG; ++c) {
-                                const float sx = s[3 * c], sy = s[3 * c + 1], sz = s[3 * c + 2];
-                                const float sv = fmaf(sx, vx, fmaf(sy, vy, sz * vz));
-                                const float bsv = fb * sv;
-                                part[4 * c] = fmaf(fa, sv, part[4 * c]);
-                                part[4 * c + 1] -= fmaf(fa, sx, bsv * vx);
-                                part[4 * c + 2] -= fmaf(fa, sy, bsv * vy);
-                                part[4 * c + 3] -= fmaf(fa, sz, bsv * vz);
-                            }
+                        for (int c = 0; c < CG; ++c) {
+                            const float sx = s[3 * c], sy = s[3 * c + 1], sz = s[3 * c + 2];
+                            const float sv = fmaf(sx, vx, fmaf(sy, vy, sz * vz));
+                            const float bsv = fb * sv;
+                            part[4 * c] = fmaf(fa, sv, part[4 * c]);
+                            part[4 * c + 1] -= fmaf(fa, sx, bsv * vx);
+                            part[4 * c + 2] -= fmaf(fa, sy, bsv * vy);
+                            part[4 * c + 3] -= fmaf(fa, sz, bsv * vz);
                         }
                     } else {
                         float val[3 * CG];
@@ -396,6 +396,11 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                     const int f = meta.y;
                     const int cnt =
                         in_bounds(f >= 0 && meta.z >= 0 && (int64_t)f + meta.z <= a.npts, a.status) ? meta.z : 0;
+                    if (FWD) {
+                        prefetch_l1(pts + f, cnt * (int)sizeof(PointRec), lane);
+                        prefetch_l1(reinterpret_cast<const AT*>(a.mu) + (size_t)f * Cp + c0,
+                                    cnt * Cp * (int)sizeof(AT), lane);
+                    }
                     for (int j = 0; j < cnt; ++j) {
                         const PointRec pr = pts[f + j];
                         float fa = 0.f, fb = 0.f, wu = 0.f, pae = 0.f, pbe = 0.f;
@@ -418,14 +423,12 @@ __global__ void __launch_bounds__(kQThreads, (MODE == kForwardGrad || MODE == kF
                             const float g2 = -fmaf(fa, pr.w.z, bwu * uz);
                             float m[CG];
                             load_row<AT>(reinterpret_cast<const AT*>(a.mu) + (size_t)(f + j) * Cp + c0, m, CG);
-                            if (open_leaf) {
 #pragma unroll
-                                for (int c = 0; c < CG; ++c) {
-                                    part[4 * c] = fmaf(kd, m[c], part[4 * c]);
-                                    part[4 * c + 1] = fmaf(g0, m[c], part[4 * c + 1]);
-                                    part[4 * c + 2] = fmaf(g1, m[c], part[4 * c + 2]);
-                                    part[4 * c + 3] = fmaf(g2, m[c], part[4 * c + 3]);
-                                }
+                            for (int c = 0; c < CG; ++c) {  // kd = g = 0 off the leaf
+                                part[4 * c] = fmaf(kd, m[c], part[4 * c]);
+                                part[4 * c + 1] = fmaf(g0, m[c], part[4 * c + 1]);
+                                part[4 * c + 2] = fmaf(g1, m[c], part[4 * c + 2]);
+                                part[4 * c + 3] = fmaf(g2, m[c], part[4 * c + 3]);
                             }
                         } else {
                             float val[CG];
