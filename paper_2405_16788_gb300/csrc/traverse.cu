@@ -113,13 +113,14 @@ k_query(const QueryArgs a) {
 
         // Forward sums: plain float partial sums (part), folded every kFoldSteps
         // warp steps into a Kahan-compensated sum (acc, cmp) for up to 36
-        // channels; per-term Kahan for more (register budget).  From 8 channels
+        // channels; per-term Kahan for more (register budget).  From 4 channels
         // on the Kahan pairs live in shared memory (one column per thread, read
-        // and written only at a fold), which leaves the registers to the walk
-        // and keeps three blocks resident per SM.
+        // and written only at a fold), which leaves the registers to the walk:
+        // six blocks per SM without spills in the walk at 4 channels, three from
+        // 8 to 32, two at 36.
         constexpr bool kBlocked = CP <= 36;
         constexpr unsigned kFoldSteps = 32;
-        constexpr bool kSmem = MODE == kForward && CP >= 8 && CP <= 36;
+        constexpr bool kSmem = MODE == kForward && CP >= 4 && CP <= 36;
         constexpr int kRegSums = (MODE == kForward && !kSmem) ? CP : 1;
         __shared__ float sh_acc[kSmem ? CP : 1][kQThreads], sh_cmp[kSmem ? CP : 1][kQThreads];
         float acc[kRegSums], cmp[kRegSums];
