@@ -283,12 +283,19 @@ k_query(const QueryArgs a) {
                             }
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
-                                float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
-                                if (NF && c0 + c >= a.G) term = s[3 * c] * wf;
+                                // -k (S.(x - p~)) = k S.(p~ - x), the kernel factor folded
+                                // into the accumulation
+                                const float dot =
+                                    fmaf(dx, s[3 * c], fmaf(dy, s[3 * c + 1], dz * s[3 * c + 2]));
+                                const bool nf = NF && c0 + c >= a.G;
                                 // blocked sums: k = wf = 0 on lanes that did not take the
                                 // node, whose term is an exact zero
-                                if (kBlocked) part[c0 + c] += term;
-                                else if (far) add_term(c0 + c, term);
+                                if (kBlocked) {
+                                    part[c0 + c] =
+                                        nf ? fmaf(s[3 * c], wf, part[c0 + c]) : fmaf(-k, dot, part[c0 + c]);
+                                } else if (far) {
+                                    add_term(c0 + c, nf ? s[3 * c] * wf : -k * dot);
+                                }
                             }
                         }
                     } else if (MODE == kAdjoint && !NF) {
@@ -392,9 +399,9 @@ k_query(const QueryArgs a) {
                                 load_row<AT>(mrow + c0, m, CH);
 #pragma unroll
                                 for (int c = 0; c < CH; ++c) {
-                                    const float v = (NF && c0 + c >= a.G ? kn : k) * m[c];
-                                    if (kBlocked) part[c0 + c] += v;  // k = kn = 0 off the leaf
-                                    else if (open_leaf) add_term(c0 + c, v);
+                                    const float kk = NF && c0 + c >= a.G ? kn : k;
+                                    if (kBlocked) part[c0 + c] = fmaf(kk, m[c], part[c0 + c]);  // k = kn = 0 off the leaf
+                                    else if (open_leaf) add_term(c0 + c, kk * m[c]);
                                 }
                             }
                         }
