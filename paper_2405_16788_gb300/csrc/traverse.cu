@@ -283,18 +283,22 @@ k_query(const QueryArgs a) {
                             }
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
-                                // -k (S.(x - p~)) = k S.(p~ - x), the kernel factor folded
-                                // into the accumulation
-                                const float dot =
-                                    fmaf(dx, s[3 * c], fmaf(dy, s[3 * c + 1], dz * s[3 * c + 2]));
                                 const bool nf = NF && c0 + c >= a.G;
                                 // blocked sums: k = wf = 0 on lanes that did not take the
                                 // node, whose term is an exact zero
-                                if (kBlocked) {
+                                if (CP <= 4 && kBlocked) {
+                                    // -k (S.(x - p~)) = k S.(p~ - x): the kernel factor folded
+                                    // into the accumulation (fewer instructions; from 8
+                                    // channels, latency bound, the scaled vector is faster)
+                                    const float dot =
+                                        fmaf(dx, s[3 * c], fmaf(dy, s[3 * c + 1], dz * s[3 * c + 2]));
                                     part[c0 + c] =
                                         nf ? fmaf(s[3 * c], wf, part[c0 + c]) : fmaf(-k, dot, part[c0 + c]);
-                                } else if (far) {
-                                    add_term(c0 + c, nf ? s[3 * c] * wf : -k * dot);
+                                } else {
+                                    float term = fmaf(vx, s[3 * c], fmaf(vy, s[3 * c + 1], vz * s[3 * c + 2]));
+                                    if (nf) term = s[3 * c] * wf;
+                                    if (kBlocked) part[c0 + c] += term;
+                                    else if (far) add_term(c0 + c, term);
                                 }
                             }
                         }
