@@ -519,6 +519,23 @@ uint64_t dipole_device_allocations(void);
  */
 int dipole_checked_build(void);
 
+/*
+ * Treelet: with enable = 1, the value forward (dipole_forward, the planned and
+ * grid forms; not the no-allocation form) of trees with up to 4 channels and
+ * float moments stages the upper tree — the nodes of depth < 3 (at most 73),
+ * their records and their first moment chunk — in each block's shared memory
+ * by one bulk copy (cp.async.bulk, no multicast) and reads those nodes from
+ * there (Alg. 1 PrimalQuery, the nodes every walk visits first).  Results are
+ * bit-identical with and without it.  The first forward after enabling
+ * allocates a block of 32 bytes per node plus 8 KB for the tree (freed with
+ * it); every forward rewrites the staged records, so forwards of one tree that
+ * overlap on the GPU race on them.  Measured 2% slower than without it on the
+ * 1M-point workload (the walk is issue bound; the nodes staged are L1 hits
+ * anyway), so it is off by default.  enable = 0 turns it off.
+ * Errors: DIPOLE_EINVAL for a NULL tree or enable not 0 or 1.
+ */
+int dipole_set_treelet(dipole_tree* tree, int32_t enable);
+
 /* Query modes of the traversal timer below. */
 typedef enum {
     DIPOLE_TIMER_FORWARD = 0,       /* dipole_forward*, dipole_forward_grid */

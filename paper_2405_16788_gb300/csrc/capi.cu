@@ -35,7 +35,8 @@ void configure_pool_once() {
 
 void free_tree_memory(dipole_tree* t) {
     // the arrays live in these blocks, except the lazily made normal/radius scratch
-    void* bufs[] = {t->point_block, t->topo_block, t->node_block, t->attr_block, t->dE, t->dgeo};
+    void* bufs[] = {t->point_block, t->topo_block, t->node_block, t->attr_block, t->dE, t->dgeo,
+                    t->tl_block};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -89,6 +90,13 @@ uint64_t dipole_kernel_launches(void) { return g_launches.load(std::memory_order
 uint64_t dipole_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 int dipole_checked_build(void) { return dip::kChecked ? 1 : 0; }
+
+int dipole_set_treelet(dipole_tree* tree, int32_t enable) {
+    if (!tree) return dip_fail(DIPOLE_EINVAL, "dipole_set_treelet: tree is NULL");
+    if (enable != 0 && enable != 1) return dip_fail(DIPOLE_EINVAL, "dipole_set_treelet: enable must be 0 or 1");
+    tree->treelet = enable;
+    return DIPOLE_OK;
+}
 
 int dipole_traversal_timer(int32_t enable) {
     if (enable != 0 && enable != 1)

@@ -50,6 +50,11 @@ struct QueryArgs {
     unsigned long long* work;
     int64_t npts;            // points of the tree (leaf point ranges lie in [0, npts))
     int64_t n_slots;         // entries of items (ranged work)
+    // treelet: the top levels of the tree staged in shared memory (forward, up to
+    // 4 channels); walk states are keys (node << kTLSlotBits | slot hint)
+    const void* tl;             // TLRec [kTLMax]
+    const uint32_t* tl_node;    // [kTLMax] treelet node ids, ascending
+    const NodeRec* nodes_k;     // node records with meta.x = the packed key of the skip
     const uint32_t* porder;  // packet (or item) order, or NULL for sorted order
     GridSpec grid;           // dense-grid queries instead of q / qperm
     uint32_t* plan;          // query plan being written (forward): kPlanWords per packet

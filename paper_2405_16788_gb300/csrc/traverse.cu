@@ -25,6 +25,38 @@
 namespace dip {
 namespace {
 
+// Value v (0..23) of a group of 24 bf16 values held in three 16-byte vectors,
+// as a float (v is a compile-time index after unrolling).
+__device__ __forceinline__ float bf16_in_group(const uint4* g, int v) {
+    const uint4 q = g[v >> 3];
+    const int w = (v >> 1) & 3;
+    const unsigned u = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+    return __uint_as_float((v & 1) ? (u & 0xffff0000u) : (u << 16));
+}
+
+// Treelet (the upper tree in shared memory): nodes of depth < kTLDepth in
+// preorder, at most kTLMax, with their records, the packed keys of their skip
+// and first child and the first moment chunk (up to 4 channels).
+constexpr int kTLDepth = 3;
+constexpr int kTLMax = 80;
+constexpr unsigned kTLSlotBits = 7, kTLInv = 127u;
+struct __align__(16) TLRec {
+    float4 geo;
+    int4 meta;      // meta.x: the packed key of the skip
+    uint4 ext;      // ext.x: the packed key of the first child
+    float4 mom[3];  // the moment row's first 12 floats
+};
+
+// The slot of node u among the ascending treelet node ids, kTLInv if absent.
+__device__ __forceinline__ unsigned tl_slot_of(const uint32_t* ids, int cnt, unsigned u) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ids[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    return (lo < cnt && ids[lo] == u) ? (unsigned)lo : kTLInv;
+}
+
 // RANGED: each work item is a preorder range [lo, hi) of one packet's walk; a
 // lane enters it in the state its depth-first walk has at lo (decided by lo's
 // ancestors alone) and stops at hi, so the items of a packet together visit
@@ -37,16 +69,12 @@ namespace {
 // kernel with channels [a.G, C) interpolated without the foreshortening term
 // (a point adds A rho(r/eps)/(4 pi r^2) mu, a far node rho(d/eps~)/(4 pi d^2)
 // M with M = sum A mu in the first slot of the channel's moment row).
-// Value v (0..23) of a group of 24 bf16 values held in three 16-byte vectors,
-// as a float (v is a compile-time index after unrolling).
-__device__ __forceinline__ float bf16_in_group(const uint4* g, int v) {
-    const uint4 q = g[v >> 3];
-    const int w = (v >> 1) & 3;
-    const unsigned u = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
-    return __uint_as_float((v & 1) ? (u & 0xffff0000u) : (u << 16));
-}
-
-template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16>
+//
+// M16: far-node moments from the bf16 copy (DIPOLE_BF16_MOMENTS).  TL: the
+// treelet (dipole_set_treelet): walk states are packed keys, node << 7 | the
+// node's treelet slot (127 outside it), carried by every skip and child key,
+// so a treelet node is read from shared memory without a lookup.
+template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16, bool TL>
 __global__ void __launch_bounds__(kQThreads, (MODE == kForward && CP <= 4) ? 6
                                           : (MODE == kForward && CP <= 32) ? 3 : (MODE == kForward && CP <= 36) ? 2 : 1)
 k_query(const QueryArgs a) {
@@ -55,12 +83,63 @@ k_query(const QueryArgs a) {
     constexpr int SR = srow(CP);
     constexpr int SR16 = srow16(CP);
     constexpr bool kS16 = MODE == kForward && M16;  // far-node moments from the bf16 copy
+    constexpr bool kTL = TL && MODE == kForward && CP <= 4 && !M16;
     constexpr int CH = CP < 4 ? CP : 4;  // channels per chunk
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const NodeRec* __restrict__ nodes = a.nodes;
+    const NodeRec* __restrict__ nodes = kTL ? a.nodes_k : a.nodes;
     const PointRec* __restrict__ pts = a.pts;
     const unsigned nn = a.nn;
+
+    // the treelet, staged once per block by one bulk copy (no multicast)
+    __shared__ TLRec sh_tl[kTL ? kTLMax : 1];
+    __shared__ __align__(16) uint32_t sh_tln[kTL ? kTLMax : 4];
+    __shared__ __align__(8) unsigned long long sh_bar;
+    __shared__ int sh_tl_ok;
+    if (kTL) {
+        const unsigned bar = (unsigned)__cvta_generic_to_shared(&sh_bar);
+        constexpr unsigned kBytes = (unsigned)(sizeof(TLRec) * kTLMax + sizeof(uint32_t) * kTLMax);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            sh_tl_ok = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+                         ::"r"(bar), "r"(kBytes) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"((unsigned)__cvta_generic_to_shared(sh_tl)), "l"(a.tl),
+                "r"((unsigned)(sizeof(TLRec) * kTLMax)), "r"(bar) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"((unsigned)__cvta_generic_to_shared(sh_tln)), "l"(a.tl_node),
+                "r"((unsigned)(sizeof(uint32_t) * kTLMax)), "r"(bar) : "memory");
+        }
+        // bounded wait for phase 0
+        unsigned done = 0;
+        for (int it = 0; it < (1 << 22) && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done) : "r"(bar) : "memory");
+        }
+        if (!done) {
+            atomicOr(a.status, kStatusTraversal);
+            sh_tl_ok = 0;  // (benign race: every failing thread writes 0)
+            // the copies may still be in flight: wait for them again, bounded
+            for (int it = 0; it < (1 << 22) && !done; ++it) {
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(done) : "r"(bar) : "memory");
+            }
+        }
+        __syncthreads();
+        if (!sh_tl_ok) return;
+    }
+    auto key_of = [&](unsigned u) -> unsigned {  // packed key of node u (treelet search)
+        return kTL ? ((u << kTLSlotBits) | tl_slot_of(sh_tln, kTLMax, u)) : u;
+    };
 
     for (;;) {
         unsigned long long pk = 0;
@@ -179,11 +258,11 @@ k_query(const QueryArgs a) {
         int n_tested = 0, n_far = 0, n_pts = 0;
         unsigned u_far = 0, u_pts = 0;  // warp counts (kCount with a.ucounts)
 
-        unsigned next = valid ? lo : nn;
+        unsigned next = key_of(valid ? lo : nn);
         if (RANGED && lo > 0u && lo < nn) {
             // the walk reaches lo unless an ancestor of lo is far; it then
             // resumes at the topmost far ancestor's skip, the largest of them
-            const unsigned start = next;
+            const unsigned start = kTL ? (next >> kTLSlotBits) : next;
             int32_t u = a.parent[lo];
             for (int up = 0; up <= kMaxLevel + 1 && u >= 0; ++up) {
                 if (!in_bounds(u < (int32_t)nn, a.status)) break;
@@ -194,7 +273,7 @@ k_query(const QueryArgs a) {
                 const float dz = __fsub_rn(x2, geo.z);
                 const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
                 const float R = __fmul_rn(a.beta, geo.w);
-                if (start == lo && d2 > __fmul_rn(R, R)) next = max(next, (unsigned)meta.x);
+                if (start == lo && d2 > __fmul_rn(R, R)) next = max(next, (unsigned)meta.x);  // packed with kTL
                 u = a.parent[u];
             }
         }
@@ -210,7 +289,8 @@ k_query(const QueryArgs a) {
         };
         // one warp step of the walk; false once the walk is over
         auto walk_step = [&](const bool fold_here) -> bool {
-            const unsigned n = __reduce_min_sync(FULL, next);
+            const unsigned key = __reduce_min_sync(FULL, next);
+            const unsigned n = kTL ? key >> kTLSlotBits : key;
             if (MODE == kForward) {
                 if (n >= hi) return false;
             } else if ((n >= hi) | (steps >= nn)) {  // a well-formed tree needs at most nn steps
@@ -218,21 +298,35 @@ k_query(const QueryArgs a) {
                 return false;
             }
             ++steps;
-            const float4 geo = __ldg(&nodes[n].geo);
-            const int4 meta = __ldg(&nodes[n].meta);
-            const bool act = next == n;
+            const unsigned slot = kTL ? (key & kTLInv) : kTLInv;
+            float4 geo;
+            int4 meta;
+            unsigned ckey;
             // forward: the node's first moment chunk is loaded before the far test
             // so that its latency overlaps the test (most visited nodes are far
             // for some lane)
             float4 s_first[MODE == kForward && !kS16 ? (3 * CH + 3) / 4 : 1];
             uint4 grp[kS16 ? 3 : 1];  // bf16 moments: the row's current group of 8 channels
-            if (MODE == kForward && kS16) {
-                load_group16(n, 0, grp);
-            } else if (MODE == kForward) {
-                const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR);
+            if (kTL && slot != kTLInv) {
+                const TLRec& r = sh_tl[kTL ? slot : 0];
+                geo = r.geo;
+                meta = r.meta;
+                ckey = r.ext.x;
 #pragma unroll
-                for (int j = 0; j < (3 * CH + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
+                for (int j = 0; j < (3 * CH + 3) / 4; ++j) s_first[j] = r.mom[j];
+            } else {
+                geo = __ldg(&nodes[n].geo);
+                meta = __ldg(&nodes[n].meta);
+                ckey = kTL ? key + (1u << kTLSlotBits) : n + 1u;
+                if (MODE == kForward && kS16) {
+                    load_group16(n, 0, grp);
+                } else if (MODE == kForward) {
+                    const float4* sp = reinterpret_cast<const float4*>(a.S + (size_t)n * SR);
+#pragma unroll
+                    for (int j = 0; j < (3 * CH + 3) / 4; ++j) s_first[j] = __ldg(sp + j);
+                }
             }
+            const bool act = next == key;
             // far test of Alg. 1 in a fixed float operation order
             const float dx = __fsub_rn(x0, geo.x);
             const float dy = __fsub_rn(x1, geo.y);
@@ -242,7 +336,7 @@ k_query(const QueryArgs a) {
             const bool far = act && (d2 > __fmul_rn(R, R));
             const bool leaf = meta.z > 0;
             const bool open_leaf = act && !far && leaf;
-            if (act) next = (far || leaf) ? (unsigned)meta.x : n + 1u;
+            if (act) next = (far || leaf) ? (unsigned)meta.x : ckey;
 
             if (MODE == kCount) {
                 if (act) {
@@ -670,11 +764,75 @@ void order_place(const uint32_t* ibucket, int64_t ni, uint32_t* ostate, uint32_t
 // Packets below this count are too few for the queue's tail to matter.
 constexpr int64_t kOrderMinPackets = 2048;
 
-template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16>
+// The treelet: nodes of depth < kTLDepth in preorder (one thread walks them),
+// their records with packed keys, and the moment rows' first 12 floats.
+__global__ void k_tl_build(unsigned nn, const NodeRec* __restrict__ nodes, const float* __restrict__ S,
+                           int SR, TLRec* __restrict__ tl, uint32_t* __restrict__ tl_node) {
+    __shared__ uint32_t ids[kTLMax];
+    __shared__ int dep[kTLMax];
+    __shared__ int cnt;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        uint32_t st_node[kTLDepth], st_next[kTLDepth];
+        int sp = 0;
+        ids[c] = 0; dep[c] = 0; ++c;
+        if (__ldg(&nodes[0].meta).z == 0 && kTLDepth > 1 && nn > 1) { st_node[0] = 0; st_next[0] = 1; sp = 1; }
+        bool bad = false;
+        while (sp > 0 && !bad) {
+            const uint32_t top = st_node[sp - 1], ch = st_next[sp - 1];
+            const uint32_t end = (uint32_t)__ldg(&nodes[top].meta).x;
+            if (ch >= end || ch >= nn) { --sp; continue; }
+            const int4 m = __ldg(&nodes[ch].meta);
+            if ((uint32_t)m.x <= ch || c >= kTLMax) { bad = true; break; }
+            st_next[sp - 1] = (uint32_t)m.x;
+            ids[c] = ch; dep[c] = sp; ++c;
+            if (m.z == 0 && sp + 1 < kTLDepth) { st_node[sp] = ch; st_next[sp] = ch + 1; ++sp; }
+        }
+        cnt = bad ? 0 : c;
+    }
+    __syncthreads();
+    const int n_tl = cnt;
+    for (int i = threadIdx.x; i < kTLMax; i += blockDim.x) tl_node[i] = i < n_tl ? ids[i] : 0xffffffffu;
+    for (int i = threadIdx.x; i < kTLMax; i += blockDim.x) {
+        TLRec r;
+        r.geo = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.meta = make_int4(0, 0, 0, 0);
+        r.ext = make_uint4(0u, 0u, 0u, 0u);
+        for (int j = 0; j < 3; ++j) r.mom[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n_tl) {
+            const uint32_t v = ids[i];
+            r.geo = __ldg(&nodes[v].geo);
+            r.meta = __ldg(&nodes[v].meta);
+            const uint32_t sk = (uint32_t)r.meta.x;
+            r.meta.x = (int)((sk << kTLSlotBits) | tl_slot_of(ids, n_tl, sk));
+            r.ext.x = ((v + 1u) << kTLSlotBits) | (r.meta.z == 0 && dep[i] + 1 < kTLDepth ? tl_slot_of(ids, n_tl, v + 1u) : kTLInv);
+            float m[12];
+            for (int j = 0; j < 12; ++j) m[j] = j < SR ? S[(size_t)v * SR + j] : 0.f;
+            for (int j = 0; j < 3; ++j) r.mom[j] = make_float4(m[4 * j], m[4 * j + 1], m[4 * j + 2], m[4 * j + 3]);
+        }
+        tl[i] = r;
+    }
+}
+
+// Node records for the treelet walk: meta.x = the packed key of the skip.
+__global__ void k_tl_keys(unsigned nn, const NodeRec* __restrict__ nodes, const uint32_t* __restrict__ tl_node,
+                          NodeRec* __restrict__ out) {
+    __shared__ uint32_t ids[kTLMax];
+    for (int i = threadIdx.x; i < kTLMax; i += blockDim.x) ids[i] = tl_node[i];
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+        NodeRec r = nodes[t];
+        const uint32_t sk = (uint32_t)r.meta.x;
+        r.meta.x = (int)((sk << kTLSlotBits) | tl_slot_of(ids, kTLMax, sk));
+        out[t] = r;
+    }
+}
+
+template <int CP, typename AT, int MODE, int KERN, bool RANGED, bool M16, bool TL = false>
 void launch_query_m(const QueryArgs& a, cudaStream_t s) {
     static int per_sm = 0;
-    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN, RANGED, M16>, a.nq, per_sm);
-    note_launch(); k_query<CP, AT, MODE, KERN, RANGED, M16><<<grid, kQThreads, 0, s>>>(a);
+    const unsigned grid = query_grid(k_query<CP, AT, MODE, KERN, RANGED, M16, TL>, a.nq, per_sm);
+    note_launch(); k_query<CP, AT, MODE, KERN, RANGED, M16, TL><<<grid, kQThreads, 0, s>>>(a);
 }
 
 // bf16 node moments (a.S16) only in the forward with bf16 attributes
@@ -683,6 +841,12 @@ void launch_query_k(const QueryArgs& a, cudaStream_t s) {
     if constexpr (MODE == kForward && std::is_same<AT, __nv_bfloat16>::value) {
         if (a.S16) {
             launch_query_m<CP, AT, MODE, KERN, RANGED, true>(a, s);
+            return;
+        }
+    }
+    if constexpr (MODE == kForward && CP <= 4) {
+        if (a.tl) {
+            launch_query_m<CP, AT, MODE, KERN, RANGED, false, true>(a, s);
             return;
         }
     }
@@ -879,6 +1043,9 @@ int query_noalloc(const dipole_tree* t, const float* queries, int64_t q, float b
     a.work = work;
     a.npts = t->n;
     a.n_slots = 0;
+    a.tl = nullptr;
+    a.tl_node = nullptr;
+    a.nodes_k = nullptr;
     a.porder = nullptr;  // packets in sorted order
     a.plan = nullptr;
     a.items = nullptr;
@@ -911,6 +1078,9 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
     const bool adj_items = big && adjoint && plan_in && plan_cost;
     const bool fwd_items = big && mode != kCount && !plan_in;
     const int64_t ni = adj_items ? np * kPlanWords : fwd_items ? 2 * np : 0;
+    // treelet: the value forward with up to 4 float moments, nodes below 2^25 (packed keys)
+    const bool use_tl = t->treelet && mode == kForward && t->Cp <= 4 && !t->S16 &&
+                        t->nn < (int64_t(1) << 25);
     // one allocation for the call's scratch (each API call costs the host microseconds)
     auto take = [&](Carve& c) {
         c.take(&small, 2 + kOrderStateWords + 1);
@@ -1025,6 +1195,42 @@ int query(const dipole_tree* t, const QueryCall& call, cudaStream_t s) {
         a.work = work;
         a.npts = t->n;
         a.n_slots = ni;
+        a.tl = nullptr;
+        a.tl_node = nullptr;
+        a.nodes_k = nullptr;
+        if (use_tl) {
+            // the block and the keyed node copy are made once per tree (geometry
+            // only); the records, which carry the moments, at every call
+            auto take_tl = [&](Carve& c, TLRec** r, uint32_t** ids, NodeRec** nk) {
+                c.take(r, kTLMax);
+                c.take(ids, kTLMax);
+                c.take(nk, t->nn);
+            };
+            TLRec* tl_rec = nullptr;
+            uint32_t* tl_ids = nullptr;
+            NodeRec* nodes_k = nullptr;
+            const bool fresh = t->tl_block == nullptr;
+            if (fresh) {
+                Carve ct;
+                take_tl(ct, &tl_rec, &tl_ids, &nodes_k);
+                void* blk = nullptr;
+                DIP_CUDA_TRY(dev_alloc(&blk, ct.off, s));
+                t->tl_block = blk;  // cached state of the tree (mutable)
+            }
+            Carve ct{static_cast<char*>(t->tl_block), 0};
+            take_tl(ct, &tl_rec, &tl_ids, &nodes_k);
+            note_launch();
+            k_tl_build<<<1, 128, 0, s>>>((unsigned)t->nn, t->nodes, t->S, srow(t->Cp), tl_rec, tl_ids);
+            if (fresh) {
+                const int64_t kb = (t->nn + 255) / 256, kcap = (int64_t)num_sms() * 8;
+                note_launch();
+                k_tl_keys<<<(unsigned)(kb < kcap ? kb : kcap), 256, 0, s>>>((unsigned)t->nn, t->nodes,
+                                                                            tl_ids, nodes_k);
+            }
+            a.tl = tl_rec;
+            a.tl_node = tl_ids;
+            a.nodes_k = nodes_k;
+        }
         a.porder = porder;
         a.plan = plan_w;
         a.items = items;

@@ -65,6 +65,10 @@ struct dipole_tree {
     float* dgeo = nullptr;       // [n, 4] adjoint opened-leaf normal and radius terms
     int attr_Cp_alloc = 0;
     int attr_dtype_alloc = -1;
+    // treelet (dipole_set_treelet): the upper tree staged in shared memory by
+    // the value forward; its block (records + node copy) is made on first use
+    int treelet = 0;
+    mutable void* tl_block = nullptr;  // TLRec [80], treelet node ids [80], node copy [nn]
 
     dip::TreeView view() const {
         dip::TreeView v;

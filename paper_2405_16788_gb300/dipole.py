@@ -43,7 +43,7 @@ EXPORTED = ["dipole_build_tree", "dipole_refit", "dipole_forward", "dipole_adjoi
             "dipole_forward_grid", "dipole_adjoint_acc_size", "dipole_adjoint_stage1",
             "dipole_adjoint_stage2", "dipole_adjoint_queries", "dipole_query_packet_counts",
             "dipole_device_allocations", "dipole_traversal_timer", "dipole_traversal_elapsed",
-            "dipole_refit_appearance", "dipole_checked_build"]
+            "dipole_refit_appearance", "dipole_checked_build", "dipole_set_treelet"]
 
 
 class DipoleError(RuntimeError):
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.dipole_device_allocations.restype = ctypes.c_uint64
         lib.dipole_checked_build.argtypes = []
         lib.dipole_checked_build.restype = ctypes.c_int
+        lib.dipole_set_treelet.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         _lib = lib
         return lib
 
@@ -146,6 +147,11 @@ def dipole_kernel_launches() -> int:
 def dipole_device_allocations() -> int:
     """Device allocations made by the library so far in this process."""
     return int(load_library().dipole_device_allocations())
+
+
+def dipole_set_treelet(tree: int, enable: bool):
+    """Stage the upper tree in shared memory for the value forward (see the header)."""
+    _check(load_library().dipole_set_treelet(ctypes.c_void_p(tree), 1 if enable else 0))
 
 
 def dipole_checked_build() -> bool:
