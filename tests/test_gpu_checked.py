@@ -4,7 +4,7 @@ permutation, parents, a leaf's point range) before using it and report
 DIPOLE_EBOUNDS instead of an out-of-range access.  compute-sanitizer is not
 available here; this build stands in for its bounds checking.  The library is
 compiled separately (libdipole_checked.so), and the forward, adjoint, gradient,
-stage and appearance parity tests run against it in a child process, where
+stage, appearance, grid, bf16-moment and treelet tests run against it in a child process, where
 every status check (dipole_sync_status) would report a caught index."""
 import os
 import subprocess
@@ -29,7 +29,8 @@ def test_parity_tests_pass_on_the_checked_build():
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "gpu and not slow",
          "tests/test_gpu_forward.py", "tests/test_gpu_adjoint.py", "tests/test_gpu_grad.py",
-         "tests/test_gpu_stages.py", "tests/test_gpu_appearance.py", "tests/test_gpu_grid.py"],
+         "tests/test_gpu_stages.py", "tests/test_gpu_appearance.py", "tests/test_gpu_grid.py",
+         "tests/test_gpu_bf16_moments.py", "tests/test_gpu_treelet.py"],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
 
